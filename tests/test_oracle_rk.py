@@ -1,0 +1,115 @@
+"""Pins for the oracle's RK step (Sec. 2 eq. stageeq / rkheat, Sec. 3 eq. block_struct_AI)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import fem, rk
+from oracle import manufactured as mf
+from oracle import tableaux as T
+
+
+def small_problem(N=6, seed=0, dim=2):
+    kap = W.lognormal_kappa(dim, N, 0.5, seed)
+    return fem.Discretisation(dim, N, kap)
+
+
+@pytest.mark.parametrize("tab", [T.radau_iia(3), T.gauss_legendre(2), T.alexander(), T.lobatto_iiic2()])
+def test_stage_equations_hold(tab):
+    """Each stage satisfies M k_i + K (u_n + dt sum_j a_ij k_j) = F_i (eq. rkheat) to roundoff."""
+    d = small_problem()
+    rng = np.random.default_rng(1)
+    u = rng.standard_normal(d.n)
+    F = rng.standard_normal((tab.s, d.n))
+    dt = 0.05
+    solver = rk.KroneckerSolver(d.M, d.K, tab.A, dt)
+    _, k = rk.step(solver, d.K, tab.b, dt, u, F)
+    for i in range(tab.s):
+        res = d.M @ k[i] + d.K @ (u + dt * sum(tab.A[i, j] * k[j] for j in range(tab.s))) - F[i]
+        assert np.abs(res).max() < 1e-12 * (1 + np.abs(F).max())
+
+
+def test_eigen_solver_agrees_with_kronecker_lu():
+    d = small_problem(N=8)
+    tab = T.radau_iia(3)
+    rng = np.random.default_rng(2)
+    r = rng.standard_normal((3, d.n))
+    k1 = rk.KroneckerSolver(d.M, d.K, tab.A, 0.1).solve(r)
+    k2 = rk.EigenSolver(d.M, d.K, tab.A, 0.1).solve(r)
+    assert np.abs(k1 - k2).max() < 1e-11 * np.abs(k1).max()
+
+
+def test_dense_brute_force():
+    """Tiny grid: the sparse LU solve equals a dense solve of the same block system."""
+    d = small_problem(N=4)
+    tab = T.radau_iia(2)
+    dt = 0.3
+    Md, Kd = d.M.toarray(), d.K.toarray()
+    n = d.n
+    big = np.zeros((2 * n, 2 * n))
+    for i in range(2):
+        for j in range(2):
+            big[i * n:(i + 1) * n, j * n:(j + 1) * n] = (i == j) * Md + dt * tab.A[i, j] * Kd
+    r = np.random.default_rng(3).standard_normal(2 * n)
+    k = rk.KroneckerSolver(d.M, d.K, tab.A, dt).solve(r.reshape(2, n)).reshape(-1)
+    assert np.abs(k - np.linalg.solve(big, r)).max() < 1e-13
+
+
+def test_backward_euler_reduction():
+    """RadauIIA(1): (M + dt K) u_{n+1} = M u_n + dt F(t_{n+1}) (textbook backward Euler)."""
+    d = small_problem(N=7)
+    tab = T.radau_iia(1)
+    rng = np.random.default_rng(4)
+    u, F = rng.standard_normal(d.n), rng.standard_normal(d.n)
+    dt = 0.2
+    u1, _ = rk.step(rk.KroneckerSolver(d.M, d.K, tab.A, dt), d.K, tab.b, dt, u, F[None, :])
+    res = (d.M + dt * d.K) @ u1 - d.M @ u - dt * F
+    assert np.abs(res).max() < 1e-14 * 10
+
+
+@pytest.mark.parametrize("dim,N,tab", [(2, 32, T.radau_iia(2)), (2, 16, T.gauss_legendre(2)), (3, 6, T.radau_iia(3))])
+def test_eigenmode_matches_scalar_recursion(dim, N, tab):
+    """Full system from u0 = S with the manufactured load stays a(t_n) S, a from the scalar RK recursion."""
+    d = fem.Discretisation(dim, N)
+    S = d.to_interior(W.sine_initial(dim, N))
+    Fs = d.to_interior(W.sine_load_space(dim, N))
+    dt = 1 / 32
+    steps = 10
+    uN, _ = rk.run(d, tab, dt, steps, S, lambda t: W.sine_load_time(dim, t) * Fs)
+    a = mf.scalar_rk_amplitudes(dim, N, tab.A, tab.b, tab.c, dt, steps)
+    assert np.abs(uN - a[-1] * S).max() < 1e-13
+
+
+@pytest.mark.parametrize("tab,q", [(T.radau_iia(2), 2), (T.radau_iia(3), 3), (T.gauss_legendre(2), 2), (T.alexander(), 1)])
+def test_polynomial_exactness(tab, q):
+    """u(t) = sum_k t^k U_k with F = M u' + K u: exact for degree <= q (stage order), not for q+1."""
+    d = small_problem(N=5, seed=2)
+    rng = np.random.default_rng(5)
+    dt, steps = 0.1, 3
+    for deg, exact in ((q, True), (q + 1, False)):
+        U = rng.standard_normal((deg + 1, d.n))
+        u_of = lambda t: sum(t**k * U[k] for k in range(deg + 1))  # noqa: E731
+        du_of = lambda t: sum(k * t ** (k - 1) * U[k] for k in range(1, deg + 1))  # noqa: E731
+        load = lambda t: d.M @ du_of(t) + d.K @ u_of(t)  # noqa: E731
+        uN, _ = rk.run(d, tab, dt, steps, u_of(0.0), load)
+        err = np.abs(uN - u_of(dt * steps)).max() / np.abs(u_of(dt * steps)).max()
+        if exact:
+            assert err < 1e-12
+        else:
+            assert err > 1e-9
+
+
+@pytest.mark.parametrize("tab,p", [(T.radau_iia(1), 1), (T.radau_iia(2), 3), (T.radau_iia(3), 5),
+                                   (T.gauss_legendre(1), 2), (T.gauss_legendre(2), 4), (T.alexander(), 3)])
+def test_convergence_order_eigenmode(tab, p):
+    """Observed order against the exact semidiscrete amplitude: 2s-1 (RadauIIA), 2s (GL)."""
+    dim, N, Tend = 2, 8, 1.0
+    errs, dts = [], []
+    for k in range(3, 8):
+        dt = Tend / 2**k
+        a = mf.scalar_rk_amplitudes(dim, N, tab.A, tab.b, tab.c, dt, 2**k)
+        errs.append(abs(a[-1] - mf.exact_amplitude(dim, N, Tend)))
+        dts.append(dt)
+    errs, dts = np.array(errs), np.array(dts)
+    use = errs > 1e-13
+    slope = np.polyfit(np.log(dts[use][-3:]), np.log(errs[use][-3:]), 1)[0]
+    assert abs(slope - p) < 0.25, slope
