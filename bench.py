@@ -1,0 +1,461 @@
+#!/usr/bin/env python
+"""Benchmark of one RK time step of the stage-coupled heat solver on GB300.
+
+Workload (default ``heat2d-1024-radau3``): 2D heat equation u_t = div(kappa grad u) + f
+on the unit square, Q1 on 1024 x 1024 quads (1,050,625 nodes), per-cell lognormal
+kappa (sigma = 0.5 in log, seed 0), RadauIIA(3), dt = 1/256, FP64 FGMRES (rtol
+1e-10) with the block-lower-triangular stage preconditioner, one V(2,2)
+weighted-Jacobi (omega = 2/3) V-cycle per block on 6 levels.  Forcing and initial
+state are the sine manufactured solution.  A bench "step" is one full time step:
+right-hand side, FGMRES solve with V-cycle preconditioning, RK update.
+
+``python bench.py --gpus N --steps K --warmup W`` prints one JSON line.
+``--impl reference`` times the FP64 CPU oracle instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "time-steps/s and DOF·stage/s at fixed L2 error; stencil/V-cycle GB/s vs HBM peak"
+# FP64 arithmetic peak: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz (matches the nominal 1.25 TFLOP/s)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP64_CLASSES = ("stage_apply", "multidot", "axpy")  # always FP64
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="heat2d-1024-radau3", choices=sorted(W.WORKLOADS))
+    ap.add_argument("--precond", default="lower", choices=["diag", "lower", "upper"])
+    ap.add_argument("--vcycle", default=None, choices=["fp64", "fp32", "bf16"])
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------
+# clock sampling during the timed region
+# ----------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id: str | None):
+        self.proc = None
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.device_id = device_id
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.device_id:
+            cmd += ["-i", self.device_id]
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def device_id_for_smi():
+    import torch
+
+    try:
+        u = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0] or None
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2403_08084_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_class: str, workload: str):
+    """DRAM bytes per launch of a kernel class from the committed ncu summary, if it
+    was taken on the current kernel sources; else None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            t = json.load(f)
+    except Exception:
+        return None
+    if t.get("source_sha") != source_hash():
+        return None
+    e = t.get("classes", {}).get(kernel_class)
+    if not e:
+        return None
+    return e.get("bytes_per_launch_full_size")
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+def make_solver(wl, precond, vcycle):
+    from paper_2403_08084_gb300 import Solver
+    from paper_2403_08084_gb300 import tableaux as PT
+
+    tab = PT.by_name(wl.tableau, wl.s)
+    kap = W.lognormal_kappa(wl.dim, wl.N, 0.5, wl.kappa_seed) if wl.kappa_seed is not None else None
+    sv = Solver(wl.N, tab, wl.dt, kappa=kap, levels=wl.levels, precond=precond, vcycle=vcycle, rtol=wl.rtol)
+    return sv, tab
+
+
+def run_steps(sv, tab, wl, u, f, n0, count, record=None):
+    stats = []
+    for n in range(n0, n0 + count):
+        t = n * wl.dt
+        coef = [W.sine_load_time(wl.dim, t + c * wl.dt) for c in tab.c]
+        stats.append(sv.step(u, u, f_space=f, f_coef=coef))
+        if record is not None:
+            record.append(u.clone())
+    return stats
+
+
+def gpu_arm(args, rank, world):
+    import torch
+
+    wl = W.WORKLOADS[args.workload]
+    vcycle = args.vcycle or wl.vcycle
+    if vcycle == "exact":
+        vcycle = "fp64"
+    precond = args.precond
+    dist = world > 1
+    if dist:
+        import torch.distributed as td
+    sv, tab = make_solver(wl, precond, vcycle)
+    nn = (wl.N + 1) ** wl.dim
+    u0 = torch.from_numpy(W.sine_initial(wl.dim, wl.N)).cuda()
+    f = torch.from_numpy(W.sine_load_space(wl.dim, wl.N)).cuda()
+    u = u0.clone()
+    stream = torch.cuda.current_stream()
+
+    # warm-up, then one instrumented step to find the kernel class that dominates device time
+    run_steps(sv, tab, wl, u, f, 0, args.warmup)
+    sv.perf_select([c for c in ("stage_apply", "jacobi", "residual", "restrict", "prolong", "coarse", "multidot",
+                                "axpy", "block_rhs")])
+    u.copy_(u0)
+    run_steps(sv, tab, wl, u, f, 0, 1)
+    prof = sv.perf_read()["classes"]
+    dominant = max(prof, key=lambda k: prof[k]["timed_ms"] if k != "other" else -1)
+    shares = {k: round(v["timed_ms"], 4) for k, v in prof.items() if v["timed_ms"] > 0}
+
+    # timed region: the workload's first K steps from t = 0
+    u.copy_(u0)
+    sv.perf_select([dominant])
+    clocks = Clocks(device_id_for_smi()) if rank == 0 else None
+    snaps = []
+    if dist:
+        td.barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = run_steps(sv, tab, wl, u, f, 0, args.steps, record=None)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        td.all_reduce(t, op=td.ReduceOp.MAX)
+        td.barrier()
+        ms = float(t.item())
+    perf = sv.perf_read()
+    u_final = u.clone()
+    # state after the first 5 steps, for the variants' agreement check
+    u5 = u0.clone()
+    run_steps(sv, tab, wl, u5, f, 0, min(5, args.steps))
+
+    steps_per_s = world * args.steps / (ms / 1e3)
+    s = wl.s
+    dof = (wl.N + 1) ** wl.dim
+    its = [st["fgmres_its"] for st in stats]
+    cls = perf["classes"][dominant]
+    hbm, hbm_src = peaks()
+    roof = None
+    if cls["timed_launches"] > 0 and cls["timed_ms"] > 0:
+        avg_s = cls["timed_ms"] / cls["timed_launches"] / 1e3
+        bpl = cls["timed_bytes"] / cls["timed_launches"]
+        fpl = cls["timed_flops"] / cls["timed_launches"]
+        gbs = bpl / avg_s / 1e9
+        tfl = fpl / avg_s / 1e12
+        fp64_kernel = dominant in FP64_CLASSES or vcycle == "fp64"
+        if fp64_kernel:
+            roof = {"bound": "alu", "achieved": round(tfl, 4), "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
+                    "frac": round(tfl / FP64_PEAK_TFLOPS, 4),
+                    "peak_source": "FP64 FMA: 152 SMs x 2/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)"}
+        else:
+            roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(gbs / hbm, 4),
+                    "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)"}
+        roof.update({"kernel": dominant, "traffic": ncu_traffic(dominant, wl.name), "launches": cls["timed_launches"],
+                     "avg_launch_us": round(avg_s * 1e6, 2), "algorithmic_bytes_per_launch": round(bpl),
+                     "algorithmic_flops_per_launch": round(fpl), "achieved_gbs": round(gbs, 1),
+                     "hbm_frac_of_measured": round(gbs / hbm, 4)})
+
+    out = {
+        "metric": METRIC,
+        "value": round(steps_per_s, 4),
+        "unit": "time-steps/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms / args.steps, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64" if vcycle == "fp64" else f"f64 outer / {vcycle} V-cycles",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "mesh": f"{wl.N}x{wl.N} Q1", "dofs": dof, "stages": s,
+                   "tableau": f"{wl.tableau}({s})", "dt": wl.dt, "kappa": "lognormal sigma=0.5 seed %s" % wl.kappa_seed,
+                   "precond": precond, "vcycle": vcycle, "levels": wl.levels, "rtol": wl.rtol,
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                   "l2_policy": "working set > L2: Krylov basis of ~its x 25 MB stage vectors per step"},
+        "dof_stage_per_s": round(steps_per_s * dof * s, 1),
+        "fgmres_its_per_step": round(sum(its) / len(its), 2),
+        "vcycles_per_step": round(sum(st["vcycles"] for st in stats) / len(stats), 2),
+        "final_rel_resid_max": max(st["rel_resid"] for st in stats),
+        "gpu_launches": perf["launches"],
+        "roofline": roof,
+        "kernel_ms_one_step": shares,
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_e2e:
+        out["e2e"] = e2e_leg(sv, tab, wl, u0, args)
+    sv.close()
+    if rank == 0 and not args.no_variants:
+        out["variants"] = variants_leg(wl, u5.cpu().numpy(), args, vcycle, precond)
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_leg(wl)
+    out["final_u_norm"] = float(torch.linalg.vector_norm(u_final).item())
+    return out
+
+
+def e2e_leg(sv, tab, wl, u0, args):
+    """Same metric through the C ABI with pinned host buffers (copies inside the call)."""
+    import torch
+
+    nn = (wl.N + 1) ** wl.dim
+    uh = u0.cpu().pin_memory()
+    fh = torch.from_numpy(W.sine_load_space(wl.dim, wl.N)).pin_memory()
+    out = torch.empty(nn, dtype=torch.float64).pin_memory()
+    K = max(1, min(args.steps, 10))
+    for n in range(1):  # warm the staging buffers
+        coef = [W.sine_load_time(wl.dim, c * wl.dt) for c in tab.c]
+        sv.step(uh, out, f_space=fh, f_coef=coef)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for n in range(K):
+        coef = [W.sine_load_time(wl.dim, (n + c) * wl.dt) for c in tab.c]
+        sv.step(uh, out, f_space=fh, f_coef=coef)
+        uh, out = out, uh
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"value": round(K / dt, 4), "unit": "time-steps/s", "steps": K, "h2d_bytes_per_step": 2 * nn * 8,
+            "d2h_bytes_per_step": nn * 8, "buffers": "pinned host (torch pin_memory), host pointers to irk_step"}
+
+
+def variants_leg(wl, u5_ref, args, vcycle0, precond0):
+    """Other preconditioner / V-cycle precision pairs on the same workload (5 steps each)."""
+    import torch
+
+    res = {}
+    nsteps = min(5, args.steps)
+    for precond, vcycle in (("diag", "fp64"), ("lower", "fp32"), ("lower", "bf16"), ("diag", "fp32")):
+        if (precond, vcycle) == (precond0, vcycle0):
+            continue
+        sv, tab = make_solver(wl, precond, vcycle)
+        u0 = torch.from_numpy(W.sine_initial(wl.dim, wl.N)).cuda()
+        f = torch.from_numpy(W.sine_load_space(wl.dim, wl.N)).cuda()
+        u = u0.clone()
+        run_steps(sv, tab, wl, u, f, 0, 1)
+        u.copy_(u0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        stats = run_steps(sv, tab, wl, u, f, 0, nsteps)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        un = u.cpu().numpy()
+        res[f"{precond}/{vcycle}"] = {
+            "steps_per_s": round(nsteps / dt, 4), "ms_per_step": round(dt * 1e3 / nsteps, 3),
+            "fgmres_its_per_step": round(sum(s["fgmres_its"] for s in stats) / nsteps, 2),
+            "rel_l2_vs_headline_after_5_steps": float(np.linalg.norm(un - u5_ref) / np.linalg.norm(u5_ref))}
+        sv.close()
+    return res
+
+
+def cpu_baseline_leg(wl):
+    """One time step of the same workload through the oracle's FGMRES + V-cycle restatement."""
+    from oracle import fem, krylov, mg, rk
+    from oracle import tableaux as OT
+
+    kap = W.lognormal_kappa(wl.dim, wl.N, 0.5, wl.kappa_seed) if wl.kappa_seed is not None else None
+    d = fem.Discretisation(wl.dim, wl.N, kap)
+    h = mg.Hierarchy(d, wl.levels)
+    ot = OT.by_name(wl.tableau, wl.s)
+    solves = [mg.VCycle(h, wl.dt * ot.A[i, i]) for i in range(wl.s)]
+    S = rk.kronecker_operator(d.M, d.K, ot.A, wl.dt)
+    P = krylov.BlockPreconditioner("lower", ot.A, d.K, wl.dt, solves)
+    u0 = d.to_interior(W.sine_initial(wl.dim, wl.N))
+    Fs = d.to_interior(W.sine_load_space(wl.dim, wl.N))
+    t0 = time.perf_counter()
+    r = np.stack([W.sine_load_time(wl.dim, c * wl.dt) * Fs for c in ot.c]) - (d.K @ u0)[None, :]
+    k, its, _, _ = krylov.fgmres(lambda v: S @ v, r.reshape(-1), P, rtol=wl.rtol)
+    u1 = u0 + wl.dt * (ot.b @ k.reshape(wl.s, -1))
+    dt = time.perf_counter() - t0
+    return {"value": round(1.0 / dt, 5), "unit": "time-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"1 time step of {wl.name} at full size (oracle FGMRES + sparse V-cycle, P_L, FP64; "
+                      f"{its} its; setup excluded)", "seconds": round(dt, 2), "u_norm": float(np.linalg.norm(u1))}
+
+
+# ----------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle
+# ----------------------------------------------------------------------------
+def reference_arm(args):
+    from oracle import fem, krylov, mg, rk
+    from oracle import tableaux as OT
+
+    wl = W.WORKLOADS[args.workload]
+    # bounded sample: the same workload on a mesh with 1/4 of the nodes (one fewer level), so that
+    # every step is a few seconds of CPU work; throughput is scaled to the full DOF count
+    Ns = max(wl.N // 2, 32)
+    lv = max(1, wl.levels - (1 if Ns < wl.N else 0))
+    kap = W.lognormal_kappa(wl.dim, Ns, 0.5, wl.kappa_seed) if wl.kappa_seed is not None else None
+    d = fem.Discretisation(wl.dim, Ns, kap)
+    h = mg.Hierarchy(d, lv)
+    ot = OT.by_name(wl.tableau, wl.s)
+    solves = [mg.VCycle(h, wl.dt * ot.A[i, i]) for i in range(wl.s)]
+    S = rk.kronecker_operator(d.M, d.K, ot.A, wl.dt)
+    P = krylov.BlockPreconditioner(args.precond, ot.A, d.K, wl.dt, solves)
+    u0 = d.to_interior(W.sine_initial(wl.dim, Ns))
+    Fs = d.to_interior(W.sine_load_space(wl.dim, Ns))
+
+    def one(u, n):
+        r = np.stack([W.sine_load_time(wl.dim, (n + c) * wl.dt) * Fs for c in ot.c]) - (d.K @ u)[None, :]
+        k, its, _, _ = krylov.fgmres(lambda v: S @ v, r.reshape(-1), P, rtol=wl.rtol)
+        return u + wl.dt * (ot.b @ k.reshape(wl.s, -1)), its
+
+    u = u0.copy()
+    for n in range(args.warmup):
+        u, _ = one(u, n)
+    u = u0.copy()
+    t0 = time.perf_counter()
+    its = []
+    for n in range(args.steps):
+        u, it = one(u, n)
+        its.append(it)
+    dt = time.perf_counter() - t0
+    scale = ((Ns + 1) ** wl.dim) / ((wl.N + 1) ** wl.dim)
+    value = args.steps / dt * scale
+    sample = (f"each step: one RK step of {wl.name} on a {Ns}x{Ns} mesh ({lv} levels), oracle FGMRES + sparse "
+              f"V-cycle, P_{args.precond[0].upper()}, FP64; steps/s scaled by the DOF ratio {scale:.4f}")
+    return {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": round(value, 6),
+        "unit": "time-steps/s",
+        "n_gpus": args.gpus,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(dt * 1e3 / args.steps, 2),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "mesh": f"{wl.N}x{wl.N} Q1", "precond": args.precond, "sample_mesh": Ns},
+        "fgmres_its_per_step": round(sum(its) / len(its), 2),
+        "cpu_baseline": {"value": round(value, 6), "unit": "time-steps/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 6), "unit": "time-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        print(json.dumps(reference_arm(args)))
+        return 0
+    import torch
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as td
+
+        td.init_process_group("nccl", device_id=torch.device("cuda", local))
+    out = gpu_arm(args, rank, world)
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as td
+
+        td.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

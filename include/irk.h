@@ -1,0 +1,187 @@
+/*
+ * irk.h -- C ABI of the GB300 stage-coupled implicit Runge-Kutta solver.
+ *
+ * The library advances the Q1 finite-element heat equation
+ *     M u' + K(kappa) u = F(t)          (Kirby & MacLachlan, "Extending Irksome",
+ *                                        Sec. 2, eq. heat / rkheat)
+ * on a uniform mesh of the unit square (dim = 2) with homogeneous Dirichlet
+ * data by one s-stage Runge-Kutta step at a time.  Each step solves the
+ * stage-coupled system of Sec. 3, eq. block_struct_AI,
+ *     (I (x) M + dt A (x) K) k = r,   r_i = F(t_n + c_i dt) - K u_n,
+ * with FP64 flexible GMRES preconditioned by the block-diagonal (P_D, eq.
+ * pcbjac) or block-triangular (P_L, eq. pcbgs; P_U, Sec. 3.1) stage
+ * preconditioner, whose diagonal blocks M + dt a_ii K are each approximated by
+ * one geometric-multigrid V-cycle (Sec. 3.1), then sets
+ *     u_{n+1} = u_n + dt sum_i b_i k_i     (Sec. 2, RK update).
+ *
+ * Data layout (all vectors, device or host):
+ *   * nodes of the full (N+1)^dim grid, x fastest (node id = ix + (N+1) iy);
+ *   * a "nodal" vector holds one double per node;
+ *   * a "stage" vector holds s doubles per node, node-major: v[node*s + i];
+ *   * boundary entries of inputs are ignored (read as 0); boundary entries of
+ *     outputs are written as 0 (homogeneous Dirichlet: by the DAE-type
+ *     conditions of Sec. 2.1 the stage values vanish there);
+ *   * per-cell data (kappa) is N^dim doubles, cells x fastest.
+ *
+ * Pointers: vector arguments may be device pointers or host pointers; the
+ * library asks the CUDA runtime which one it got and, for host memory, copies
+ * through its own device buffers inside the call.  All device work is
+ * enqueued on the stream given to irk_create (NULL = the legacy default
+ * stream).  The caller keeps ownership of every pointer it passes; the handle
+ * owns all scratch memory (Krylov basis, multigrid level vectors).
+ *
+ * Errors: every entry point returns IRK_OK (0) or a negative IRK_E* code and
+ * records a message that irk_last_error() returns (per thread).  No C++
+ * exception crosses this boundary.
+ */
+#ifndef IRK_H
+#define IRK_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IRK_OK 0
+#define IRK_EINVAL (-1)     /* bad argument, tableau, mesh or option */
+#define IRK_ENOMEM (-2)     /* device or host allocation failed */
+#define IRK_ECUDA (-3)      /* a CUDA runtime call failed */
+#define IRK_ENOCONV (-4)    /* FGMRES reached maxit; outputs hold the last iterate */
+#define IRK_ENONFINITE (-5) /* NaN or Inf in the residual */
+
+/* block stage preconditioners (Sec. 3.1) */
+#define IRK_PC_DIAG 0  /* P_D = I (x) M + dt D (x) K          (eq. pcbjac, AI form)   */
+#define IRK_PC_LOWER 1 /* P_L = I (x) M + dt (L + D) (x) K    (eq. pcbgs, AI form)    */
+#define IRK_PC_UPPER 2 /* P_U = I (x) M + dt (U + D) (x) K    (Sec. 3.1)              */
+
+/* storage / arithmetic of the multigrid V-cycles inside the FP64 FGMRES */
+#define IRK_PREC_FP64 0 /* vectors and arithmetic in double                         */
+#define IRK_PREC_FP32 1 /* vectors and arithmetic in float                          */
+#define IRK_PREC_BF16 2 /* vectors stored as bfloat16, arithmetic in float          */
+
+#define IRK_MAX_STAGES 4
+
+typedef struct irk_handle irk_handle;
+
+typedef struct {
+  int dim;             /* 2 */
+  int n_cells;         /* N: cells per axis of the uniform mesh of [0,1]^dim */
+  int levels;          /* multigrid levels >= 1; N divisible by 2^(levels-1), coarsest >= 2 cells */
+  const double* kappa; /* host, N^dim per-cell diffusivities (> 0), or NULL for kappa = 1; copied */
+} irk_mesh;
+
+typedef struct {
+  int s;            /* stages, 1..IRK_MAX_STAGES */
+  const double* A;  /* host, s*s row-major Butcher matrix; copied */
+  const double* b;  /* host, s weights; copied */
+  const double* c;  /* host, s abscissae; copied */
+} irk_tableau;
+
+typedef struct {
+  int precond;      /* IRK_PC_* */
+  int vcycle_prec;  /* IRK_PREC_* */
+  int nu_pre;       /* weighted-Jacobi pre-smoothing sweeps per level (default 2) */
+  int nu_post;      /* post-smoothing sweeps per level (default 2) */
+  double omega;     /* Jacobi weight (default 2/3) */
+  double rtol;      /* stop when ||r_j||_2 <= rtol ||r_0||_2 (default 1e-10) */
+  int restart;      /* FGMRES restart length m (default 50) */
+  int maxit;        /* total FGMRES iterations allowed per solve (default 500) */
+} irk_options;
+
+typedef struct {
+  int fgmres_its;   /* Arnoldi steps (= preconditioner applications) of the last solve */
+  int vcycles;      /* single-block V-cycles applied in the last solve */
+  double rel_resid; /* final ||r||_2 / ||r_0||_2 estimate of the last solve */
+  int converged;    /* 1 if rel_resid <= rtol */
+} irk_stats;
+
+/* Fill *opt with the defaults listed above (P_L, FP64 V-cycles). */
+void irk_default_options(irk_options* opt);
+
+/* Build a solver for one mesh, tableau and step size (Sec. 3, eq. block_struct_AI).
+ * Validates the tableau (finite entries; row sums of A equal c to 1e-6, which
+ * also rejects a transposed A), builds the Galerkin multigrid hierarchy of M and K(kappa) on the host, factors the
+ * coarsest blocks, uploads everything and allocates the Krylov basis.
+ * stream: a cudaStream_t (NULL = legacy default stream).  *out is set on success. */
+int irk_create(irk_handle** out, const irk_mesh* mesh, const irk_tableau* tab, double dt,
+               const irk_options* opt, void* stream);
+
+/* Release every resource of the handle (NULL is accepted). */
+int irk_destroy(irk_handle* h);
+
+/* Replace the per-cell diffusivity (host, N^dim doubles) and rebuild the
+ * operators, the hierarchy and the coarse factors; the step size is kept. */
+int irk_set_kappa(irk_handle* h, const double* kappa_host);
+
+/* One RK step (Sec. 2): solve for the stages k and set
+ * u_np1 = u_n + dt sum_i b_i k_i.
+ *   u_n        nodal, input.
+ *   f_space    nodal, optional (NULL = 0): spatial load vector F^ (integrals of f against the hats).
+ *   f_coef     host, s doubles, optional (NULL = all 1): F_i += f_coef[i] * F^.
+ *   f_stages   stage vector, optional (NULL = 0): F_i += f_stages[:, i].
+ *   u_np1      nodal, output (may alias u_n).
+ *   stages_out stage vector, optional output of k.
+ *   stats      optional.
+ * Returns IRK_ENOCONV if FGMRES did not reach rtol within maxit (outputs still written). */
+int irk_step(irk_handle* h, const double* u_n, const double* f_space, const double* f_coef,
+             const double* f_stages, double* u_np1, double* stages_out, irk_stats* stats);
+
+/* Solve (I (x) M + dt A (x) K) k = r for a given stage vector r (no RK update). */
+int irk_solve(irk_handle* h, const double* r, double* k, irk_stats* stats);
+
+/* y = (I (x) M + dt A (x) K) x for stage vectors (transpose != 0: A^T instead of A). */
+int irk_apply_operator(irk_handle* h, const double* x, double* y, int transpose);
+
+/* z = P^{-1} v: one application of the configured block preconditioner, each
+ * block approximated by one V-cycle (transpose != 0: the transposed
+ * preconditioner P^T, used by the adjoint). */
+int irk_apply_preconditioner(irk_handle* h, const double* v, double* z, int transpose);
+
+/* Discrete adjoint of irk_step (not in the paper).  With S = I (x) M + dt A (x) K:
+ *   solve S^T mu = dt (b (x) lam_np1) by FGMRES with the transposed preconditioner,
+ *   lam_n = lam_np1 - K sum_i mu_i,
+ *   grad[c] += -kappa_c sum_i mu_i|_c^T K_e U_i|_c,  U_i = u_n + dt sum_j a_ij k_j,
+ * where K_e is the unit-diffusivity element matrix, so grad accumulates dJ/d(log kappa).
+ *   u_n, stages   the forward step's input state and stages (nodal / stage vectors).
+ *   lam_np1       nodal adjoint state after the step (input); lam_n nodal output (may alias).
+ *   grad_accum    per-cell, N^dim doubles, accumulated (+=); may be NULL. */
+int irk_step_adjoint(irk_handle* h, const double* u_n, const double* stages, const double* lam_np1,
+                     double* lam_n, double* grad_accum, irk_stats* stats);
+
+/* Kernel classes counted by the built-in instrumentation. */
+#define IRK_K_STAGE_APPLY 0 /* stage operator (FP64)                        */
+#define IRK_K_JACOBI 1      /* weighted-Jacobi sweep                         */
+#define IRK_K_RESIDUAL 2    /* multigrid residual                            */
+#define IRK_K_RESTRICT 3    /* full-weighting restriction                    */
+#define IRK_K_PROLONG 4     /* bilinear prolongation + correction            */
+#define IRK_K_COARSE 5      /* coarsest-level dense solve                    */
+#define IRK_K_MULTIDOT 6    /* Arnoldi multi-dot partial sums                */
+#define IRK_K_AXPY 7        /* Arnoldi / solution multi-axpy                 */
+#define IRK_K_BLOCK_RHS 8   /* triangular-preconditioner block right side    */
+#define IRK_K_OTHER 9       /* reductions, scaling, Givens, casts, RHS, update */
+#define IRK_K_COUNT 10
+
+typedef struct {
+  long long launches;                   /* kernels launched since the last irk_perf_select */
+  long long class_launches[IRK_K_COUNT];
+  double class_bytes[IRK_K_COUNT];      /* algorithmic DRAM bytes (each operand moved once) */
+  double class_flops[IRK_K_COUNT];      /* algorithmic floating-point operations */
+  long long timed_launches[IRK_K_COUNT];/* launches bracketed by CUDA events */
+  double timed_ms[IRK_K_COUNT];         /* their summed device time */
+  double timed_bytes[IRK_K_COUNT];
+  double timed_flops[IRK_K_COUNT];
+} irk_perf;
+
+/* Reset the counters; time every launch of the classes in class_mask (bit k =
+ * IRK_K_k) with a pair of CUDA events on the handle's stream (0 = no timing). */
+int irk_perf_select(irk_handle* h, unsigned class_mask);
+
+/* Copy the counters (synchronises the handle's stream to read the events). */
+int irk_perf_read(irk_handle* h, irk_perf* out);
+
+/* The message recorded by the last failing call on this thread ("" if none). */
+const char* irk_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IRK_H */

@@ -1,0 +1,941 @@
+// C-ABI entry points and the host-side orchestration of one RK step:
+// right-hand side, FP64 flexible GMRES with the block stage preconditioners of
+// Sec. 3.1 (each diagonal block approximated by one geometric-multigrid V-cycle),
+// and the RK update of Sec. 2.  See include/irk.h for the contract.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/irk.h"
+#include "common.cuh"
+#include "hierarchy.h"
+#include "kernels.h"
+
+using namespace irk;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CK(call)                                                                               \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) return fail(IRK_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+#define CK_LAUNCH()                                                                                  \
+  do {                                                                                               \
+    cudaError_t e_ = cudaGetLastError();                                                             \
+    if (e_ != cudaSuccess) return fail(IRK_ECUDA, "kernel launch failed: %s", cudaGetErrorString(e_)); \
+  } while (0)
+
+#define TRY(x)          \
+  do {                  \
+    int r_ = (x);       \
+    if (r_ != IRK_OK) return r_; \
+  } while (0)
+
+size_t prec_bytes(int prec) { return prec == IRK_PREC_FP64 ? 8 : (prec == IRK_PREC_FP32 ? 4 : 2); }
+
+struct Level {
+  int N = 0, nx = 0;
+  size_t nn = 0;
+  double hm = 0.0;  // h^2 / 36
+  std::vector<double> cf_host;
+  double* cf_d = nullptr;     // stencil records, double
+  float* cf_f = nullptr;      // stencil records, float
+  double* dinv_d = nullptr;   // omega / diag, s per node
+  float* dinv_f = nullptr;
+  void* xa = nullptr;         // V-cycle vectors (s per node, V-cycle precision)
+  void* xb = nullptr;
+  void* b = nullptr;
+  void* r = nullptr;
+};
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct irk_handle {
+  int dim = 2, N = 0, s = 0, L = 0;
+  double dt = 0.0;
+  irk_options opt{};
+  cudaStream_t st = nullptr;
+  std::vector<double> A, b, c, kappa;
+  std::vector<Level> lev;
+  // coarsest-level exact solve
+  int nint = 0;
+  int* cmap = nullptr;
+  double* binv_d = nullptr;
+  float* binv_f = nullptr;
+  double* kappa_d = nullptr;
+  // Krylov space
+  size_t ne = 0;  // entries of a stage vector
+  int m = 0;
+  double* V = nullptr;
+  double* Z = nullptr;
+  double *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr;
+  double *h1 = nullptr, *h2 = nullptr, *partial = nullptr, *scal = nullptr;
+  double* pinned = nullptr;  // host-visible copies of the residual estimate
+  double *rhs = nullptr, *k = nullptr, *tmp = nullptr;
+  DevBuf stage_bufs[8];
+  int vcycles = 0;
+  // instrumentation
+  irk_perf perf{};
+  unsigned perf_mask = 0;
+  std::vector<cudaEvent_t> ev;  // start/stop pairs
+  std::vector<int> ev_cls;
+  size_t ev_used = 0;
+};
+
+namespace {
+
+// ----------------------------------------------------------------------------
+// memory helpers
+// ----------------------------------------------------------------------------
+template <typename P>
+int dalloc(P** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc((void**)p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(IRK_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+  }
+  return IRK_OK;
+}
+
+template <typename P>
+void dfree(P*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+bool is_device_ptr(const void* p) {
+  if (p == nullptr) return false;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Device view of a caller input: the pointer itself if it is device memory,
+// else a copy in staging slot `slot` (enqueued on the handle's stream).
+int dev_in(irk_handle* h, const void* p, size_t bytes, int slot, const void** out) {
+  if (p == nullptr || is_device_ptr(p)) {
+    *out = p;
+    return IRK_OK;
+  }
+  DevBuf& b = h->stage_bufs[slot];
+  if (b.bytes < bytes) {
+    dfree(b.p);
+    b.bytes = 0;
+    TRY(dalloc(&b.p, bytes));
+    b.bytes = bytes;
+  }
+  CK(cudaMemcpyAsync(b.p, p, bytes, cudaMemcpyHostToDevice, h->st));
+  *out = b.p;
+  return IRK_OK;
+}
+
+// Device destination for a caller output; *host is set when the result must be
+// copied back to the caller's host memory with dev_out_finish.
+int dev_out(irk_handle* h, void* p, size_t bytes, int slot, void** out, bool* host) {
+  *host = false;
+  if (p == nullptr || is_device_ptr(p)) {
+    *out = p;
+    return IRK_OK;
+  }
+  DevBuf& b = h->stage_bufs[slot];
+  if (b.bytes < bytes) {
+    dfree(b.p);
+    b.bytes = 0;
+    TRY(dalloc(&b.p, bytes));
+    b.bytes = bytes;
+  }
+  *out = b.p;
+  *host = true;
+  return IRK_OK;
+}
+
+int dev_out_finish(irk_handle* h, void* host_ptr, const void* dev, size_t bytes) {
+  CK(cudaMemcpyAsync(host_ptr, dev, bytes, cudaMemcpyDeviceToHost, h->st));
+  return IRK_OK;
+}
+
+// ----------------------------------------------------------------------------
+// instrumentation: launch counts, algorithmic bytes / flops, optional event timing
+// ----------------------------------------------------------------------------
+void perf_drain(irk_handle* h, bool accumulate) {
+  if (h->ev_used == 0) return;
+  cudaStreamSynchronize(h->st);
+  for (size_t i = 0; i < h->ev_used; ++i) {
+    float ms = 0.f;
+    if (accumulate && cudaEventElapsedTime(&ms, h->ev[2 * i], h->ev[2 * i + 1]) == cudaSuccess)
+      h->perf.timed_ms[h->ev_cls[i]] += ms;
+  }
+  cudaGetLastError();
+  h->ev_used = 0;
+}
+
+int perf_slot(irk_handle* h, int cls) {
+  constexpr size_t kMaxPairs = 8192;
+  if (h->ev_used == h->ev.size() / 2) {
+    if (h->ev.size() / 2 >= kMaxPairs) {
+      perf_drain(h, true);
+    } else {
+      cudaEvent_t a, b;
+      if (cudaEventCreate(&a) != cudaSuccess) return -1;
+      if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return -1;
+      }
+      h->ev.push_back(a);
+      h->ev.push_back(b);
+      h->ev_cls.push_back(0);
+    }
+  }
+  const size_t i = h->ev_used++;
+  h->ev_cls[i] = cls;
+  return (int)i;
+}
+
+// Counts one kernel launch of class `cls`; brackets it with events when selected.
+struct KScope {
+  irk_handle* h;
+  int slot = -1;
+  KScope(irk_handle* hh, int cls, double bytes, double flops) : h(hh) {
+    h->perf.launches++;
+    h->perf.class_launches[cls]++;
+    h->perf.class_bytes[cls] += bytes;
+    h->perf.class_flops[cls] += flops;
+    if (h->perf_mask & (1u << cls)) {
+      slot = perf_slot(h, cls);
+      if (slot >= 0) {
+        h->perf.timed_launches[cls]++;
+        h->perf.timed_bytes[cls] += bytes;
+        h->perf.timed_flops[cls] += flops;
+        cudaEventRecord(h->ev[2 * slot], h->st);
+      }
+    }
+  }
+  ~KScope() {
+    if (slot >= 0) cudaEventRecord(h->ev[2 * slot + 1], h->st);
+  }
+};
+
+inline double n_int(int nx) { return (double)(nx - 2) * (double)(nx - 2); }
+
+// ----------------------------------------------------------------------------
+// setup
+// ----------------------------------------------------------------------------
+int validate(const irk_mesh* mesh, const irk_tableau* tab, double dt, const irk_options* opt) {
+  if (!mesh || !tab || !opt) return fail(IRK_EINVAL, "null mesh, tableau or options");
+  if (mesh->dim != 2) return fail(IRK_EINVAL, "dim = %d: this build supports dim = 2", mesh->dim);
+  const int N = mesh->n_cells, L = mesh->levels;
+  if (N < 2 || N > 16384) return fail(IRK_EINVAL, "n_cells = %d out of range [2, 16384]", N);
+  if (L < 1 || L > 14) return fail(IRK_EINVAL, "levels = %d out of range [1, 14]", L);
+  const int div = 1 << (L - 1);
+  if (N % div != 0) return fail(IRK_EINVAL, "n_cells = %d not divisible by 2^(levels-1) = %d", N, div);
+  const int Nc = N / div;
+  if (Nc < 2) return fail(IRK_EINVAL, "coarsest level has %d cells per axis (< 2)", Nc);
+  if (Nc > 64) return fail(IRK_EINVAL, "coarsest level has %d cells per axis (> 64): add levels", Nc);
+  if (mesh->kappa) {
+    const size_t nc = (size_t)N * N;
+    for (size_t i = 0; i < nc; ++i)
+      if (!(mesh->kappa[i] > 0.0) || !std::isfinite(mesh->kappa[i]))
+        return fail(IRK_EINVAL, "kappa[%zu] = %g is not positive and finite", i, mesh->kappa[i]);
+  }
+  const int s = tab->s;
+  if (s < 1 || s > IRK_MAX_STAGES) return fail(IRK_EINVAL, "s = %d out of range [1, %d]", s, IRK_MAX_STAGES);
+  if (!tab->A || !tab->b || !tab->c) return fail(IRK_EINVAL, "null tableau array");
+  double bsum = 0.0;
+  for (int i = 0; i < s; ++i) {
+    double row = 0.0;
+    for (int j = 0; j < s; ++j) {
+      const double a = tab->A[i * s + j];
+      if (!std::isfinite(a)) return fail(IRK_EINVAL, "A[%d][%d] is not finite", i, j);
+      row += a;
+    }
+    if (!std::isfinite(tab->b[i]) || !std::isfinite(tab->c[i])) return fail(IRK_EINVAL, "b or c not finite");
+    if (std::fabs(row - tab->c[i]) > 1e-6)
+      return fail(IRK_EINVAL, "row %d of A sums to %.17g but c[%d] = %.17g (transposed A?)", i, row, i, tab->c[i]);
+    bsum += tab->b[i];
+  }
+  if (std::fabs(bsum - 1.0) > 1e-6) return fail(IRK_EINVAL, "sum(b) = %.17g != 1", bsum);
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(IRK_EINVAL, "dt = %g must be positive", dt);
+  if (opt->precond < IRK_PC_DIAG || opt->precond > IRK_PC_UPPER) return fail(IRK_EINVAL, "bad precond %d", opt->precond);
+  if (opt->vcycle_prec < IRK_PREC_FP64 || opt->vcycle_prec > IRK_PREC_BF16)
+    return fail(IRK_EINVAL, "bad vcycle_prec %d", opt->vcycle_prec);
+  if (opt->nu_pre < 1 || opt->nu_post < 1 || opt->nu_pre > 16 || opt->nu_post > 16)
+    return fail(IRK_EINVAL, "nu_pre / nu_post must be in [1, 16]");
+  if (!(opt->omega > 0.0 && opt->omega < 2.0)) return fail(IRK_EINVAL, "omega = %g not in (0, 2)", opt->omega);
+  if (!(opt->rtol > 0.0 && opt->rtol < 1.0)) return fail(IRK_EINVAL, "rtol = %g not in (0, 1)", opt->rtol);
+  if (opt->restart < 1 || opt->restart > 100) return fail(IRK_EINVAL, "restart = %d not in [1, 100]", opt->restart);
+  if (opt->maxit < 1) return fail(IRK_EINVAL, "maxit = %d < 1", opt->maxit);
+  return IRK_OK;
+}
+
+// Build the hierarchy's host data and upload it (also used by irk_set_kappa).
+int build_operators(irk_handle* h) {
+  const int s = h->s;
+  std::vector<double> sigma(s);
+  for (int i = 0; i < s; ++i) sigma[i] = h->dt * h->A[i * s + i];
+  for (int l = 0; l < h->L; ++l) {
+    Level& Lv = h->lev[l];
+    if (l == 0)
+      stiffness_records_2d(Lv.N, h->kappa.empty() ? nullptr : h->kappa.data(), Lv.cf_host);
+    else
+      galerkin_coarsen_2d(h->lev[l - 1].N, h->lev[l - 1].cf_host, Lv.cf_host);
+    std::vector<double> dinv;
+    jacobi_inverse_diag_2d(Lv.N, Lv.cf_host, Lv.hm, sigma.data(), s, h->opt.omega, dinv);
+    std::vector<float> cff(Lv.cf_host.begin(), Lv.cf_host.end()), dinvf(dinv.begin(), dinv.end());
+    CK(cudaMemcpyAsync(Lv.cf_d, Lv.cf_host.data(), Lv.cf_host.size() * 8, cudaMemcpyHostToDevice, h->st));
+    CK(cudaMemcpyAsync(Lv.dinv_d, dinv.data(), dinv.size() * 8, cudaMemcpyHostToDevice, h->st));
+    CK(cudaMemcpyAsync(Lv.cf_f, cff.data(), cff.size() * 4, cudaMemcpyHostToDevice, h->st));
+    CK(cudaMemcpyAsync(Lv.dinv_f, dinvf.data(), dinvf.size() * 4, cudaMemcpyHostToDevice, h->st));
+    CK(cudaStreamSynchronize(h->st));  // host vectors above go out of scope
+  }
+  // exact coarsest solve: dense inverse of each diagonal block
+  Level& Lc = h->lev[h->L - 1];
+  std::vector<int> map;
+  interior_nodes_2d(Lc.N, map);
+  const int nint = (int)map.size();
+  std::vector<double> all((size_t)s * nint * nint), inv;
+  for (int i = 0; i < s; ++i) {
+    if (!dense_block_inverse_2d(Lc.N, Lc.cf_host, Lc.hm, sigma[i], map, inv))
+      return fail(IRK_EINVAL, "coarsest block %d (sigma = %g) is singular", i, sigma[i]);
+    std::copy(inv.begin(), inv.end(), all.begin() + (size_t)i * nint * nint);
+  }
+  std::vector<float> allf(all.begin(), all.end());
+  CK(cudaMemcpyAsync(h->cmap, map.data(), map.size() * sizeof(int), cudaMemcpyHostToDevice, h->st));
+  CK(cudaMemcpyAsync(h->binv_d, all.data(), all.size() * 8, cudaMemcpyHostToDevice, h->st));
+  CK(cudaMemcpyAsync(h->binv_f, allf.data(), allf.size() * 4, cudaMemcpyHostToDevice, h->st));
+  if (!h->kappa.empty())
+    CK(cudaMemcpyAsync(h->kappa_d, h->kappa.data(), h->kappa.size() * 8, cudaMemcpyHostToDevice, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return IRK_OK;
+}
+
+void destroy(irk_handle* h) {
+  if (!h) return;
+  for (Level& Lv : h->lev) {
+    dfree(Lv.cf_d), dfree(Lv.cf_f), dfree(Lv.dinv_d), dfree(Lv.dinv_f);
+    dfree(Lv.xa), dfree(Lv.xb), dfree(Lv.b), dfree(Lv.r);
+  }
+  dfree(h->cmap), dfree(h->binv_d), dfree(h->binv_f), dfree(h->kappa_d);
+  dfree(h->V), dfree(h->Z), dfree(h->H), dfree(h->cs), dfree(h->sn), dfree(h->g), dfree(h->y);
+  dfree(h->h1), dfree(h->h2), dfree(h->partial), dfree(h->scal);
+  dfree(h->rhs), dfree(h->k), dfree(h->tmp);
+  for (DevBuf& b : h->stage_bufs) dfree(b.p);
+  for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+  if (h->pinned) cudaFreeHost(h->pinned);
+  delete h;
+}
+
+int create(irk_handle** out, const irk_mesh* mesh, const irk_tableau* tab, double dt, const irk_options* opt,
+           void* stream) {
+  if (!out) return fail(IRK_EINVAL, "null output handle pointer");
+  *out = nullptr;
+  TRY(validate(mesh, tab, dt, opt));
+  irk_handle* h = new irk_handle();
+  h->N = mesh->n_cells;
+  h->L = mesh->levels;
+  h->s = tab->s;
+  h->dt = dt;
+  h->opt = *opt;
+  h->st = (cudaStream_t)stream;
+  const int s = h->s;
+  h->A.assign(tab->A, tab->A + s * s);
+  h->b.assign(tab->b, tab->b + s);
+  h->c.assign(tab->c, tab->c + s);
+  if (mesh->kappa) h->kappa.assign(mesh->kappa, mesh->kappa + (size_t)h->N * h->N);
+  auto bail = [&](int code) {
+    destroy(h);
+    return code;
+  };
+  const size_t vb = prec_bytes(opt->vcycle_prec);
+  h->lev.resize(h->L);
+  for (int l = 0; l < h->L; ++l) {
+    Level& Lv = h->lev[l];
+    Lv.N = h->N >> l;
+    Lv.nx = Lv.N + 1;
+    Lv.nn = (size_t)Lv.nx * Lv.nx;
+    const double hh = 1.0 / Lv.N;
+    Lv.hm = hh * hh / 36.0;
+    int r = IRK_OK;
+    if ((r = dalloc(&Lv.cf_d, Lv.nn * kCoef2 * 8)) || (r = dalloc(&Lv.cf_f, Lv.nn * kCoef2 * 4)) ||
+        (r = dalloc(&Lv.dinv_d, Lv.nn * s * 8)) || (r = dalloc(&Lv.dinv_f, Lv.nn * s * 4)) ||
+        (r = dalloc(&Lv.xa, Lv.nn * s * vb)) || (r = dalloc(&Lv.xb, Lv.nn * s * vb)) ||
+        (r = dalloc(&Lv.b, Lv.nn * s * vb)) || (r = dalloc(&Lv.r, Lv.nn * s * vb)))
+      return bail(r);
+    // boundary entries of every level vector stay zero for the handle's lifetime
+    if (cudaMemsetAsync(Lv.xa, 0, Lv.nn * s * vb, h->st) || cudaMemsetAsync(Lv.xb, 0, Lv.nn * s * vb, h->st) ||
+        cudaMemsetAsync(Lv.b, 0, Lv.nn * s * vb, h->st) || cudaMemsetAsync(Lv.r, 0, Lv.nn * s * vb, h->st))
+      return bail(fail(IRK_ECUDA, "cudaMemsetAsync failed"));
+  }
+  const int Nc = h->lev[h->L - 1].N;
+  h->nint = (Nc - 1) * (Nc - 1);
+  int r = IRK_OK;
+  if ((r = dalloc(&h->cmap, (size_t)h->nint * sizeof(int))) ||
+      (r = dalloc(&h->binv_d, (size_t)s * h->nint * h->nint * 8)) ||
+      (r = dalloc(&h->binv_f, (size_t)s * h->nint * h->nint * 4)) ||
+      (r = dalloc(&h->kappa_d, (size_t)h->N * h->N * 8)))
+    return bail(r);
+  h->ne = h->lev[0].nn * s;
+  h->m = opt->restart;
+  const size_t ne = h->ne, m = h->m;
+  if ((r = dalloc(&h->V, (m + 1) * ne * 8)) || (r = dalloc(&h->Z, m * ne * 8)) ||
+      (r = dalloc(&h->H, (m + 1) * m * 8)) || (r = dalloc(&h->cs, m * 8)) || (r = dalloc(&h->sn, m * 8)) ||
+      (r = dalloc(&h->g, (m + 1) * 8)) || (r = dalloc(&h->y, m * 8)) || (r = dalloc(&h->h1, (m + 1) * 8)) ||
+      (r = dalloc(&h->h2, (m + 1) * 8)) ||
+      (r = dalloc(&h->partial, (m + 1) * (size_t)krylov_partial_blocks() * 8)) || (r = dalloc(&h->scal, 16 * 8)) ||
+      (r = dalloc(&h->rhs, ne * 8)) || (r = dalloc(&h->k, ne * 8)) || (r = dalloc(&h->tmp, ne * 8)))
+    return bail(r);
+  if (cudaMemsetAsync(h->V, 0, (m + 1) * ne * 8, h->st) || cudaMemsetAsync(h->Z, 0, m * ne * 8, h->st) ||
+      cudaMemsetAsync(h->H, 0, (m + 1) * m * 8, h->st))
+    return bail(fail(IRK_ECUDA, "cudaMemsetAsync failed"));
+  if (cudaMallocHost((void**)&h->pinned, 8 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(fail(IRK_ENOMEM, "cudaMallocHost failed"));
+  }
+  if ((r = build_operators(h)) != IRK_OK) return bail(r);
+  *out = h;
+  return IRK_OK;
+}
+
+// ----------------------------------------------------------------------------
+// V-cycle (one per block, or S blocks batched over interleaved stages)
+// ----------------------------------------------------------------------------
+template <typename T, typename C>
+struct Prec;
+template <>
+struct Prec<double, double> {
+  static const double* cf(const Level& L) { return L.cf_d; }
+  static const double* dinv(const Level& L) { return L.dinv_d; }
+  static const double* binv(const irk_handle* h) { return h->binv_d; }
+};
+template <>
+struct Prec<float, float> {
+  static const float* cf(const Level& L) { return L.cf_f; }
+  static const float* dinv(const Level& L) { return L.dinv_f; }
+  static const float* binv(const irk_handle* h) { return h->binv_f; }
+};
+template <>
+struct Prec<__nv_bfloat16, float> {
+  static const float* cf(const Level& L) { return L.cf_f; }
+  static const float* dinv(const Level& L) { return L.dinv_f; }
+  static const float* binv(const irk_handle* h) { return h->binv_f; }
+};
+
+// x0 = V(b0) for blocks st0 .. st0+S-1 (S == s: all blocks batched; S == 1: block st0).
+// b0 and x0 are S-interleaved level-0 vectors of precision T; x0 may be nullptr, in
+// which case the result is left in an internal buffer that is returned.
+template <typename T, typename C>
+T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2) {
+  using MG = MG2<T, C>;
+  using P = Prec<T, C>;
+  const int s = h->s, L = h->L;
+  const double p = sizeof(T), c = sizeof(C);
+  Vec8 sig{};
+  for (int i = 0; i < S; ++i) sig.v[i] = h->dt * h->A[(st0 + i) * s + (st0 + i)];
+  cudaStream_t st = h->st;
+  const T* bl = b0;
+  std::vector<T*> cur(L, nullptr);
+  auto sweep = [&](Level& Lv, const C* cf, const C* dinv, const T* xin, const T* b, T* xout) {
+    const double n = n_int(Lv.nx);
+    if (xin == nullptr) {
+      KScope k(h, IRK_K_JACOBI, n * S * (2 * p + c), n * S);
+      MG::jacobi(S, st, Lv.nx, cf, Lv.hm, sig, dinv, s, xin, b, xout);
+    } else {
+      KScope k(h, IRK_K_JACOBI, n * (S * (3 * p + c) + kCoef2 * c), 33.0 * n * S);
+      MG::jacobi(S, st, Lv.nx, cf, Lv.hm, sig, dinv, s, xin, b, xout);
+    }
+  };
+  for (int l = 0; l < L - 1; ++l) {
+    Level& Lv = h->lev[l];
+    Level& Lc = h->lev[l + 1];
+    const C* cf = P::cf(Lv);
+    const C* dinv = P::dinv(Lv) + st0;
+    // choose the two buffers so that the last of the nu1 + nu2 sweeps lands in `last`
+    T* last = (l == 0 && x0) ? x0 : (T*)Lv.xa;
+    T* other = (l == 0 && x0) ? (T*)Lv.xa : (T*)Lv.xb;
+    T* bufs[2];
+    if ((nu1 + nu2) % 2 == 1) {
+      bufs[0] = last, bufs[1] = other;
+    } else {
+      bufs[0] = other, bufs[1] = last;
+    }
+    int w = 0;
+    sweep(Lv, cf, dinv, nullptr, bl, bufs[w]);
+    for (int k = 1; k < nu1; ++k, w ^= 1) sweep(Lv, cf, dinv, bufs[w], bl, bufs[w ^ 1]);
+    cur[l] = bufs[w];
+    const double nf = n_int(Lv.nx), nc = n_int(Lc.nx);
+    {
+      KScope k(h, IRK_K_RESIDUAL, nf * (3 * S * p + kCoef2 * c), 31.0 * nf * S);
+      MG::residual(S, st, Lv.nx, cf, Lv.hm, sig, cur[l], bl, (T*)Lv.r);
+    }
+    {
+      KScope k(h, IRK_K_RESTRICT, (nf + nc) * S * p, 12.0 * nc * S);
+      MG::restrict_(S, st, Lv.nx, (const T*)Lv.r, Lc.nx, (T*)Lc.b);
+    }
+    bl = (const T*)Lc.b;
+  }
+  {  // coarsest level: exact solve
+    Level& Lc = h->lev[L - 1];
+    T* xc = (L == 1 && x0) ? x0 : (T*)Lc.xa;
+    const C* binv = P::binv(h) + (size_t)st0 * h->nint * h->nint;
+    const double ni = h->nint;
+    KScope k(h, IRK_K_COARSE, S * ni * ni * c + 2 * S * ni * p, 2.0 * S * ni * ni);
+    MG::coarse_solve(S, st, h->nint, binv, h->cmap, bl, xc);
+    cur[L - 1] = xc;
+  }
+  for (int l = L - 2; l >= 0; --l) {
+    Level& Lv = h->lev[l];
+    Level& Lc = h->lev[l + 1];
+    const C* cf = P::cf(Lv);
+    const C* dinv = P::dinv(Lv) + st0;
+    const T* bfine = (l == 0) ? b0 : (const T*)Lv.b;
+    const double nf = n_int(Lv.nx), nc = n_int(Lc.nx);
+    {
+      KScope k(h, IRK_K_PROLONG, (nc + 2 * nf) * S * p, 5.0 * nf * S);
+      MG::prolong_add(S, st, Lc.nx, cur[l + 1], Lv.nx, cur[l]);
+    }
+    T* last = (l == 0 && x0) ? x0 : (T*)Lv.xa;
+    T* other = (l == 0 && x0) ? (T*)Lv.xa : (T*)Lv.xb;
+    T* a = cur[l];
+    T* bnext = (a == last) ? other : last;
+    for (int k = 0; k < nu2; ++k) {
+      sweep(Lv, cf, dinv, a, bfine, bnext);
+      std::swap(a, bnext);
+    }
+    cur[l] = a;
+  }
+  h->vcycles += S;
+  return cur[0];
+}
+
+// z = P^{-1} v with the configured block preconditioner (v, z: double stage vectors).
+// transpose: apply P^T (the triangular sweep runs the other way with A^T couplings
+// and every V(nu1, nu2) cycle becomes V(nu2, nu1), its transpose).
+template <typename T, typename C>
+int precond_apply(irk_handle* h, const double* v, double* z, bool transpose) {
+  using MG = MG2<T, C>;
+  const int s = h->s;
+  const int nu1 = transpose ? h->opt.nu_post : h->opt.nu_pre;
+  const int nu2 = transpose ? h->opt.nu_pre : h->opt.nu_post;
+  Level& L0 = h->lev[0];
+  cudaStream_t st = h->st;
+  const double p = sizeof(T), c = sizeof(C), ne = (double)h->ne;
+  if (h->opt.precond == IRK_PC_DIAG || s == 1) {
+    if constexpr (std::is_same<T, double>::value) {
+      vcycle<T, C>(h, s, 0, v, z, nu1, nu2);
+    } else {
+      {
+        KScope k(h, IRK_K_OTHER, ne * (8 + p), 0);
+        MG::cast_to(st, v, (T*)L0.b, h->ne);
+      }
+      T* x = vcycle<T, C>(h, s, 0, (const T*)L0.b, nullptr, nu1, nu2);
+      KScope k(h, IRK_K_OTHER, ne * (8 + p), 0);
+      MG::cast_from(st, x, z, h->ne);
+    }
+    CK_LAUNCH();
+    return IRK_OK;
+  }
+  // triangular sweep: lower (forward) or upper (backward) in the effective matrix
+  bool lower = (h->opt.precond == IRK_PC_LOWER);
+  if (transpose) lower = !lower;
+  const C* cf = Prec<T, C>::cf(L0);
+  const double n = n_int(L0.nx);
+  for (int step = 0; step < s; ++step) {
+    const int i = lower ? step : s - 1 - step;
+    Vec8 cj{};
+    int done = 0;
+    for (int j = 0; j < s; ++j) {
+      const bool solved = lower ? (j < i) : (j > i);
+      const double a = transpose ? h->A[j * s + i] : h->A[i * s + j];
+      cj.v[j] = solved ? h->dt * a : 0.0;
+      done += (solved && a != 0.0) ? 1 : 0;
+    }
+    {  // single-stage right-hand side in level-0 b (precision T)
+      KScope k(h, IRK_K_BLOCK_RHS, n * (8 + done * 8 + kCoef2 * c + p), 19.0 * done * n);
+      MG::block_rhs(s, st, L0.nx, cf, v, z, i, cj, (T*)L0.b);
+    }
+    T* x = vcycle<T, C>(h, 1, i, (const T*)L0.b, nullptr, nu1, nu2);
+    KScope k(h, IRK_K_OTHER, n * (p + 8), 0);
+    MG::scatter_stage(s, st, L0.nx, x, i, z);
+  }
+  CK_LAUNCH();
+  return IRK_OK;
+}
+
+int precond(irk_handle* h, const double* v, double* z, bool transpose) {
+  switch (h->opt.vcycle_prec) {
+    case IRK_PREC_FP64: return precond_apply<double, double>(h, v, z, transpose);
+    case IRK_PREC_FP32: return precond_apply<float, float>(h, v, z, transpose);
+    default: return precond_apply<__nv_bfloat16, float>(h, v, z, transpose);
+  }
+}
+
+Mat4 mixing(const irk_handle* h, bool transpose) {
+  Mat4 m{};
+  const int s = h->s;
+  for (int i = 0; i < s; ++i)
+    for (int j = 0; j < s; ++j) m.v[i * s + j] = h->dt * (transpose ? h->A[j * s + i] : h->A[i * s + j]);
+  return m;
+}
+
+int apply_operator(irk_handle* h, const double* x, double* y, bool transpose) {
+  const Level& L0 = h->lev[0];
+  const int s = h->s;
+  KScope k(h, IRK_K_STAGE_APPLY, (double)L0.nn * (16.0 * s + 8.0 * kCoef2), n_int(L0.nx) * s * (28.0 + 2.0 * s));
+  launch_stage_apply(s, h->st, L0.nx, L0.cf_d, L0.hm, mixing(h, transpose), x, y);
+  CK_LAUNCH();
+  return IRK_OK;
+}
+
+void multidot(irk_handle* h, const double* V, size_t ld, int count, const double* w, double* out) {
+  const double n = (double)h->ne;
+  {
+    KScope k(h, IRK_K_MULTIDOT, (count + 1.0) * n * 8, 2.0 * count * n);
+    launch_multidot(h->st, V, ld, count, w, h->ne, h->partial);
+  }
+  const double nb = krylov_partial_blocks();
+  KScope k(h, IRK_K_OTHER, count * nb * 8, count * nb);
+  launch_reduce_partials(h->st, h->partial, count, out);
+}
+
+void multi_axpy(irk_handle* h, double* w, const double* V, size_t ld, int count, const double* coef, double sign) {
+  const double n = (double)h->ne;
+  KScope k(h, IRK_K_AXPY, (count + 2.0) * n * 8, 2.0 * count * n);
+  launch_multi_axpy(h->st, w, V, ld, count, coef, sign, h->ne);
+}
+
+void scale(irk_handle* h, double* dst, const double* src, const double* denom) {
+  KScope k(h, IRK_K_OTHER, 16.0 * h->ne, (double)h->ne);
+  launch_scale(h->st, dst, src, denom, h->ne);
+}
+
+// ||v||_2 into scal[slot] (device), its square into scal[slot + 1].
+int norm2(irk_handle* h, const double* v, int slot) {
+  multidot(h, v, 0, 1, v, h->scal + slot + 1);
+  KScope k(h, IRK_K_OTHER, 0, 0);
+  launch_sqrt_scalar(h->st, h->scal + slot + 1, h->scal + slot);
+  CK_LAUNCH();
+  return IRK_OK;
+}
+
+// ----------------------------------------------------------------------------
+// FGMRES (right preconditioned, CGS2 Arnoldi, Givens on the device)
+// ----------------------------------------------------------------------------
+int fgmres(irk_handle* h, const double* rhs, double* x, bool transpose, irk_stats* stats) {
+  cudaStream_t st = h->st;
+  const size_t ne = h->ne;
+  const int m = h->m, ldh = m + 1;
+  h->vcycles = 0;
+  CK(cudaMemsetAsync(x, 0, ne * 8, st));
+  // beta = ||rhs||; scal[0] = beta, scal[1] = beta^2
+  TRY(norm2(h, rhs, 0));
+  CK(cudaMemcpyAsync(h->pinned, h->scal, 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const double r0 = h->pinned[0];
+  if (!std::isfinite(r0)) return fail(IRK_ENONFINITE, "right-hand side norm is %g", r0);
+  int its = 0;
+  double rel = (r0 == 0.0) ? 0.0 : 1.0;
+  bool conv = (r0 == 0.0);
+  const double* r = rhs;
+  while (!conv && its < h->opt.maxit) {
+    scale(h, h->V, r, h->scal);  // V_0 = r / beta
+    {
+      KScope k(h, IRK_K_OTHER, 0, 0);
+      launch_init_g(st, h->g, m + 1, h->scal);
+    }
+    int J = 0;
+    for (int j = 0; j < m; ++j) {
+      double* vj = h->V + (size_t)j * ne;
+      double* zj = h->Z + (size_t)j * ne;
+      double* w = h->V + (size_t)(j + 1) * ne;
+      TRY(precond(h, vj, zj, transpose));
+      TRY(apply_operator(h, zj, w, transpose));
+      // classical Gram-Schmidt, twice
+      multidot(h, h->V, ne, j + 1, w, h->h1);
+      multi_axpy(h, w, h->V, ne, j + 1, h->h1, -1.0);
+      multidot(h, h->V, ne, j + 1, w, h->h2);
+      multi_axpy(h, w, h->V, ne, j + 1, h->h2, -1.0);
+      // ||w||^2 -> scal[3]; Givens (hn -> scal[4], rel -> scal[5], hn -> scal[6]); w /= ||w||
+      multidot(h, w, 0, 1, w, h->scal + 3);
+      {
+        KScope k(h, IRK_K_OTHER, 0, 0);
+        launch_givens(st, j, ldh, h->H, h->cs, h->sn, h->g, h->h1, h->h2, h->scal + 3, h->scal + 4, r0, h->scal + 5);
+      }
+      scale(h, w, w, h->scal + 4);
+      CK_LAUNCH();
+      CK(cudaMemcpyAsync(h->pinned + 2, h->scal + 5, 16, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      rel = h->pinned[2];
+      const double hn = h->pinned[3];
+      ++its;
+      J = j + 1;
+      if (!std::isfinite(rel) || !std::isfinite(hn))
+        return fail(IRK_ENONFINITE, "FGMRES residual estimate is %g at iteration %d", rel, its);
+      if (rel <= h->opt.rtol || hn == 0.0) conv = true;
+      if (conv || its >= h->opt.maxit) break;
+    }
+    {  // x += Z y, y = R^{-1} g
+      KScope k(h, IRK_K_OTHER, 0, 0);
+      launch_trisolve(st, J, ldh, h->H, h->g, h->y);
+    }
+    multi_axpy(h, x, h->Z, ne, J, h->y, 1.0);
+    CK_LAUNCH();
+    if (conv || its >= h->opt.maxit) break;
+    // restart: r = rhs - S x in tmp, beta = ||r||
+    TRY(apply_operator(h, x, h->tmp, transpose));
+    {
+      KScope k(h, IRK_K_OTHER, 24.0 * ne, (double)ne);
+      launch_sub(st, h->tmp, rhs, h->tmp, ne);
+    }
+    TRY(norm2(h, h->tmp, 0));
+    r = h->tmp;
+  }
+  if (stats) {
+    stats->fgmres_its = its;
+    stats->vcycles = h->vcycles;
+    stats->rel_resid = rel;
+    stats->converged = conv ? 1 : 0;
+  }
+  if (!conv) return fail(IRK_ENOCONV, "FGMRES stopped at maxit = %d with relative residual %g", its, rel);
+  return IRK_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+extern "C" {
+
+void irk_default_options(irk_options* o) {
+  if (!o) return;
+  o->precond = IRK_PC_LOWER;
+  o->vcycle_prec = IRK_PREC_FP64;
+  o->nu_pre = 2;
+  o->nu_post = 2;
+  o->omega = 2.0 / 3.0;
+  o->rtol = 1e-10;
+  o->restart = 50;
+  o->maxit = 500;
+}
+
+const char* irk_last_error(void) { return g_err.c_str(); }
+
+int irk_perf_select(irk_handle* h, unsigned class_mask) {
+  if (!h) return fail(IRK_EINVAL, "null handle");
+  perf_drain(h, false);
+  h->perf = irk_perf{};
+  h->perf_mask = class_mask & ((1u << IRK_K_COUNT) - 1);
+  return IRK_OK;
+}
+
+int irk_perf_read(irk_handle* h, irk_perf* out) {
+  if (!h || !out) return fail(IRK_EINVAL, "null argument");
+  perf_drain(h, true);
+  *out = h->perf;
+  return IRK_OK;
+}
+
+int irk_create(irk_handle** out, const irk_mesh* mesh, const irk_tableau* tab, double dt, const irk_options* opt,
+               void* stream) {
+  try {
+    g_err.clear();
+    return create(out, mesh, tab, dt, opt, stream);
+  } catch (const std::bad_alloc&) {
+    return fail(IRK_ENOMEM, "host allocation failed");
+  } catch (...) {
+    return fail(IRK_EINVAL, "unexpected host exception in irk_create");
+  }
+}
+
+int irk_destroy(irk_handle* h) {
+  if (!h) return IRK_OK;
+  cudaStreamSynchronize(h->st);
+  destroy(h);
+  return IRK_OK;
+}
+
+int irk_set_kappa(irk_handle* h, const double* kappa) {
+  if (!h) return fail(IRK_EINVAL, "null handle");
+  if (!kappa) return fail(IRK_EINVAL, "null kappa");
+  try {
+    const size_t nc = (size_t)h->N * h->N;
+    for (size_t i = 0; i < nc; ++i)
+      if (!(kappa[i] > 0.0) || !std::isfinite(kappa[i]))
+        return fail(IRK_EINVAL, "kappa[%zu] = %g is not positive and finite", i, kappa[i]);
+    CK(cudaStreamSynchronize(h->st));
+    h->kappa.assign(kappa, kappa + nc);
+    return build_operators(h);
+  } catch (...) {
+    return fail(IRK_ENOMEM, "host allocation failed");
+  }
+}
+
+int irk_apply_operator(irk_handle* h, const double* x, double* y, int transpose) {
+  if (!h || !x || !y) return fail(IRK_EINVAL, "null argument");
+  const size_t bytes = h->ne * 8;
+  const void* xd;
+  void* yd;
+  bool yhost;
+  TRY(dev_in(h, x, bytes, 0, &xd));
+  TRY(dev_out(h, y, bytes, 1, &yd, &yhost));
+  TRY(apply_operator(h, (const double*)xd, (double*)yd, transpose != 0));
+  if (yhost) TRY(dev_out_finish(h, y, yd, bytes));
+  CK(cudaStreamSynchronize(h->st));
+  return IRK_OK;
+}
+
+int irk_apply_preconditioner(irk_handle* h, const double* v, double* z, int transpose) {
+  if (!h || !v || !z) return fail(IRK_EINVAL, "null argument");
+  const size_t bytes = h->ne * 8;
+  const void* vd;
+  void* zd;
+  bool zhost;
+  TRY(dev_in(h, v, bytes, 0, &vd));
+  TRY(dev_out(h, z, bytes, 1, &zd, &zhost));
+  // the triangular sweeps read z for the stages already solved: start from zero
+  CK(cudaMemsetAsync(zd, 0, bytes, h->st));
+  h->vcycles = 0;
+  TRY(precond(h, (const double*)vd, (double*)zd, transpose != 0));
+  if (zhost) TRY(dev_out_finish(h, z, zd, bytes));
+  CK(cudaStreamSynchronize(h->st));
+  return IRK_OK;
+}
+
+int irk_solve(irk_handle* h, const double* r, double* k, irk_stats* stats) {
+  if (!h || !r || !k) return fail(IRK_EINVAL, "null argument");
+  const size_t bytes = h->ne * 8;
+  const void* rd;
+  void* kd;
+  bool khost;
+  TRY(dev_in(h, r, bytes, 0, &rd));
+  TRY(dev_out(h, k, bytes, 1, &kd, &khost));
+  const int rc = fgmres(h, (const double*)rd, (double*)kd, false, stats);
+  if (rc != IRK_OK && rc != IRK_ENOCONV) return rc;
+  if (khost) TRY(dev_out_finish(h, k, kd, bytes));
+  CK(cudaStreamSynchronize(h->st));
+  return rc;
+}
+
+int irk_step(irk_handle* h, const double* u_n, const double* f_space, const double* f_coef, const double* f_stages,
+             double* u_np1, double* stages_out, irk_stats* stats) {
+  if (!h || !u_n || !u_np1) return fail(IRK_EINVAL, "null argument");
+  const int s = h->s;
+  const size_t nn = h->lev[0].nn, nb = nn * 8, sb = h->ne * 8;
+  const void *ud, *fd, *fsd;
+  void *outd, *kd;
+  bool outhost, khost;
+  TRY(dev_in(h, u_n, nb, 2, &ud));
+  TRY(dev_in(h, f_space, nb, 3, &fd));
+  TRY(dev_in(h, f_stages, sb, 4, &fsd));
+  TRY(dev_out(h, u_np1, nb, 5, &outd, &outhost));
+  TRY(dev_out(h, stages_out, sb, 6, &kd, &khost));
+  Vec8 fc{};
+  for (int i = 0; i < s; ++i) fc.v[i] = f_coef ? f_coef[i] : 1.0;
+  {
+    const double nn_d = (double)nn;
+    KScope k(h, IRK_K_OTHER, nn_d * (8 + 8 + 8.0 * kCoef2 + 8.0 * s + (fsd ? 8.0 * s : 0.0)),
+             n_int(h->lev[0].nx) * (17.0 + 2.0 * s));
+    launch_rhs(s, h->st, h->lev[0].nx, h->lev[0].cf_d, (const double*)ud, (const double*)fd, fc,
+               (const double*)fsd, h->rhs);
+  }
+  CK_LAUNCH();
+  const int rc = fgmres(h, h->rhs, h->k, false, stats);
+  if (rc != IRK_OK && rc != IRK_ENOCONV) return rc;
+  Vec8 bdt{};
+  for (int i = 0; i < s; ++i) bdt.v[i] = h->dt * h->b[i];
+  {
+    KScope k(h, IRK_K_OTHER, (double)nn * (16.0 + 8.0 * s), 2.0 * s * n_int(h->lev[0].nx));
+    launch_rk_update(s, h->st, h->lev[0].nx, (const double*)ud, h->k, bdt, (double*)outd);
+  }
+  CK_LAUNCH();
+  if (kd) CK(cudaMemcpyAsync(kd, h->k, sb, cudaMemcpyDeviceToDevice, h->st));
+  if (outhost) TRY(dev_out_finish(h, u_np1, outd, nb));
+  if (khost) TRY(dev_out_finish(h, stages_out, kd, sb));
+  CK(cudaStreamSynchronize(h->st));
+  return rc;
+}
+
+int irk_step_adjoint(irk_handle* h, const double* u_n, const double* stages, const double* lam_np1, double* lam_n,
+                     double* grad_accum, irk_stats* stats) {
+  if (!h || !u_n || !stages || !lam_np1 || !lam_n) return fail(IRK_EINVAL, "null argument");
+  const int s = h->s;
+  const size_t nn = h->lev[0].nn, nb = nn * 8, sb = h->ne * 8, gb = (size_t)h->N * h->N * 8;
+  const void *ud, *kd, *ld;
+  void *lod, *gd = nullptr;
+  bool lohost, ghost = false;
+  TRY(dev_in(h, u_n, nb, 2, &ud));
+  TRY(dev_in(h, stages, sb, 4, &kd));
+  TRY(dev_in(h, lam_np1, nb, 3, &ld));
+  TRY(dev_out(h, lam_n, nb, 5, &lod, &lohost));
+  if (grad_accum) {
+    if (is_device_ptr(grad_accum)) {
+      gd = grad_accum;
+    } else {
+      const void* gin;
+      TRY(dev_in(h, grad_accum, gb, 7, &gin));  // accumulate onto the caller's values
+      gd = (void*)gin;
+      ghost = true;
+    }
+  }
+  // rhs_i = dt b_i lam_{n+1}
+  Vec8 fc{};
+  for (int i = 0; i < s; ++i) fc.v[i] = h->dt * h->b[i];
+  {
+    KScope k(h, IRK_K_OTHER, (double)nn * (8.0 + 8.0 * s), n_int(h->lev[0].nx) * s);
+    launch_rhs(s, h->st, h->lev[0].nx, h->lev[0].cf_d, nullptr, (const double*)ld, fc, nullptr, h->rhs);
+  }
+  CK_LAUNCH();
+  const int rc = fgmres(h, h->rhs, h->k, true, stats);  // h->k = mu
+  if (rc != IRK_OK && rc != IRK_ENOCONV) return rc;
+  if (gd) {
+    Mat4 dtA = mixing(h, false);
+    const double ncell = (double)h->N * h->N;
+    KScope k(h, IRK_K_OTHER, ncell * 24.0 + (double)nn * (8.0 + 16.0 * s), ncell * s * (4.0 * (1 + 2 * s) + 36.0));
+    launch_cell_gradient(s, h->st, h->N, h->kappa.empty() ? nullptr : h->kappa_d, (const double*)ud,
+                         (const double*)kd, dtA, h->k, (double*)gd);
+  }
+  {
+    KScope k(h, IRK_K_OTHER, (double)nn * (24.0 + 8.0 * s + 8.0 * kCoef2), 18.0 * s * n_int(h->lev[0].nx));
+    launch_adjoint_lambda(s, h->st, h->lev[0].nx, h->lev[0].cf_d, (const double*)ld, h->k, (double*)lod);
+  }
+  CK_LAUNCH();
+  if (lohost) TRY(dev_out_finish(h, lam_n, lod, nb));
+  if (ghost) TRY(dev_out_finish(h, grad_accum, gd, gb));
+  CK(cudaStreamSynchronize(h->st));
+  return rc;
+}
+
+}  // extern "C"

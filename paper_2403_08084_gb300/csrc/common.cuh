@@ -1,0 +1,101 @@
+// Shared device-side definitions of the GB300 stage-coupled RK solver.
+//
+// Grid conventions (2D, uniform mesh of the unit square with N cells per axis):
+//   nx = N + 1 nodes per axis, node p = ix + nx * iy, x fastest; interior nodes
+//   have 1 <= ix, iy <= nx - 2.  Every level vector spans the full node grid and
+//   keeps zeros on the boundary (homogeneous Dirichlet), so stencils need no
+//   bounds logic for interior nodes.  Stage vectors are node-major with the S
+//   stage values of a node contiguous: v[p * S + i].
+//
+// The stiffness operator of a level is stored as a symmetric 9-point stencil,
+// five values per node in one record: {D, E, N, NE, NW} = the couplings of p
+// with itself, p+1, p+nx, p+nx+1 and p+nx-1.  The couplings towards W, S, SW
+// and SE are read from the neighbours' records (symmetry).  The mass matrix of
+// a level is the constant Q1 stencil (h^2/36) [1 4 1; 4 16 4; 1 4 1].
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+namespace irk {
+
+constexpr int kMaxS = 4;     // IRK_MAX_STAGES
+constexpr int kCoef2 = 5;    // stencil record length (2D)
+
+// Small fixed-size arrays passed to kernels by value.
+struct Vec8 {
+  double v[8];
+};
+struct Mat4 {
+  double v[kMaxS * kMaxS];  // row-major S x S, leading dimension S
+};
+
+// ----------------------------------------------------------------------------
+// precision helpers: storage type T, compute type C
+// ----------------------------------------------------------------------------
+template <typename C, typename T>
+__device__ __forceinline__ C ld(const T* p) {
+  return static_cast<C>(*p);
+}
+template <>
+__device__ __forceinline__ float ld<float, __nv_bfloat16>(const __nv_bfloat16* p) {
+  return __bfloat162float(*p);
+}
+template <>
+__device__ __forceinline__ double ld<double, __nv_bfloat16>(const __nv_bfloat16* p) {
+  return static_cast<double>(__bfloat162float(*p));
+}
+
+template <typename T, typename C>
+__device__ __forceinline__ void st(T* p, C v) {
+  *p = static_cast<T>(v);
+}
+template <>
+__device__ __forceinline__ void st<__nv_bfloat16, float>(__nv_bfloat16* p, float v) {
+  *p = __float2bfloat16_rn(v);
+}
+template <>
+__device__ __forceinline__ void st<__nv_bfloat16, double>(__nv_bfloat16* p, double v) {
+  *p = __float2bfloat16_rn(static_cast<float>(v));
+}
+
+// ----------------------------------------------------------------------------
+// 2D stencil primitives at an interior node p
+// ----------------------------------------------------------------------------
+// (K x)(p) for one stage i of an S-interleaved vector.
+template <int S, typename C, typename T>
+__device__ __forceinline__ C k_apply(const C* __restrict__ cf, const T* __restrict__ x, int p, int nx, int i) {
+  const C* c0 = cf + (size_t)p * kCoef2;
+  const C* cw = cf + (size_t)(p - 1) * kCoef2;
+  const C* cs = cf + (size_t)(p - nx) * kCoef2;
+  const C* csw = cf + (size_t)(p - nx - 1) * kCoef2;
+  const C* cse = cf + (size_t)(p - nx + 1) * kCoef2;
+  C y = c0[0] * ld<C>(x + (size_t)p * S + i);
+  y += c0[1] * ld<C>(x + (size_t)(p + 1) * S + i);
+  y += cw[1] * ld<C>(x + (size_t)(p - 1) * S + i);
+  y += c0[2] * ld<C>(x + (size_t)(p + nx) * S + i);
+  y += cs[2] * ld<C>(x + (size_t)(p - nx) * S + i);
+  y += c0[3] * ld<C>(x + (size_t)(p + nx + 1) * S + i);
+  y += csw[3] * ld<C>(x + (size_t)(p - nx - 1) * S + i);
+  y += c0[4] * ld<C>(x + (size_t)(p + nx - 1) * S + i);
+  y += cse[4] * ld<C>(x + (size_t)(p - nx + 1) * S + i);
+  return y;
+}
+
+// 36/h^2 (M x)(p): the unscaled mass stencil [1 4 1; 4 16 4; 1 4 1].
+template <int S, typename C, typename T>
+__device__ __forceinline__ C m_apply_unscaled(const T* __restrict__ x, int p, int nx, int i) {
+  auto X = [&](int q) { return ld<C>(x + (size_t)q * S + i); };
+  C edge = X(p - 1) + X(p + 1) + X(p - nx) + X(p + nx);
+  C corner = X(p - nx - 1) + X(p - nx + 1) + X(p + nx - 1) + X(p + nx + 1);
+  return C(16) * X(p) + C(4) * edge + corner;
+}
+
+__device__ __forceinline__ bool interior2(int ix, int iy, int nx) {
+  return ix >= 1 && iy >= 1 && ix <= nx - 2 && iy <= nx - 2;
+}
+
+}  // namespace irk

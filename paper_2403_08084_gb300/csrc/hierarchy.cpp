@@ -1,0 +1,224 @@
+// Host-side construction of the multigrid hierarchy: level stencils,
+// Galerkin coarse operators, Jacobi diagonals and the exact coarsest-level
+// inverse (Sec. 3.1: each diagonal block M + dt a_ii K is approximated by one
+// multigrid V-cycle).
+#include "hierarchy.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstddef>
+#include <utility>
+
+namespace irk {
+
+namespace {
+enum { kD = 0, kE = 1, kN = 2, kNE = 3, kNW = 4, kRec = 5 };
+
+// K(a, b) for nodes a = (ax, ay), b = a + (dx, dy), |dx|, |dy| <= 1, from records.
+inline double coupling(const std::vector<double>& cf, int nx, int ax, int ay, int dx, int dy) {
+  const size_t a = (size_t)ax + (size_t)nx * ay;
+  auto R = [&](size_t node, int k) { return cf[node * kRec + k]; };
+  if (dx == 0 && dy == 0) return R(a, kD);
+  if (dx == 1 && dy == 0) return R(a, kE);
+  if (dx == -1 && dy == 0) return R(a - 1, kE);
+  if (dx == 0 && dy == 1) return R(a, kN);
+  if (dx == 0 && dy == -1) return R(a - nx, kN);
+  if (dx == 1 && dy == 1) return R(a, kNE);
+  if (dx == -1 && dy == -1) return R(a - nx - 1, kNE);
+  if (dx == -1 && dy == 1) return R(a, kNW);
+  return R(a + 1 - nx, kNW);  // (1, -1)
+}
+
+// Record slot holding K(I, J) for J = I + (dx, dy) if (dx, dy) is a forward
+// direction or the node itself; -1 for the four backward directions.
+inline int forward_slot(int dx, int dy) {
+  if (dx == 0 && dy == 0) return kD;
+  if (dx == 1 && dy == 0) return kE;
+  if (dx == 0 && dy == 1) return kN;
+  if (dx == 1 && dy == 1) return kNE;
+  if (dx == -1 && dy == 1) return kNW;
+  return -1;
+}
+
+// Coarse parents of fine index i (1D linear interpolation): returns count.
+inline int parents(int i, int* idx, double* w) {
+  if ((i & 1) == 0) {
+    idx[0] = i / 2;
+    w[0] = 1.0;
+    return 1;
+  }
+  idx[0] = (i - 1) / 2;
+  idx[1] = (i + 1) / 2;
+  w[0] = w[1] = 0.5;
+  return 2;
+}
+
+inline bool interior(int ix, int iy, int nx) { return ix >= 1 && iy >= 1 && ix <= nx - 2 && iy <= nx - 2; }
+}  // namespace
+
+void stiffness_records_2d(int N, const double* kappa, std::vector<double>& cf) {
+  const int nx = N + 1;
+  cf.assign((size_t)nx * nx * kRec, 0.0);
+  for (int cy = 0; cy < N; ++cy) {
+    for (int cx = 0; cx < N; ++cx) {
+      const double k = kappa ? kappa[(size_t)cx + (size_t)N * cy] : 1.0;
+      const size_t p0 = (size_t)cx + (size_t)nx * cy, p1 = p0 + 1, p2 = p0 + nx, p3 = p2 + 1;
+      // bilinear element matrix kappa/6 [[4,-1,-1,-2],[-1,4,-2,-1],[-1,-2,4,-1],[-2,-1,-1,4]]
+      for (size_t p : {p0, p1, p2, p3}) cf[p * kRec + kD] += 4.0 * k / 6.0;
+      cf[p0 * kRec + kE] += -k / 6.0;   // p0 - p1
+      cf[p2 * kRec + kE] += -k / 6.0;   // p2 - p3
+      cf[p0 * kRec + kN] += -k / 6.0;   // p0 - p2
+      cf[p1 * kRec + kN] += -k / 6.0;   // p1 - p3
+      cf[p0 * kRec + kNE] += -2.0 * k / 6.0;  // p0 - p3
+      cf[p1 * kRec + kNW] += -2.0 * k / 6.0;  // p1 - p2
+    }
+  }
+}
+
+void galerkin_coarsen_2d(int Nf, const std::vector<double>& cff, std::vector<double>& cfc) {
+  const int Nc = Nf / 2, nxf = Nf + 1, nxc = Nc + 1;
+  cfc.assign((size_t)nxc * nxc * kRec, 0.0);
+  int pax[2], pay[2], pbx[2], pby[2];
+  double wax[2], way[2], wbx[2], wby[2];
+  for (int ay = 0; ay < nxf; ++ay) {
+    const int nay = parents(ay, pay, way);
+    for (int ax = 0; ax < nxf; ++ax) {
+      const int nax = parents(ax, pax, wax);
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int by = ay + dy;
+        if (by < 0 || by >= nxf) continue;
+        const int nby = parents(by, pby, wby);
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int bx = ax + dx;
+          if (bx < 0 || bx >= nxf) continue;
+          const double v = coupling(cff, nxf, ax, ay, dx, dy);
+          if (v == 0.0) continue;
+          const int nbx = parents(bx, pbx, wbx);
+          for (int ia = 0; ia < nay; ++ia)
+            for (int ja = 0; ja < nax; ++ja)
+              for (int ib = 0; ib < nby; ++ib)
+                for (int jb = 0; jb < nbx; ++jb) {
+                  const int slot = forward_slot(pbx[jb] - pax[ja], pby[ib] - pay[ia]);
+                  if (slot < 0) continue;  // counted from the symmetric pair
+                  const size_t I = (size_t)pax[ja] + (size_t)nxc * pay[ia];
+                  cfc[I * kRec + slot] += wax[ja] * way[ia] * v * wbx[jb] * wby[ib];
+                }
+        }
+      }
+    }
+  }
+}
+
+void jacobi_inverse_diag_2d(int N, const std::vector<double>& cf, double hm, const double* sigma, int S,
+                            double omega, std::vector<double>& dinv) {
+  const int nx = N + 1;
+  dinv.assign((size_t)nx * nx * S, 0.0);
+  for (int iy = 1; iy < nx - 1; ++iy)
+    for (int ix = 1; ix < nx - 1; ++ix) {
+      const size_t p = (size_t)ix + (size_t)nx * iy;
+      for (int i = 0; i < S; ++i) dinv[p * S + i] = omega / (16.0 * hm + sigma[i] * cf[p * kRec + kD]);
+    }
+}
+
+void interior_nodes_2d(int N, std::vector<int>& map) {
+  const int nx = N + 1;
+  map.clear();
+  for (int iy = 1; iy < nx - 1; ++iy)
+    for (int ix = 1; ix < nx - 1; ++ix) map.push_back(ix + nx * iy);
+}
+
+bool dense_block_inverse_2d(int N, const std::vector<double>& cf, double hm, double sigma,
+                            const std::vector<int>& map, std::vector<double>& inv) {
+  const int nx = N + 1;
+  const int n = (int)map.size();
+  std::vector<int> pos((size_t)nx * nx, -1);
+  for (int c = 0; c < n; ++c) pos[map[c]] = c;
+  // B = M + sigma K on interior nodes, M = hm [1 4 1; 4 16 4; 1 4 1]
+  std::vector<double> B((size_t)n * n, 0.0);
+  for (int r = 0; r < n; ++r) {
+    const int p = map[r], ix = p % nx, iy = p / nx;
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int jx = ix + dx, jy = iy + dy;
+        if (!interior(jx, jy, nx)) continue;
+        const int c = pos[jx + nx * jy];
+        const double m = hm * ((dx == 0 ? 4.0 : 1.0) * (dy == 0 ? 4.0 : 1.0));
+        B[(size_t)r * n + c] = m + sigma * coupling(cf, nx, ix, iy, dx, dy);
+      }
+  }
+  const int bw = nx - 1;  // |row - col| <= nx - 1 for the 9-point stencil in interior numbering
+  if (sigma >= 0.0) {
+    // M + sigma K is symmetric positive definite: banded LU without pivoting keeps the band.
+    std::vector<double> F = B;
+    bool ok = true;
+    for (int k = 0; k < n && ok; ++k) {
+      const double piv = F[(size_t)k * n + k];
+      if (!(piv > 0.0) || !std::isfinite(piv)) {
+        ok = false;
+        break;
+      }
+      const int rmax = std::min(n - 1, k + bw);
+      for (int r = k + 1; r <= rmax; ++r) {
+        const double f = F[(size_t)r * n + k] / piv;
+        if (f == 0.0) continue;
+        F[(size_t)r * n + k] = f;
+        for (int c = k + 1; c <= rmax; ++c) F[(size_t)r * n + c] -= f * F[(size_t)k * n + c];
+      }
+    }
+    if (ok) {
+      inv.assign((size_t)n * n, 0.0);
+      std::vector<double> y(n);
+      for (int col = 0; col < n; ++col) {
+        std::fill(y.begin(), y.end(), 0.0);
+        y[col] = 1.0;
+        for (int r = col + 1; r < n; ++r) {  // L y = e_col (unit lower, band)
+          double v = y[r];
+          for (int c = std::max(col, r - bw); c < r; ++c) v -= F[(size_t)r * n + c] * y[c];
+          y[r] = v;
+        }
+        for (int r = n - 1; r >= 0; --r) {  // U x = y
+          double v = y[r];
+          const int cmax = std::min(n - 1, r + bw);
+          for (int c = r + 1; c <= cmax; ++c) v -= F[(size_t)r * n + c] * y[c];
+          y[r] = v / F[(size_t)r * n + r];
+        }
+        for (int r = 0; r < n; ++r) inv[(size_t)r * n + col] = y[r];
+      }
+      return true;
+    }
+  }
+  // General case: Gauss-Jordan elimination with partial pivoting on [B | I].
+  inv.assign((size_t)n * n, 0.0);
+  for (int r = 0; r < n; ++r) inv[(size_t)r * n + r] = 1.0;
+  for (int k = 0; k < n; ++k) {
+    int piv = k;
+    double best = std::fabs(B[(size_t)k * n + k]);
+    for (int r = k + 1; r < n; ++r) {
+      const double v = std::fabs(B[(size_t)r * n + k]);
+      if (v > best) best = v, piv = r;
+    }
+    if (!(best > 0.0) || !std::isfinite(best)) return false;
+    if (piv != k) {
+      for (int c = 0; c < n; ++c) {
+        std::swap(B[(size_t)k * n + c], B[(size_t)piv * n + c]);
+        std::swap(inv[(size_t)k * n + c], inv[(size_t)piv * n + c]);
+      }
+    }
+    const double d = 1.0 / B[(size_t)k * n + k];
+    double* Bk = &B[(size_t)k * n];
+    double* Ik = &inv[(size_t)k * n];
+    for (int c = 0; c < n; ++c) Bk[c] *= d, Ik[c] *= d;
+    for (int r = 0; r < n; ++r) {
+      if (r == k) continue;
+      const double f = B[(size_t)r * n + k];
+      if (f == 0.0) continue;
+      double* Br = &B[(size_t)r * n];
+      double* Ir = &inv[(size_t)r * n];
+      for (int c = 0; c < n; ++c) Br[c] -= f * Bk[c];
+      for (int c = 0; c < n; ++c) Ir[c] -= f * Ik[c];
+    }
+  }
+  return true;
+}
+
+}  // namespace irk

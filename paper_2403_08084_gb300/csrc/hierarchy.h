@@ -1,0 +1,29 @@
+// Host-side construction of the multigrid hierarchy (plain C++, no CUDA).
+#pragma once
+
+#include <vector>
+
+namespace irk {
+
+// Level-0 stiffness stencil records {D, E, N, NE, NW} per node of the full
+// (N+1)^2 grid, assembled cell by cell from the bilinear element matrix with
+// per-cell diffusivity (kappa == nullptr: kappa = 1).
+void stiffness_records_2d(int N, const double* kappa, std::vector<double>& cf);
+
+// Galerkin coarse stencil P^T K_f P (P = bilinear interpolation on the full
+// grid) from fine records with Nf cells per axis to Nf/2.
+void galerkin_coarsen_2d(int Nf, const std::vector<double>& cff, std::vector<double>& cfc);
+
+// omega / diag(M + sigma_i K) at interior nodes (0 on the boundary), node-major
+// with S values per node; hm = h^2/36.
+void jacobi_inverse_diag_2d(int N, const std::vector<double>& cf, double hm, const double* sigma, int S,
+                            double omega, std::vector<double>& dinv);
+
+// Interior node ids of an N-cell grid (x fastest) and the dense inverse of
+// M + sigma K restricted to them (row-major, nint x nint).  Returns false if the
+// matrix is singular to working precision.
+void interior_nodes_2d(int N, std::vector<int>& map);
+bool dense_block_inverse_2d(int N, const std::vector<double>& cf, double hm, double sigma,
+                            const std::vector<int>& map, std::vector<double>& inv);
+
+}  // namespace irk

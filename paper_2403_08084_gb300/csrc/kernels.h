@@ -1,0 +1,58 @@
+// Host-side launchers of the solver's CUDA kernels (internal to libirk.so).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstddef>
+
+namespace irk {
+
+struct Vec8;
+struct Mat4;
+
+// Multigrid kernels for one precision: storage T, arithmetic C (mg2d.cuh).
+template <typename T, typename C>
+struct MG2 {
+  static void jacobi(int S, cudaStream_t st, int nx, const C* cf, double hm, const Vec8& sigma, const C* dinv,
+                     int dstride, const T* xin, const T* b, T* xout);
+  static void residual(int S, cudaStream_t st, int nx, const C* cf, double hm, const Vec8& sigma, const T* x,
+                       const T* b, T* r);
+  static void restrict_(int S, cudaStream_t st, int nxf, const T* rf, int nxc, T* bc);
+  static void prolong_add(int S, cudaStream_t st, int nxc, const T* ec, int nxf, T* xf);
+  static void block_rhs(int SF, cudaStream_t st, int nx, const C* cf, const double* v, const double* z, int i,
+                        const Vec8& cj, T* out);
+  static void scatter_stage(int SF, cudaStream_t st, int nx, const T* x, int i, double* z);
+  static void cast_to(cudaStream_t st, const double* src, T* dst, size_t n);
+  static void cast_from(cudaStream_t st, const T* src, double* dst, size_t n);
+  static void coarse_solve(int S, cudaStream_t st, int nint, const C* binv, const int* map, const T* b, T* x);
+};
+
+// FP64 stage-operator kernels (op2d.cu).
+void launch_stage_apply(int S, cudaStream_t st, int nx, const double* cf, double hm, const Mat4& mix, const double* x,
+                        double* y);
+void launch_rhs(int S, cudaStream_t st, int nx, const double* cf, const double* u, const double* fsp,
+                const Vec8& fcoef, const double* fst, double* r);
+void launch_rk_update(int S, cudaStream_t st, int nx, const double* u, const double* k, const Vec8& bdt,
+                      double* out);
+void launch_adjoint_lambda(int S, cudaStream_t st, int nx, const double* cf, const double* lam_np1, const double* mu,
+                           double* lam_n);
+void launch_cell_gradient(int S, cudaStream_t st, int N, const double* kappa, const double* u, const double* k,
+                          const Mat4& dtA, const double* mu, double* grad);
+
+// Krylov kernels (krylov.cu), FP64.
+int krylov_partial_blocks();
+void launch_multidot(cudaStream_t st, const double* V, size_t ld, int count, const double* w, size_t n,
+                     double* partial);
+void launch_reduce_partials(cudaStream_t st, const double* partial, int count, double* out);
+void launch_multi_axpy(cudaStream_t st, double* w, const double* V, size_t ld, int count, const double* coef,
+                       double sign, size_t n);
+void launch_scale(cudaStream_t st, double* dst, const double* src, const double* denom, size_t n);
+void launch_givens(cudaStream_t st, int j, int ldh, double* H, double* cs, double* sn, double* g, const double* h1,
+                   const double* h2, const double* hn2, double* hn_out, double r0, double* rel_out);
+void launch_trisolve(cudaStream_t st, int J, int ldh, const double* H, const double* g, double* y);
+void launch_sqrt_scalar(cudaStream_t st, const double* in, double* out);
+void launch_sub(cudaStream_t st, double* out, const double* a, const double* b, size_t n);
+void launch_init_g(cudaStream_t st, double* g, int m1, const double* beta);
+
+}  // namespace irk

@@ -1,0 +1,199 @@
+// FP64 kernels of flexible GMRES (the outer solver of Sec. 4.1): Arnoldi
+// multi-dot products and multi-axpys for classical Gram-Schmidt applied twice,
+// the Givens update of the Hessenberg column and the triangular solve, all on
+// the device so the host never reads the Krylov data.
+//
+// Reductions are deterministic: every block writes one partial sum per dot
+// product and a second kernel adds the partials in a fixed order.
+#include "kernels.h"
+
+#include <cmath>
+
+namespace irk {
+
+namespace {
+constexpr int kThreads = 256;
+constexpr int kPartialBlocks = 152 * 4;  // partial sums per dot product (4 blocks per SM)
+constexpr int kGroup = 8;                // dot products accumulated per pass over w
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// partial[k * nb + blockIdx.x] = sum over this block's elements of V_k[e] w[e],
+// for k = blockIdx.y * kGroup + g < count.
+__global__ void __launch_bounds__(kThreads) multidot_kernel(const double* __restrict__ V, size_t ld, int count,
+                                                            const double* __restrict__ w, size_t n,
+                                                            double* __restrict__ partial) {
+  __shared__ double red[kThreads / 32][kGroup];
+  const int k0 = blockIdx.y * kGroup;
+  const int kn = min(kGroup, count - k0);
+  double acc[kGroup];
+#pragma unroll
+  for (int g = 0; g < kGroup; ++g) acc[g] = 0.0;
+  for (size_t e = blockIdx.x * (size_t)kThreads + threadIdx.x; e < n; e += (size_t)gridDim.x * kThreads) {
+    const double we = w[e];
+#pragma unroll
+    for (int g = 0; g < kGroup; ++g)
+      if (g < kn) acc[g] = fma(V[(size_t)(k0 + g) * ld + e], we, acc[g]);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int g = 0; g < kGroup; ++g) {
+    const double v = warp_sum(acc[g]);
+    if (lane == 0) red[warp][g] = v;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int g = 0; g < kGroup; ++g) {
+      double v = (lane < kThreads / 32) ? red[lane][g] : 0.0;
+      v = warp_sum(v);
+      if (lane == 0 && g < kn) partial[(size_t)(k0 + g) * gridDim.x + blockIdx.x] = v;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) reduce_partials_kernel(const double* __restrict__ partial, int nb,
+                                                                   double* __restrict__ out) {
+  __shared__ double red[kThreads / 32];
+  const int k = blockIdx.x;
+  double v = 0.0;
+  for (int b = threadIdx.x; b < nb; b += kThreads) v += partial[(size_t)k * nb + b];
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    v = (lane < kThreads / 32) ? red[lane] : 0.0;
+    v = warp_sum(v);
+    if (lane == 0) out[k] = v;
+  }
+}
+
+// w += sign * sum_k coef[k] V_k
+__global__ void __launch_bounds__(kThreads) multi_axpy_kernel(double* __restrict__ w, const double* __restrict__ V,
+                                                              size_t ld, int count, const double* __restrict__ coef,
+                                                              double sign, size_t n) {
+  __shared__ double c[128];
+  for (int k = threadIdx.x; k < count; k += kThreads) c[k] = sign * coef[k];
+  __syncthreads();
+  for (size_t e = blockIdx.x * (size_t)kThreads + threadIdx.x; e < n; e += (size_t)gridDim.x * kThreads) {
+    double acc = w[e];
+    for (int k = 0; k < count; ++k) acc = fma(c[k], V[(size_t)k * ld + e], acc);
+    w[e] = acc;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) scale_kernel(double* __restrict__ dst, const double* __restrict__ src,
+                                                         const double* __restrict__ denom, size_t n) {
+  const double d = *denom;
+  const double inv = (d != 0.0) ? 1.0 / d : 0.0;
+  for (size_t e = blockIdx.x * (size_t)kThreads + threadIdx.x; e < n; e += (size_t)gridDim.x * kThreads)
+    dst[e] = src[e] * inv;
+}
+
+// Column j of the Hessenberg matrix is h1 + h2 (the two Gram-Schmidt passes) with
+// subdiagonal hn = sqrt(hn2); apply the earlier rotations, form the new one,
+// update g and report |g_{j+1}| / r0.  One thread.
+__global__ void givens_kernel(int j, int ldh, double* __restrict__ H, double* __restrict__ cs,
+                              double* __restrict__ sn, double* __restrict__ g, const double* __restrict__ h1,
+                              const double* __restrict__ h2, const double* __restrict__ hn2,
+                              double* __restrict__ hn_out, double r0, double* __restrict__ rel_out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double* col = H + (size_t)j * ldh;
+  for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
+  const double hn2v = *hn2;
+  const double hn = (hn2v < 0.0) ? 0.0 : sqrt(hn2v);  // NaN stays NaN (fmax would hide it)
+  col[j + 1] = hn;
+  *hn_out = hn;
+  for (int i = 0; i < j; ++i) {
+    const double a = col[i], b = col[i + 1];
+    col[i] = cs[i] * a + sn[i] * b;
+    col[i + 1] = -sn[i] * a + cs[i] * b;
+  }
+  const double a = col[j], b = col[j + 1];
+  const double rho = hypot(a, b);
+  double c = 1.0, s = 0.0;
+  if (rho != 0.0) {
+    c = a / rho;
+    s = b / rho;
+  }
+  cs[j] = c;
+  sn[j] = s;
+  col[j] = rho;
+  col[j + 1] = 0.0;
+  g[j + 1] = -s * g[j];
+  g[j] = c * g[j];
+  rel_out[0] = fabs(g[j + 1]) / r0;
+  rel_out[1] = hn;
+}
+
+// y = R^{-1} g for the J x J upper-triangular R stored column-major in H.  One thread.
+__global__ void trisolve_kernel(int J, int ldh, const double* __restrict__ H, const double* __restrict__ g,
+                                double* __restrict__ y) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int i = J - 1; i >= 0; --i) {
+    double v = g[i];
+    for (int k = i + 1; k < J; ++k) v -= H[(size_t)k * ldh + i] * y[k];
+    y[i] = v / H[(size_t)i * ldh + i];
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) sub_kernel(double* __restrict__ out, const double* __restrict__ a,
+                                                       const double* __restrict__ b, size_t n) {
+  for (size_t e = blockIdx.x * (size_t)kThreads + threadIdx.x; e < n; e += (size_t)gridDim.x * kThreads)
+    out[e] = a[e] - b[e];
+}
+
+__global__ void sqrt_scalar_kernel(const double* __restrict__ in, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const double v = *in;
+    *out = (v < 0.0) ? 0.0 : sqrt(v);  // NaN stays NaN
+  }
+}
+
+__global__ void init_g_kernel(double* __restrict__ g, int m1, const double* __restrict__ beta) {
+  for (int i = threadIdx.x; i < m1; i += blockDim.x) g[i] = (i == 0) ? *beta : 0.0;
+}
+
+int grid_for(size_t n) {
+  size_t b = (n + kThreads - 1) / kThreads;
+  if (b > (size_t)kPartialBlocks) b = kPartialBlocks;
+  return b < 1 ? 1 : (int)b;
+}
+}  // namespace
+
+int krylov_partial_blocks() { return kPartialBlocks; }
+
+void launch_multidot(cudaStream_t st, const double* V, size_t ld, int count, const double* w, size_t n,
+                     double* partial) {
+  dim3 g(kPartialBlocks, (count + kGroup - 1) / kGroup);
+  multidot_kernel<<<g, kThreads, 0, st>>>(V, ld, count, w, n, partial);
+}
+void launch_reduce_partials(cudaStream_t st, const double* partial, int count, double* out) {
+  reduce_partials_kernel<<<count, kThreads, 0, st>>>(partial, kPartialBlocks, out);
+}
+void launch_multi_axpy(cudaStream_t st, double* w, const double* V, size_t ld, int count, const double* coef,
+                       double sign, size_t n) {
+  multi_axpy_kernel<<<grid_for(n), kThreads, 0, st>>>(w, V, ld, count, coef, sign, n);
+}
+void launch_scale(cudaStream_t st, double* dst, const double* src, const double* denom, size_t n) {
+  scale_kernel<<<grid_for(n), kThreads, 0, st>>>(dst, src, denom, n);
+}
+void launch_givens(cudaStream_t st, int j, int ldh, double* H, double* cs, double* sn, double* g, const double* h1,
+                   const double* h2, const double* hn2, double* hn_out, double r0, double* rel_out) {
+  givens_kernel<<<1, 32, 0, st>>>(j, ldh, H, cs, sn, g, h1, h2, hn2, hn_out, r0, rel_out);
+}
+void launch_trisolve(cudaStream_t st, int J, int ldh, const double* H, const double* g, double* y) {
+  trisolve_kernel<<<1, 32, 0, st>>>(J, ldh, H, g, y);
+}
+void launch_sub(cudaStream_t st, double* out, const double* a, const double* b, size_t n) {
+  sub_kernel<<<grid_for(n), kThreads, 0, st>>>(out, a, b, n);
+}
+void launch_sqrt_scalar(cudaStream_t st, const double* in, double* out) { sqrt_scalar_kernel<<<1, 32, 0, st>>>(in, out); }
+void launch_init_g(cudaStream_t st, double* g, int m1, const double* beta) { init_g_kernel<<<1, 128, 0, st>>>(g, m1, beta); }
+
+}  // namespace irk

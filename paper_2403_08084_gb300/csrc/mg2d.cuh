@@ -1,0 +1,238 @@
+// Geometric-multigrid kernels for one diagonal block B = M + sigma K of the
+// stage system (Sec. 3.1: "approximate the inverse of this block with a
+// standard multigrid method").  Templated on the vector storage type T, the
+// arithmetic type C and the number S of stage-interleaved blocks handled in one
+// pass (S > 1 batches the independent blocks of the block-diagonal
+// preconditioner so that every stencil and coefficient load serves all S).
+//
+// The launchers at the bottom are explicitly instantiated per precision in
+// mg2d_f64.cu / mg2d_f32.cu / mg2d_bf16.cu.
+#pragma once
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace irk {
+
+constexpr int kBX = 32, kBY = 8;
+
+inline dim3 interior_grid(int nx) {
+  int m = nx - 2;
+  return dim3((m + kBX - 1) / kBX, (m + kBY - 1) / kBY);
+}
+
+// Weighted Jacobi sweep  x_out = x_in + omega D^{-1} (b - B x_in), B = M + sigma_i K.
+// dinv holds omega / diag(B) per node and stage with stride dstride; xin == nullptr
+// means a zero initial guess (x_out = omega D^{-1} b).
+template <typename T, typename C, int S>
+__global__ void __launch_bounds__(kBX* kBY) jacobi_kernel(int nx, const C* __restrict__ cf, C hm, Vec8 sigma,
+                                                          const C* __restrict__ dinv, int dstride,
+                                                          const T* __restrict__ xin, const T* __restrict__ b,
+                                                          T* __restrict__ xout) {
+  const int ix = 1 + blockIdx.x * kBX + threadIdx.x;
+  const int iy = 1 + blockIdx.y * kBY + threadIdx.y;
+  if (ix > nx - 2 || iy > nx - 2) return;
+  const int p = ix + nx * iy;
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    const C bi = ld<C>(b + (size_t)p * S + i);
+    const C di = dinv[(size_t)p * dstride + i];
+    C xn;
+    if (xin == nullptr) {
+      xn = di * bi;
+    } else {
+      const C sg = static_cast<C>(sigma.v[i]);
+      const C bx = hm * m_apply_unscaled<S, C>(xin, p, nx, i) + sg * k_apply<S, C>(cf, xin, p, nx, i);
+      xn = ld<C>(xin + (size_t)p * S + i) + di * (bi - bx);
+    }
+    st(xout + (size_t)p * S + i, xn);
+  }
+}
+
+// r = b - B x on interior nodes.
+template <typename T, typename C, int S>
+__global__ void __launch_bounds__(kBX* kBY) residual_kernel(int nx, const C* __restrict__ cf, C hm, Vec8 sigma,
+                                                            const T* __restrict__ x, const T* __restrict__ b,
+                                                            T* __restrict__ r) {
+  const int ix = 1 + blockIdx.x * kBX + threadIdx.x;
+  const int iy = 1 + blockIdx.y * kBY + threadIdx.y;
+  if (ix > nx - 2 || iy > nx - 2) return;
+  const int p = ix + nx * iy;
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    const C sg = static_cast<C>(sigma.v[i]);
+    const C bx = hm * m_apply_unscaled<S, C>(x, p, nx, i) + sg * k_apply<S, C>(cf, x, p, nx, i);
+    st(r + (size_t)p * S + i, ld<C>(b + (size_t)p * S + i) - bx);
+  }
+}
+
+// b_c = P^T r_f: full weighting (1, 1/2, 1/4) onto coarse interior nodes (the
+// transpose of bilinear interpolation, so the coarse operators are Galerkin).
+template <typename T, typename C, int S>
+__global__ void __launch_bounds__(kBX* kBY) restrict_kernel(int nxf, const T* __restrict__ rf, int nxc,
+                                                            T* __restrict__ bc) {
+  const int I = 1 + blockIdx.x * kBX + threadIdx.x;
+  const int J = 1 + blockIdx.y * kBY + threadIdx.y;
+  if (I > nxc - 2 || J > nxc - 2) return;
+  const int q = 2 * I + nxf * 2 * J;
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    auto R = [&](int o) { return ld<C>(rf + (size_t)(q + o) * S + i); };
+    C v = R(0) + C(0.5) * (R(-1) + R(1) + R(-nxf) + R(nxf)) +
+          C(0.25) * (R(-nxf - 1) + R(-nxf + 1) + R(nxf - 1) + R(nxf + 1));
+    st(bc + (size_t)(I + nxc * J) * S + i, v);
+  }
+}
+
+// x_f += P e_c: bilinear interpolation.  With I0 = ix >> 1, I1 = (ix + 1) >> 1 (equal
+// for even ix) the average of the four corner values is the interpolant.
+template <typename T, typename C, int S>
+__global__ void __launch_bounds__(kBX* kBY) prolong_add_kernel(int nxc, const T* __restrict__ ec, int nxf,
+                                                               T* __restrict__ xf) {
+  const int ix = 1 + blockIdx.x * kBX + threadIdx.x;
+  const int iy = 1 + blockIdx.y * kBY + threadIdx.y;
+  if (ix > nxf - 2 || iy > nxf - 2) return;
+  const int I0 = ix >> 1, I1 = (ix + 1) >> 1, J0 = iy >> 1, J1 = (iy + 1) >> 1;
+  const int p = ix + nxf * iy;
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    auto E = [&](int I, int J) { return ld<C>(ec + (size_t)(I + nxc * J) * S + i); };
+    C v = C(0.25) * ((E(I0, J0) + E(I1, J0)) + (E(I0, J1) + E(I1, J1)));
+    st(xf + (size_t)p * S + i, ld<C>(xf + (size_t)p * S + i) + v);
+  }
+}
+
+// Right-hand side of one block of the triangular preconditioners:
+// out = v_i - sum_j cj[j] K z_j  (cj[j] = dt a_ij for the stages already solved, else 0).
+template <typename T, typename C, int SF>
+__global__ void __launch_bounds__(kBX* kBY) block_rhs_kernel(int nx, const C* __restrict__ cf,
+                                                             const double* __restrict__ v,
+                                                             const double* __restrict__ z, int i, Vec8 cj,
+                                                             T* __restrict__ out) {
+  const int ix = 1 + blockIdx.x * kBX + threadIdx.x;
+  const int iy = 1 + blockIdx.y * kBY + threadIdx.y;
+  if (ix > nx - 2 || iy > nx - 2) return;
+  const int p = ix + nx * iy;
+  C acc = static_cast<C>(v[(size_t)p * SF + i]);
+#pragma unroll
+  for (int j = 0; j < SF; ++j) {
+    if (cj.v[j] != 0.0) acc -= static_cast<C>(cj.v[j]) * k_apply<SF, C>(cf, z, p, nx, j);
+  }
+  st(out + p, acc);
+}
+
+// z[:, i] = x on interior nodes (single-stage x into an SF-interleaved double vector).
+template <typename T, typename C, int SF>
+__global__ void __launch_bounds__(kBX* kBY) scatter_stage_kernel(int nx, const T* __restrict__ x, int i,
+                                                                 double* __restrict__ z) {
+  const int ix = 1 + blockIdx.x * kBX + threadIdx.x;
+  const int iy = 1 + blockIdx.y * kBY + threadIdx.y;
+  if (ix > nx - 2 || iy > nx - 2) return;
+  const int p = ix + nx * iy;
+  z[(size_t)p * SF + i] = static_cast<double>(ld<C>(x + p));
+}
+
+template <typename T, typename C>
+__global__ void cast_to_kernel(const double* __restrict__ src, T* __restrict__ dst, size_t n) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    st(dst + e, static_cast<C>(src[e]));
+}
+template <typename T, typename C>
+__global__ void cast_from_kernel(const T* __restrict__ src, double* __restrict__ dst, size_t n) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    dst[e] = static_cast<double>(ld<C>(src + e));
+}
+
+// Exact coarsest-level solve x = B_c^{-1} b with a precomputed dense inverse per
+// stage (the paper's multigrid uses a direct coarse solve).  blockIdx.y = stage;
+// one warp per row; the stage's interior right-hand side is staged in shared memory.
+template <typename T, typename C, int S>
+__global__ void coarse_solve_kernel(int nint, const C* __restrict__ binv, const int* __restrict__ map,
+                                    const T* __restrict__ b, T* __restrict__ x) {
+  extern __shared__ unsigned char smem_raw[];
+  C* bs = reinterpret_cast<C*>(smem_raw);
+  const int i = blockIdx.y;
+  for (int c = threadIdx.x; c < nint; c += blockDim.x) bs[c] = ld<C>(b + (size_t)map[c] * S + i);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const C* Bi = binv + (size_t)i * nint * nint;
+  for (int r = blockIdx.x * nw + warp; r < nint; r += gridDim.x * nw) {
+    C acc = 0;
+    const C* row = Bi + (size_t)r * nint;
+    for (int c = lane; c < nint; c += 32) acc += row[c] * bs[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) st(x + (size_t)map[r] * S + i, acc);
+  }
+}
+
+// ----------------------------------------------------------------------------
+// launchers
+// ----------------------------------------------------------------------------
+#define IRK_DISPATCH_S(S, ...)                 \
+  switch (S) {                                 \
+    case 1: { constexpr int SS = 1; __VA_ARGS__; } break; \
+    case 2: { constexpr int SS = 2; __VA_ARGS__; } break; \
+    case 3: { constexpr int SS = 3; __VA_ARGS__; } break; \
+    case 4: { constexpr int SS = 4; __VA_ARGS__; } break; \
+    default: break;                            \
+  }
+
+template <typename T, typename C>
+void MG2<T, C>::jacobi(int S, cudaStream_t st, int nx, const C* cf, double hm, const Vec8& sigma, const C* dinv,
+                       int dstride, const T* xin, const T* b, T* xout) {
+  dim3 g = interior_grid(nx), blk(kBX, kBY);
+  IRK_DISPATCH_S(S, jacobi_kernel<T, C, SS><<<g, blk, 0, st>>>(nx, cf, (C)hm, sigma, dinv, dstride, xin, b, xout));
+}
+template <typename T, typename C>
+void MG2<T, C>::residual(int S, cudaStream_t st, int nx, const C* cf, double hm, const Vec8& sigma, const T* x,
+                         const T* b, T* r) {
+  dim3 g = interior_grid(nx), blk(kBX, kBY);
+  IRK_DISPATCH_S(S, residual_kernel<T, C, SS><<<g, blk, 0, st>>>(nx, cf, (C)hm, sigma, x, b, r));
+}
+template <typename T, typename C>
+void MG2<T, C>::restrict_(int S, cudaStream_t st, int nxf, const T* rf, int nxc, T* bc) {
+  dim3 g = interior_grid(nxc), blk(kBX, kBY);
+  IRK_DISPATCH_S(S, restrict_kernel<T, C, SS><<<g, blk, 0, st>>>(nxf, rf, nxc, bc));
+}
+template <typename T, typename C>
+void MG2<T, C>::prolong_add(int S, cudaStream_t st, int nxc, const T* ec, int nxf, T* xf) {
+  dim3 g = interior_grid(nxf), blk(kBX, kBY);
+  IRK_DISPATCH_S(S, prolong_add_kernel<T, C, SS><<<g, blk, 0, st>>>(nxc, ec, nxf, xf));
+}
+template <typename T, typename C>
+void MG2<T, C>::block_rhs(int SF, cudaStream_t st, int nx, const C* cf, const double* v, const double* z, int i,
+                          const Vec8& cj, T* out) {
+  dim3 g = interior_grid(nx), blk(kBX, kBY);
+  IRK_DISPATCH_S(SF, block_rhs_kernel<T, C, SS><<<g, blk, 0, st>>>(nx, cf, v, z, i, cj, out));
+}
+template <typename T, typename C>
+void MG2<T, C>::scatter_stage(int SF, cudaStream_t st, int nx, const T* x, int i, double* z) {
+  dim3 g = interior_grid(nx), blk(kBX, kBY);
+  IRK_DISPATCH_S(SF, scatter_stage_kernel<T, C, SS><<<g, blk, 0, st>>>(nx, x, i, z));
+}
+template <typename T, typename C>
+void MG2<T, C>::cast_to(cudaStream_t st, const double* src, T* dst, size_t n) {
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  cast_to_kernel<T, C><<<blocks, 256, 0, st>>>(src, dst, n);
+}
+template <typename T, typename C>
+void MG2<T, C>::cast_from(cudaStream_t st, const T* src, double* dst, size_t n) {
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  cast_from_kernel<T, C><<<blocks, 256, 0, st>>>(src, dst, n);
+}
+template <typename T, typename C>
+void MG2<T, C>::coarse_solve(int S, cudaStream_t st, int nint, const C* binv, const int* map, const T* b, T* x) {
+  const int threads = 256, rows_per_block = threads / 32;
+  int gx = (nint + rows_per_block - 1) / rows_per_block;
+  if (gx > 152 * 4) gx = 152 * 4;
+  dim3 g(gx, S);
+  size_t shm = sizeof(C) * (size_t)nint;
+  IRK_DISPATCH_S(S, coarse_solve_kernel<T, C, SS><<<g, threads, shm, st>>>(nint, binv, map, b, x));
+}
+
+}  // namespace irk

@@ -1,0 +1,195 @@
+// FP64 kernels of the outer iteration: the stage operator of Sec. 3,
+// eq. block_struct_AI, the right-hand side of Sec. 2 eq. rkheat, the RK update
+// (Sec. 2) and the pieces of the discrete adjoint step.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace irk {
+
+namespace {
+constexpr int BX = 32, BY = 8;
+
+inline dim3 all_nodes_grid(int nx) { return dim3((nx + BX - 1) / BX, (nx + BY - 1) / BY); }
+
+// (K u)(p) for a caller-supplied nodal vector whose boundary entries must be read as 0.
+__device__ __forceinline__ double k_apply_masked(const double* __restrict__ cf, const double* __restrict__ u, int ix,
+                                                 int iy, int nx) {
+  const int p = ix + nx * iy;
+  auto U = [&](int dx, int dy) {
+    const int jx = ix + dx, jy = iy + dy;
+    return interior2(jx, jy, nx) ? u[jx + nx * jy] : 0.0;
+  };
+  const double* c0 = cf + (size_t)p * kCoef2;
+  const double* cw = cf + (size_t)(p - 1) * kCoef2;
+  const double* cs = cf + (size_t)(p - nx) * kCoef2;
+  const double* csw = cf + (size_t)(p - nx - 1) * kCoef2;
+  const double* cse = cf + (size_t)(p - nx + 1) * kCoef2;
+  double y = c0[0] * U(0, 0);
+  y += c0[1] * U(1, 0) + cw[1] * U(-1, 0);
+  y += c0[2] * U(0, 1) + cs[2] * U(0, -1);
+  y += c0[3] * U(1, 1) + csw[3] * U(-1, -1);
+  y += c0[4] * U(-1, 1) + cse[4] * U(1, -1);
+  return y;
+}
+}  // namespace
+
+// y_i = M x_i + sum_j mix_ij K x_j (mix = dt A or dt A^T) on interior nodes, 0 on the boundary.
+// One load of the S interleaved values per stencil point serves every stage; the
+// S x S mixing stays in registers.
+template <int S>
+__global__ void __launch_bounds__(BX* BY) stage_apply_kernel(int nx, const double* __restrict__ cf, double hm, Mat4 mix,
+                                                             const double* __restrict__ x, double* __restrict__ y) {
+  const int ix = blockIdx.x * BX + threadIdx.x;
+  const int iy = blockIdx.y * BY + threadIdx.y;
+  if (ix >= nx || iy >= nx) return;
+  const int p = ix + nx * iy;
+  if (!interior2(ix, iy, nx)) {
+#pragma unroll
+    for (int i = 0; i < S; ++i) y[(size_t)p * S + i] = 0.0;
+    return;
+  }
+  double kx[S];
+#pragma unroll
+  for (int j = 0; j < S; ++j) kx[j] = k_apply<S, double>(cf, x, p, nx, j);
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    double acc = hm * m_apply_unscaled<S, double>(x, p, nx, i);
+#pragma unroll
+    for (int j = 0; j < S; ++j) acc += mix.v[i * S + j] * kx[j];
+    y[(size_t)p * S + i] = acc;
+  }
+}
+
+// r_i = fcoef_i F^ + F_i - K u_n (Sec. 2 eq. rkheat moved to the right-hand side).
+template <int S>
+__global__ void __launch_bounds__(BX* BY) rhs_kernel(int nx, const double* __restrict__ cf, const double* __restrict__ u,
+                                                     const double* __restrict__ fsp, Vec8 fcoef,
+                                                     const double* __restrict__ fst, double* __restrict__ r) {
+  const int ix = blockIdx.x * BX + threadIdx.x;
+  const int iy = blockIdx.y * BY + threadIdx.y;
+  if (ix >= nx || iy >= nx) return;
+  const int p = ix + nx * iy;
+  if (!interior2(ix, iy, nx)) {
+#pragma unroll
+    for (int i = 0; i < S; ++i) r[(size_t)p * S + i] = 0.0;
+    return;
+  }
+  const double ku = (u != nullptr) ? k_apply_masked(cf, u, ix, iy, nx) : 0.0;
+  const double f = (fsp != nullptr) ? fsp[p] : 0.0;
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    double v = fcoef.v[i] * f - ku;
+    if (fst != nullptr) v += fst[(size_t)p * S + i];
+    r[(size_t)p * S + i] = v;
+  }
+}
+
+// u_{n+1} = u_n + sum_i (dt b_i) k_i on interior nodes, 0 on the boundary.
+template <int S>
+__global__ void rk_update_kernel(int nx, const double* __restrict__ u, const double* __restrict__ k, Vec8 bdt,
+                                 double* __restrict__ out) {
+  const int ix = blockIdx.x * BX + threadIdx.x;
+  const int iy = blockIdx.y * BY + threadIdx.y;
+  if (ix >= nx || iy >= nx) return;
+  const int p = ix + nx * iy;
+  double v = 0.0;
+  if (interior2(ix, iy, nx)) {
+    v = u[p];
+#pragma unroll
+    for (int i = 0; i < S; ++i) v += bdt.v[i] * k[(size_t)p * S + i];
+  }
+  out[p] = v;
+}
+
+// lam_n = lam_{n+1} - K sum_i mu_i (interior), 0 on the boundary.
+template <int S>
+__global__ void adjoint_lambda_kernel(int nx, const double* __restrict__ cf, const double* __restrict__ lam1,
+                                      const double* __restrict__ mu, double* __restrict__ lam0) {
+  const int ix = blockIdx.x * BX + threadIdx.x;
+  const int iy = blockIdx.y * BY + threadIdx.y;
+  if (ix >= nx || iy >= nx) return;
+  const int p = ix + nx * iy;
+  double v = 0.0;
+  if (interior2(ix, iy, nx)) {
+    double kmu = 0.0;
+#pragma unroll
+    for (int i = 0; i < S; ++i) kmu += k_apply<S, double>(cf, mu, p, nx, i);
+    v = lam1[p] - kmu;
+  }
+  lam0[p] = v;
+}
+
+// grad[c] += -kappa_c sum_i mu_i|_c^T K_e U_i|_c, U_i = u_n + sum_j (dt a_ij) k_j, with the
+// unit-diffusivity bilinear element matrix K_e = [[4,-1,-1,-2],[-1,4,-2,-1],[-1,-2,4,-1],[-2,-1,-1,4]]/6
+// (corners ordered (0,0), (1,0), (0,1), (1,1)).  One thread per cell, no atomics.
+template <int S>
+__global__ void cell_gradient_kernel(int N, const double* __restrict__ kappa, const double* __restrict__ u,
+                                     const double* __restrict__ k, Mat4 dtA, const double* __restrict__ mu,
+                                     double* __restrict__ grad) {
+  const int cx = blockIdx.x * BX + threadIdx.x;
+  const int cy = blockIdx.y * BY + threadIdx.y;
+  if (cx >= N || cy >= N) return;
+  const int nx = N + 1;
+  int q[4], qx[4], qy[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    qx[a] = cx + (a & 1);
+    qy[a] = cy + (a >> 1);
+    q[a] = qx[a] + nx * qy[a];
+  }
+  double total = 0.0;
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    double U[4], m[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const bool in = interior2(qx[a], qy[a], nx);
+      double v = in ? u[q[a]] : 0.0;
+#pragma unroll
+      for (int j = 0; j < S; ++j) v += dtA.v[i * S + j] * k[(size_t)q[a] * S + j];
+      U[a] = in ? v : 0.0;
+      m[a] = in ? mu[(size_t)q[a] * S + i] : 0.0;
+    }
+    const double KU0 = 4 * U[0] - U[1] - U[2] - 2 * U[3];
+    const double KU1 = -U[0] + 4 * U[1] - 2 * U[2] - U[3];
+    const double KU2 = -U[0] - 2 * U[1] + 4 * U[2] - U[3];
+    const double KU3 = -2 * U[0] - U[1] - U[2] + 4 * U[3];
+    total += m[0] * KU0 + m[1] * KU1 + m[2] * KU2 + m[3] * KU3;
+  }
+  const int c = cx + N * cy;
+  const double kap = (kappa != nullptr) ? kappa[c] : 1.0;
+  grad[c] += -kap * total / 6.0;
+}
+
+#define IRK_DISPATCH_S(S, ...)                                \
+  switch (S) {                                                \
+    case 1: { constexpr int SS = 1; __VA_ARGS__; } break;     \
+    case 2: { constexpr int SS = 2; __VA_ARGS__; } break;     \
+    case 3: { constexpr int SS = 3; __VA_ARGS__; } break;     \
+    case 4: { constexpr int SS = 4; __VA_ARGS__; } break;     \
+    default: break;                                           \
+  }
+
+void launch_stage_apply(int S, cudaStream_t st, int nx, const double* cf, double hm, const Mat4& mix, const double* x,
+                        double* y) {
+  IRK_DISPATCH_S(S, stage_apply_kernel<SS><<<all_nodes_grid(nx), dim3(BX, BY), 0, st>>>(nx, cf, hm, mix, x, y));
+}
+void launch_rhs(int S, cudaStream_t st, int nx, const double* cf, const double* u, const double* fsp,
+                const Vec8& fcoef, const double* fst, double* r) {
+  IRK_DISPATCH_S(S, rhs_kernel<SS><<<all_nodes_grid(nx), dim3(BX, BY), 0, st>>>(nx, cf, u, fsp, fcoef, fst, r));
+}
+void launch_rk_update(int S, cudaStream_t st, int nx, const double* u, const double* k, const Vec8& bdt,
+                      double* out) {
+  IRK_DISPATCH_S(S, rk_update_kernel<SS><<<all_nodes_grid(nx), dim3(BX, BY), 0, st>>>(nx, u, k, bdt, out));
+}
+void launch_adjoint_lambda(int S, cudaStream_t st, int nx, const double* cf, const double* lam_np1, const double* mu,
+                           double* lam_n) {
+  IRK_DISPATCH_S(S, adjoint_lambda_kernel<SS><<<all_nodes_grid(nx), dim3(BX, BY), 0, st>>>(nx, cf, lam_np1, mu, lam_n));
+}
+void launch_cell_gradient(int S, cudaStream_t st, int N, const double* kappa, const double* u, const double* k,
+                          const Mat4& dtA, const double* mu, double* grad) {
+  dim3 g((N + BX - 1) / BX, (N + BY - 1) / BY);
+  IRK_DISPATCH_S(S, cell_gradient_kernel<SS><<<g, dim3(BX, BY), 0, st>>>(N, kappa, u, k, dtA, mu, grad));
+}
+
+}  // namespace irk
