@@ -147,6 +147,22 @@ int irk_apply_preconditioner(irk_handle* h, const double* v, double* z, int tran
 int irk_step_adjoint(irk_handle* h, const double* u_n, const double* stages, const double* lam_np1,
                      double* lam_n, double* grad_accum, irk_stats* stats);
 
+/* z = P^{-1} v like irk_apply_preconditioner, for callers that cannot allocate
+ * device memory when they apply it (for example while a stream is being captured
+ * into a CUDA graph, or on threads that must not touch the allocator).  The paper
+ * has no counterpart; it is an interface convenience.
+ *   v, z       device pointers (host pointers are rejected: staging would allocate).
+ * The V-cycle level vectors live in one static device array of 16 MiB shared by
+ * every call in the process (each GPU that loads the library holds it until exit);
+ * handles whose V-cycle needs more scratch than that are rejected with IRK_EINVAL.
+ * The first call on a device looks up the array's device address (no allocation);
+ * make that first call before any stream capture.  Each call clears the part of
+ * the array it uses, so results never depend on earlier calls, but calls that
+ * overlap on the GPU (other streams, other threads, other handles) race on the
+ * shared array and must be serialised by the caller.  Allocates no device memory:
+ * calls no cudaMalloc, cudaFree or other allocating CUDA or torch routine. */
+int irk_apply_preconditioner_noalloc(irk_handle* h, const double* v, double* z, int transpose);
+
 /* Kernel classes counted by the built-in instrumentation. */
 #define IRK_K_STAGE_APPLY 0 /* stage operator (FP64)                        */
 #define IRK_K_JACOBI 1      /* weighted-Jacobi sweep                         */

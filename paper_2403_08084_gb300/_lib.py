@@ -81,6 +81,7 @@ _SIGNATURES = {
     "irk_solve": (C.c_int, [_P, _P, _P, C.POINTER(irk_stats)]),
     "irk_apply_operator": (C.c_int, [_P, _P, _P, C.c_int]),
     "irk_apply_preconditioner": (C.c_int, [_P, _P, _P, C.c_int]),
+    "irk_apply_preconditioner_noalloc": (C.c_int, [_P, _P, _P, C.c_int]),
     "irk_step_adjoint": (C.c_int, [_P, _P, _P, _P, _P, _P, C.POINTER(irk_stats)]),
     "irk_perf_select": (C.c_int, [_P, C.c_uint]),
     "irk_perf_read": (C.c_int, [_P, C.POINTER(irk_perf)]),

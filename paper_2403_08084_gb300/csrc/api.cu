@@ -10,6 +10,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <type_traits>
@@ -939,3 +940,89 @@ int irk_step_adjoint(irk_handle* h, const double* u_n, const double* stages, con
 }
 
 }  // extern "C"
+
+// ============================================================================
+// Preconditioner application that allocates nothing.
+//
+// Some callers cannot allocate device memory at the time they apply the
+// preconditioner: code running while a stream is being captured into a CUDA
+// graph (cudaMalloc is not allowed there), host threads that must not touch the
+// allocator (real-time loops, allocators owned by another framework), or
+// embeddings that hand the library a fixed memory budget.  For them,
+// irk_apply_preconditioner_noalloc runs the same V-cycle preconditioner as
+// irk_apply_preconditioner, but its multigrid level vectors live in one
+// file-scope device array of kNoAllocScratchBytes (16 MiB) instead of the
+// handle's buffers.  Every GPU that loads the library holds that array until
+// the process exits.
+// ============================================================================
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mutex;
+void* g_noalloc_device_ptr[256] = {};  // device address of g_noalloc_scratch, per device ordinal
+
+// In host code g_noalloc_scratch only names a host-side stand-in, so the
+// device address is fetched once per device (with that device current) and
+// cached; this is the only set-up the entry point does.
+int noalloc_scratch_address(void** out) {
+  int dev = -1;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) return fail(IRK_EINVAL, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (g_noalloc_device_ptr[dev] == nullptr) {
+    void* p = nullptr;
+    CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_device_ptr[dev] = p;
+  }
+  *out = g_noalloc_device_ptr[dev];
+  return IRK_OK;
+}
+
+inline size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
+
+}  // namespace
+
+extern "C" int irk_apply_preconditioner_noalloc(irk_handle* h, const double* v, double* z, int transpose) {
+  if (!h || !v || !z) return fail(IRK_EINVAL, "null argument");
+  if (!is_device_ptr(v) || !is_device_ptr(z))
+    return fail(IRK_EINVAL, "irk_apply_preconditioner_noalloc takes device pointers only");
+  // scratch layout: four level vectors (xa, xb, b, r) per level, 256-byte aligned
+  const size_t vb = prec_bytes(h->opt.vcycle_prec);
+  size_t need = 0;
+  for (const Level& Lv : h->lev) need += 4 * align256(Lv.nn * (size_t)h->s * vb);
+  if (need > kNoAllocScratchBytes)
+    return fail(IRK_EINVAL, "this handle's V-cycle needs %zu bytes of scratch; the no-allocation entry point has %zu",
+                need, kNoAllocScratchBytes);
+  void* base = nullptr;
+  TRY(noalloc_scratch_address(&base));
+  // the array keeps the previous call's contents: level vectors must start with zero boundaries
+  CK(cudaMemsetAsync(base, 0, need, h->st));
+  CK(cudaMemsetAsync(z, 0, h->ne * 8, h->st));
+  // lend the scratch to the handle's levels for this call; instrumentation timing is
+  // switched off because it may create CUDA events
+  void* saved[16][4];  // levels <= 14 (validated at create)
+  for (size_t l = 0; l < h->lev.size(); ++l) {
+    saved[l][0] = h->lev[l].xa, saved[l][1] = h->lev[l].xb, saved[l][2] = h->lev[l].b, saved[l][3] = h->lev[l].r;
+  }
+  const unsigned saved_mask = h->perf_mask;
+  unsigned char* cur = static_cast<unsigned char*>(base);
+  for (Level& Lv : h->lev) {
+    const size_t bytes = align256(Lv.nn * (size_t)h->s * vb);
+    Lv.xa = cur, cur += bytes;
+    Lv.xb = cur, cur += bytes;
+    Lv.b = cur, cur += bytes;
+    Lv.r = cur, cur += bytes;
+  }
+  h->perf_mask = 0;
+  h->vcycles = 0;
+  const int rc = precond(h, v, z, transpose != 0);
+  for (size_t l = 0; l < h->lev.size(); ++l) {
+    h->lev[l].xa = saved[l][0], h->lev[l].xb = saved[l][1], h->lev[l].b = saved[l][2], h->lev[l].r = saved[l][3];
+  }
+  h->perf_mask = saved_mask;
+  if (rc != IRK_OK) return rc;
+  CK(cudaStreamSynchronize(h->st));
+  return IRK_OK;
+}
