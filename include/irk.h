@@ -53,6 +53,11 @@ extern "C" {
 #define IRK_PC_LOWER 1 /* P_L = I (x) M + dt (L + D) (x) K    (eq. pcbgs, AI form)    */
 #define IRK_PC_UPPER 2 /* P_U = I (x) M + dt (U + D) (x) K    (Sec. 3.1)              */
 
+/* Arnoldi orthogonalisation (the paper does not fix one) */
+#define IRK_ORTH_CGS2 0 /* classical Gram-Schmidt, always two passes                       */
+#define IRK_ORTH_DGKS 1 /* classical Gram-Schmidt, second pass only when ||w'|| < ||w||/sqrt(2)
+                           (Daniel-Gragg-Kaufman-Stewart test), norm by Pythagoras otherwise   */
+
 /* storage / arithmetic of the multigrid V-cycles inside the FP64 FGMRES */
 #define IRK_PREC_FP64 0 /* vectors and arithmetic in double                         */
 #define IRK_PREC_FP32 1 /* vectors and arithmetic in float                          */
@@ -85,6 +90,7 @@ typedef struct {
   double rtol;      /* stop when ||r_j||_2 <= rtol ||r_0||_2 (default 1e-10) */
   int restart;      /* FGMRES restart length m (default 50) */
   int maxit;        /* total FGMRES iterations allowed per solve (default 500) */
+  int orth;         /* IRK_ORTH_* (default IRK_ORTH_CGS2) */
 } irk_options;
 
 typedef struct {
@@ -94,7 +100,7 @@ typedef struct {
   int converged;    /* 1 if rel_resid <= rtol */
 } irk_stats;
 
-/* Fill *opt with the defaults listed above (P_L, FP64 V-cycles). */
+/* Fill *opt with the defaults listed above (P_L, FP64 V-cycles, CGS2 Arnoldi). */
 void irk_default_options(irk_options* opt);
 
 /* Build a solver for one mesh, tableau and step size (Sec. 3, eq. block_struct_AI).

@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -64,6 +65,7 @@ struct Level {
   std::vector<double> cf_host;
   double* cf_d = nullptr;     // stencil records, double
   float* cf_f = nullptr;      // stencil records, float
+  double* brec_d = nullptr;   // FP64 V-cycles: records of M + dt a_ii K, stage-major
   double* dinv_d = nullptr;   // omega / diag, s per node
   float* dinv_f = nullptr;
   void* xa = nullptr;         // V-cycle vectors (s per node, V-cycle precision)
@@ -99,10 +101,20 @@ struct irk_handle {
   double* Z = nullptr;
   double *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr;
   double *h1 = nullptr, *h2 = nullptr, *partial = nullptr, *scal = nullptr;
+  int* iflag = nullptr;  // device flags (re-orthogonalisation decision)
   double* pinned = nullptr;  // host-visible copies of the residual estimate
   double *rhs = nullptr, *k = nullptr, *tmp = nullptr;
   DevBuf stage_bufs[8];
   int vcycles = 0;
+  // one CUDA graph per FGMRES iteration index j and direction (captured on first use)
+  struct IterGraph {
+    cudaGraphExec_t exec = nullptr;
+    irk_perf delta{};
+    int vcycles = 0;
+  };
+  std::vector<IterGraph> graphs[2];
+  cudaStream_t cap_stream = nullptr;
+  bool use_graphs = true;
   // instrumentation
   irk_perf perf{};
   unsigned perf_mask = 0;
@@ -299,6 +311,7 @@ int validate(const irk_mesh* mesh, const irk_tableau* tab, double dt, const irk_
   if (!(opt->rtol > 0.0 && opt->rtol < 1.0)) return fail(IRK_EINVAL, "rtol = %g not in (0, 1)", opt->rtol);
   if (opt->restart < 1 || opt->restart > 100) return fail(IRK_EINVAL, "restart = %d not in [1, 100]", opt->restart);
   if (opt->maxit < 1) return fail(IRK_EINVAL, "maxit = %d < 1", opt->maxit);
+  if (opt->orth != IRK_ORTH_CGS2 && opt->orth != IRK_ORTH_DGKS) return fail(IRK_EINVAL, "bad orth %d", opt->orth);
   return IRK_OK;
 }
 
@@ -320,6 +333,11 @@ int build_operators(irk_handle* h) {
     CK(cudaMemcpyAsync(Lv.dinv_d, dinv.data(), dinv.size() * 8, cudaMemcpyHostToDevice, h->st));
     CK(cudaMemcpyAsync(Lv.cf_f, cff.data(), cff.size() * 4, cudaMemcpyHostToDevice, h->st));
     CK(cudaMemcpyAsync(Lv.dinv_f, dinvf.data(), dinvf.size() * 4, cudaMemcpyHostToDevice, h->st));
+    std::vector<double> brec;
+    if (Lv.brec_d) {
+      block_records_2d(Lv.N, Lv.cf_host, Lv.hm, sigma.data(), s, brec);
+      CK(cudaMemcpyAsync(Lv.brec_d, brec.data(), brec.size() * 8, cudaMemcpyHostToDevice, h->st));
+    }
     CK(cudaStreamSynchronize(h->st));  // host vectors above go out of scope
   }
   // exact coarsest solve: dense inverse of each diagonal block
@@ -346,15 +364,19 @@ int build_operators(irk_handle* h) {
 void destroy(irk_handle* h) {
   if (!h) return;
   for (Level& Lv : h->lev) {
-    dfree(Lv.cf_d), dfree(Lv.cf_f), dfree(Lv.dinv_d), dfree(Lv.dinv_f);
+    dfree(Lv.cf_d), dfree(Lv.cf_f), dfree(Lv.brec_d), dfree(Lv.dinv_d), dfree(Lv.dinv_f);
     dfree(Lv.xa), dfree(Lv.xb), dfree(Lv.b), dfree(Lv.r);
   }
   dfree(h->cmap), dfree(h->binv_d), dfree(h->binv_f), dfree(h->kappa_d);
   dfree(h->V), dfree(h->Z), dfree(h->H), dfree(h->cs), dfree(h->sn), dfree(h->g), dfree(h->y);
-  dfree(h->h1), dfree(h->h2), dfree(h->partial), dfree(h->scal);
+  dfree(h->h1), dfree(h->h2), dfree(h->partial), dfree(h->scal), dfree(h->iflag);
   dfree(h->rhs), dfree(h->k), dfree(h->tmp);
   for (DevBuf& b : h->stage_bufs) dfree(b.p);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+  for (auto& gv : h->graphs)
+    for (auto& G : gv)
+      if (G.exec) cudaGraphExecDestroy(G.exec);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->pinned) cudaFreeHost(h->pinned);
   delete h;
 }
@@ -390,6 +412,7 @@ int create(irk_handle** out, const irk_mesh* mesh, const irk_tableau* tab, doubl
     const double hh = 1.0 / Lv.N;
     Lv.hm = hh * hh / 36.0;
     int r = IRK_OK;
+    if (opt->vcycle_prec == IRK_PREC_FP64 && (r = dalloc(&Lv.brec_d, Lv.nn * kCoef2 * s * 8))) return bail(r);
     if ((r = dalloc(&Lv.cf_d, Lv.nn * kCoef2 * 8)) || (r = dalloc(&Lv.cf_f, Lv.nn * kCoef2 * 4)) ||
         (r = dalloc(&Lv.dinv_d, Lv.nn * s * 8)) || (r = dalloc(&Lv.dinv_f, Lv.nn * s * 4)) ||
         (r = dalloc(&Lv.xa, Lv.nn * s * vb)) || (r = dalloc(&Lv.xb, Lv.nn * s * vb)) ||
@@ -415,7 +438,7 @@ int create(irk_handle** out, const irk_mesh* mesh, const irk_tableau* tab, doubl
       (r = dalloc(&h->H, (m + 1) * m * 8)) || (r = dalloc(&h->cs, m * 8)) || (r = dalloc(&h->sn, m * 8)) ||
       (r = dalloc(&h->g, (m + 1) * 8)) || (r = dalloc(&h->y, m * 8)) || (r = dalloc(&h->h1, (m + 1) * 8)) ||
       (r = dalloc(&h->h2, (m + 1) * 8)) ||
-      (r = dalloc(&h->partial, (m + 1) * (size_t)krylov_partial_blocks() * 8)) || (r = dalloc(&h->scal, 16 * 8)) ||
+      (r = dalloc(&h->partial, (m + 1) * (size_t)krylov_partial_blocks() * 8)) || (r = dalloc(&h->scal, 16 * 8)) || (r = dalloc(&h->iflag, 16 * sizeof(int))) ||
       (r = dalloc(&h->rhs, ne * 8)) || (r = dalloc(&h->k, ne * 8)) || (r = dalloc(&h->tmp, ne * 8)))
     return bail(r);
   if (cudaMemsetAsync(h->V, 0, (m + 1) * ne * 8, h->st) || cudaMemsetAsync(h->Z, 0, m * ne * 8, h->st) ||
@@ -426,6 +449,13 @@ int create(irk_handle** out, const irk_mesh* mesh, const irk_tableau* tab, doubl
     return bail(fail(IRK_ENOMEM, "cudaMallocHost failed"));
   }
   if ((r = build_operators(h)) != IRK_OK) return bail(r);
+  if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(fail(IRK_ECUDA, "cudaStreamCreateWithFlags failed"));
+  }
+  h->graphs[0].resize(h->m);
+  h->graphs[1].resize(h->m);
+  if (const char* e = getenv("IRK_NO_GRAPHS")) h->use_graphs = (e[0] == '\0' || e[0] == '0');
   *out = h;
   return IRK_OK;
 }
@@ -437,18 +467,21 @@ template <typename T, typename C>
 struct Prec;
 template <>
 struct Prec<double, double> {
+  static const double* rec(const Level& L) { return L.brec_d; }
   static const double* cf(const Level& L) { return L.cf_d; }
   static const double* dinv(const Level& L) { return L.dinv_d; }
   static const double* binv(const irk_handle* h) { return h->binv_d; }
 };
 template <>
 struct Prec<float, float> {
+  static const float* rec(const Level&) { return nullptr; }
   static const float* cf(const Level& L) { return L.cf_f; }
   static const float* dinv(const Level& L) { return L.dinv_f; }
   static const float* binv(const irk_handle* h) { return h->binv_f; }
 };
 template <>
 struct Prec<__nv_bfloat16, float> {
+  static const float* rec(const Level&) { return nullptr; }
   static const float* cf(const Level& L) { return L.cf_f; }
   static const float* dinv(const Level& L) { return L.dinv_f; }
   static const float* binv(const irk_handle* h) { return h->binv_f; }
@@ -470,9 +503,13 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2) {
   std::vector<T*> cur(L, nullptr);
   auto sweep = [&](Level& Lv, const C* cf, const C* dinv, const T* xin, const T* b, T* xout) {
     const double n = n_int(Lv.nx);
+    const C* rec = P::rec(Lv);
     if (xin == nullptr) {
       KScope k(h, IRK_K_JACOBI, n * S * (2 * p + c), n * S);
       MG::jacobi(S, st, Lv.nx, cf, Lv.hm, sig, dinv, s, xin, b, xout);
+    } else if (rec != nullptr) {  // B_i records: 9 products + 2 per node and stage
+      KScope k(h, IRK_K_JACOBI, n * S * (3 * p + c + kCoef2 * c), 20.0 * n * S);
+      MG::jacobi_rec(S, st, Lv.nx, rec + (size_t)st0 * Lv.nn * kCoef2, Lv.nn * kCoef2, dinv, s, xin, b, xout);
     } else {
       KScope k(h, IRK_K_JACOBI, n * (S * (3 * p + c) + kCoef2 * c), 33.0 * n * S);
       MG::jacobi(S, st, Lv.nx, cf, Lv.hm, sig, dinv, s, xin, b, xout);
@@ -497,7 +534,10 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2) {
     for (int k = 1; k < nu1; ++k, w ^= 1) sweep(Lv, cf, dinv, bufs[w], bl, bufs[w ^ 1]);
     cur[l] = bufs[w];
     const double nf = n_int(Lv.nx), nc = n_int(Lc.nx);
-    {
+    if (const C* rec = P::rec(Lv)) {
+      KScope k(h, IRK_K_RESIDUAL, nf * S * (3 * p + kCoef2 * c), 18.0 * nf * S);
+      MG::residual_rec(S, st, Lv.nx, rec + (size_t)st0 * Lv.nn * kCoef2, Lv.nn * kCoef2, cur[l], bl, (T*)Lv.r);
+    } else {
       KScope k(h, IRK_K_RESIDUAL, nf * (3 * S * p + kCoef2 * c), 31.0 * nf * S);
       MG::residual(S, st, Lv.nx, cf, Lv.hm, sig, cur[l], bl, (T*)Lv.r);
     }
@@ -654,14 +694,137 @@ int norm2(irk_handle* h, const double* v, int slot) {
 // ----------------------------------------------------------------------------
 // FGMRES (right preconditioned, CGS2 Arnoldi, Givens on the device)
 // ----------------------------------------------------------------------------
+// One Arnoldi step of FGMRES for basis index j: z_j = P^{-1} v_j, w = S z_j,
+// orthogonalisation, Givens update and normalisation; ends by copying
+// (|g_{j+1}| / r0, h_{j+1,j}) to pinned host memory.  Uses only device pointers
+// and values fixed for the handle, so it can be captured into a CUDA graph.
+int arnoldi_step(irk_handle* h, int j, bool transpose) {
+  cudaStream_t st = h->st;
+  const size_t ne = h->ne;
+  const int ldh = h->m + 1;
+  double* vj = h->V + (size_t)j * ne;
+  double* zj = h->Z + (size_t)j * ne;
+  double* w = h->V + (size_t)(j + 1) * ne;
+  double* r0p = h->scal + 9;
+  TRY(precond(h, vj, zj, transpose));
+  TRY(apply_operator(h, zj, w, transpose));
+  if (h->opt.orth == IRK_ORTH_CGS2) {
+    // classical Gram-Schmidt, twice
+    multidot(h, h->V, ne, j + 1, w, h->h1);
+    multi_axpy(h, w, h->V, ne, j + 1, h->h1, -1.0);
+    multidot(h, h->V, ne, j + 1, w, h->h2);
+    multi_axpy(h, w, h->V, ne, j + 1, h->h2, -1.0);
+    // ||w||^2 -> scal[3]; Givens (hn -> scal[4], rel -> scal[5], hn -> scal[6]); w /= ||w||
+    multidot(h, w, 0, 1, w, h->scal + 3);
+    {
+      KScope k(h, IRK_K_OTHER, 0, 0);
+      launch_givens(st, j, ldh, h->H, h->cs, h->sn, h->g, h->h1, h->h2, h->scal + 3, h->scal + 4, r0p, h->scal + 5);
+    }
+    scale(h, w, w, h->scal + 4);
+  } else {
+    // one pass with ||w||^2 (V_{j+1} is w itself), DGKS test, normalisation fused
+    multidot(h, h->V, ne, j + 2, w, h->h1);
+    {
+      KScope k(h, IRK_K_OTHER, 0, 0);
+      launch_orth_decide(st, j, h->h1, h->h2, 0.5, h->iflag, h->scal + 3, h->scal + 8);
+    }
+    {
+      const double n = (double)ne;
+      KScope k(h, IRK_K_AXPY, (j + 3.0) * n * 8, 2.0 * (j + 1) * n);
+      launch_multi_axpy(st, w, h->V, ne, j + 1, h->h1, -1.0, ne, h->scal + 8);
+    }
+    {  // second pass, only when the test asked for it (these kernels return at once otherwise)
+      KScope k1(h, IRK_K_OTHER, 0, 0);
+      launch_multidot(st, h->V, ne, j + 1, w, ne, h->partial, h->iflag);
+      KScope k2(h, IRK_K_OTHER, 0, 0);
+      launch_reduce_partials(st, h->partial, j + 1, h->h2, h->iflag);
+      KScope k3(h, IRK_K_OTHER, 0, 0);
+      launch_multi_axpy(st, w, h->V, ne, j + 1, h->h2, -1.0, ne, nullptr, h->iflag);
+      KScope k4(h, IRK_K_OTHER, 0, 0);
+      launch_multidot(st, w, 0, 1, w, ne, h->partial, h->iflag);
+      KScope k5(h, IRK_K_OTHER, 0, 0);
+      launch_reduce_partials(st, h->partial, 1, h->scal + 3, h->iflag);
+    }
+    {
+      KScope k(h, IRK_K_OTHER, 0, 0);
+      launch_givens(st, j, ldh, h->H, h->cs, h->sn, h->g, h->h1, h->h2, h->scal + 3, h->scal + 4, r0p, h->scal + 5);
+    }
+    KScope k(h, IRK_K_OTHER, 0, 0);
+    launch_scale(st, w, w, h->scal + 4, ne, h->iflag);
+  }
+  CK_LAUNCH();
+  CK(cudaMemcpyAsync(h->pinned + 2, h->scal + 5, 16, cudaMemcpyDeviceToHost, st));
+  return IRK_OK;
+}
+
+// Capture arnoldi_step(j) on the private capture stream and instantiate it.  The
+// instrumentation counters the capture produced are kept as the graph's per-replay
+// increment (the capture itself runs nothing).
+int capture_arnoldi_step(irk_handle* h, int j, bool transpose) {
+  auto& G = h->graphs[transpose ? 1 : 0][j];
+  const irk_perf before = h->perf;
+  const int vc_before = h->vcycles;
+  cudaStream_t saved = h->st;
+  h->st = h->cap_stream;
+  cudaError_t e = cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    h->st = saved;
+    return fail(IRK_ECUDA, "cudaStreamBeginCapture failed: %s", cudaGetErrorString(e));
+  }
+  const int rc = arnoldi_step(h, j, transpose);
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(h->st, &graph);
+  h->st = saved;
+  if (rc != IRK_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return fail(IRK_ECUDA, "cudaStreamEndCapture failed: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&G.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    G.exec = nullptr;
+    return fail(IRK_ECUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(e));
+  }
+  irk_perf d{};
+  d.launches = h->perf.launches - before.launches;
+  for (int c = 0; c < IRK_K_COUNT; ++c) {
+    d.class_launches[c] = h->perf.class_launches[c] - before.class_launches[c];
+    d.class_bytes[c] = h->perf.class_bytes[c] - before.class_bytes[c];
+    d.class_flops[c] = h->perf.class_flops[c] - before.class_flops[c];
+  }
+  G.delta = d;
+  G.vcycles = h->vcycles - vc_before;
+  h->perf = before;
+  h->vcycles = vc_before;
+  return IRK_OK;
+}
+
+// Run Arnoldi step j: replay its graph (eager launches while kernels are being timed).
+int run_arnoldi_step(irk_handle* h, int j, bool transpose) {
+  if (!h->use_graphs || h->perf_mask != 0) return arnoldi_step(h, j, transpose);
+  auto& G = h->graphs[transpose ? 1 : 0][j];
+  if (!G.exec) TRY(capture_arnoldi_step(h, j, transpose));
+  CK(cudaGraphLaunch(G.exec, h->st));
+  h->perf.launches += G.delta.launches;
+  for (int c = 0; c < IRK_K_COUNT; ++c) {
+    h->perf.class_launches[c] += G.delta.class_launches[c];
+    h->perf.class_bytes[c] += G.delta.class_bytes[c];
+    h->perf.class_flops[c] += G.delta.class_flops[c];
+  }
+  h->vcycles += G.vcycles;
+  return IRK_OK;
+}
+
 int fgmres(irk_handle* h, const double* rhs, double* x, bool transpose, irk_stats* stats) {
   cudaStream_t st = h->st;
   const size_t ne = h->ne;
   const int m = h->m, ldh = m + 1;
   h->vcycles = 0;
   CK(cudaMemsetAsync(x, 0, ne * 8, st));
-  // beta = ||rhs||; scal[0] = beta, scal[1] = beta^2
+  // beta = ||rhs||; scal[0] = beta, scal[1] = beta^2; r0 kept in scal[9]
   TRY(norm2(h, rhs, 0));
+  CK(cudaMemcpyAsync(h->scal + 9, h->scal, 8, cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(h->pinned, h->scal, 8, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   const double r0 = h->pinned[0];
@@ -678,25 +841,7 @@ int fgmres(irk_handle* h, const double* rhs, double* x, bool transpose, irk_stat
     }
     int J = 0;
     for (int j = 0; j < m; ++j) {
-      double* vj = h->V + (size_t)j * ne;
-      double* zj = h->Z + (size_t)j * ne;
-      double* w = h->V + (size_t)(j + 1) * ne;
-      TRY(precond(h, vj, zj, transpose));
-      TRY(apply_operator(h, zj, w, transpose));
-      // classical Gram-Schmidt, twice
-      multidot(h, h->V, ne, j + 1, w, h->h1);
-      multi_axpy(h, w, h->V, ne, j + 1, h->h1, -1.0);
-      multidot(h, h->V, ne, j + 1, w, h->h2);
-      multi_axpy(h, w, h->V, ne, j + 1, h->h2, -1.0);
-      // ||w||^2 -> scal[3]; Givens (hn -> scal[4], rel -> scal[5], hn -> scal[6]); w /= ||w||
-      multidot(h, w, 0, 1, w, h->scal + 3);
-      {
-        KScope k(h, IRK_K_OTHER, 0, 0);
-        launch_givens(st, j, ldh, h->H, h->cs, h->sn, h->g, h->h1, h->h2, h->scal + 3, h->scal + 4, r0, h->scal + 5);
-      }
-      scale(h, w, w, h->scal + 4);
-      CK_LAUNCH();
-      CK(cudaMemcpyAsync(h->pinned + 2, h->scal + 5, 16, cudaMemcpyDeviceToHost, st));
+      TRY(run_arnoldi_step(h, j, transpose));
       CK(cudaStreamSynchronize(st));
       rel = h->pinned[2];
       const double hn = h->pinned[3];
@@ -750,6 +895,7 @@ void irk_default_options(irk_options* o) {
   o->rtol = 1e-10;
   o->restart = 50;
   o->maxit = 500;
+  o->orth = IRK_ORTH_CGS2;
 }
 
 const char* irk_last_error(void) { return g_err.c_str(); }

@@ -109,6 +109,16 @@ void galerkin_coarsen_2d(int Nf, const std::vector<double>& cff, std::vector<dou
   }
 }
 
+void block_records_2d(int N, const std::vector<double>& cf, double hm, const double* sigma, int S,
+                      std::vector<double>& rec) {
+  const size_t nn = (size_t)(N + 1) * (N + 1);
+  rec.assign(nn * kRec * S, 0.0);
+  const double mass[kRec] = {16.0 * hm, 4.0 * hm, 4.0 * hm, hm, hm};  // D, E, N, NE, NW
+  for (int i = 0; i < S; ++i)
+    for (size_t p = 0; p < nn; ++p)
+      for (int k = 0; k < kRec; ++k) rec[((size_t)i * nn + p) * kRec + k] = mass[k] + sigma[i] * cf[p * kRec + k];
+}
+
 void jacobi_inverse_diag_2d(int N, const std::vector<double>& cf, double hm, const double* sigma, int S,
                             double omega, std::vector<double>& dinv) {
   const int nx = N + 1;

@@ -14,6 +14,11 @@ void stiffness_records_2d(int N, const double* kappa, std::vector<double>& cf);
 // grid) from fine records with Nf cells per axis to Nf/2.
 void galerkin_coarsen_2d(int Nf, const std::vector<double>& cff, std::vector<double>& cfc);
 
+// Stencil records of B_i = M + sigma_i K for each stage, stage-major
+// (S blocks of (N+1)^2 records); M is the Q1 mass stencil hm [1 4 1; 4 16 4; 1 4 1].
+void block_records_2d(int N, const std::vector<double>& cf, double hm, const double* sigma, int S,
+                      std::vector<double>& rec);
+
 // omega / diag(M + sigma_i K) at interior nodes (0 on the boundary), node-major
 // with S values per node; hm = h^2/36.
 void jacobi_inverse_diag_2d(int N, const std::vector<double>& cf, double hm, const double* sigma, int S,

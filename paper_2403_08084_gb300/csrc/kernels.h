@@ -18,6 +18,11 @@ struct MG2 {
                      int dstride, const T* xin, const T* b, T* xout);
   static void residual(int S, cudaStream_t st, int nx, const C* cf, double hm, const Vec8& sigma, const T* x,
                        const T* b, T* r);
+  // the same with B_i = M + sigma_i K stored per stage (stage-major records, stride rstride)
+  static void jacobi_rec(int S, cudaStream_t st, int nx, const C* rec, size_t rstride, const C* dinv, int dstride,
+                         const T* xin, const T* b, T* xout);
+  static void residual_rec(int S, cudaStream_t st, int nx, const C* rec, size_t rstride, const T* x, const T* b,
+                           T* r);
   static void restrict_(int S, cudaStream_t st, int nxf, const T* rf, int nxc, T* bc);
   static void prolong_add(int S, cudaStream_t st, int nxc, const T* ec, int nxf, T* xf);
   static void block_rhs(int SF, cudaStream_t st, int nx, const C* cf, const double* v, const double* z, int i,
@@ -42,14 +47,19 @@ void launch_cell_gradient(int S, cudaStream_t st, int N, const double* kappa, co
 
 // Krylov kernels (krylov.cu), FP64.
 int krylov_partial_blocks();
+// run_if: optional device flag; the kernel does nothing when *run_if == 0.
 void launch_multidot(cudaStream_t st, const double* V, size_t ld, int count, const double* w, size_t n,
-                     double* partial);
-void launch_reduce_partials(cudaStream_t st, const double* partial, int count, double* out);
+                     double* partial, const int* run_if = nullptr);
+void launch_reduce_partials(cudaStream_t st, const double* partial, int count, double* out,
+                            const int* run_if = nullptr);
 void launch_multi_axpy(cudaStream_t st, double* w, const double* V, size_t ld, int count, const double* coef,
-                       double sign, size_t n);
-void launch_scale(cudaStream_t st, double* dst, const double* src, const double* denom, size_t n);
+                       double sign, size_t n, const double* scale = nullptr, const int* run_if = nullptr);
+void launch_scale(cudaStream_t st, double* dst, const double* src, const double* denom, size_t n,
+                  const int* run_if = nullptr);
+void launch_orth_decide(cudaStream_t st, int j, double* h1, double* h2, double eta2, int* redo, double* hn2,
+                        double* inv);
 void launch_givens(cudaStream_t st, int j, int ldh, double* H, double* cs, double* sn, double* g, const double* h1,
-                   const double* h2, const double* hn2, double* hn_out, double r0, double* rel_out);
+                   const double* h2, const double* hn2, double* hn_out, const double* r0, double* rel_out);
 void launch_trisolve(cudaStream_t st, int J, int ldh, const double* H, const double* g, double* y);
 void launch_sqrt_scalar(cudaStream_t st, const double* in, double* out);
 void launch_sub(cudaStream_t st, double* out, const double* a, const double* b, size_t n);

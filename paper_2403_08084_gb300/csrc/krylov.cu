@@ -26,7 +26,9 @@ __device__ __forceinline__ double warp_sum(double v) {
 // for k = blockIdx.y * kGroup + g < count.
 __global__ void __launch_bounds__(kThreads) multidot_kernel(const double* __restrict__ V, size_t ld, int count,
                                                             const double* __restrict__ w, size_t n,
-                                                            double* __restrict__ partial) {
+                                                            double* __restrict__ partial,
+                                                            const int* __restrict__ run_if) {
+  if (run_if != nullptr && *run_if == 0) return;
   __shared__ double red[kThreads / 32][kGroup];
   const int k0 = blockIdx.y * kGroup;
   const int kn = min(kGroup, count - k0);
@@ -57,7 +59,9 @@ __global__ void __launch_bounds__(kThreads) multidot_kernel(const double* __rest
 }
 
 __global__ void __launch_bounds__(kThreads) reduce_partials_kernel(const double* __restrict__ partial, int nb,
-                                                                   double* __restrict__ out) {
+                                                                   double* __restrict__ out,
+                                                                   const int* __restrict__ run_if) {
+  if (run_if != nullptr && *run_if == 0) return;
   __shared__ double red[kThreads / 32];
   const int k = blockIdx.x;
   double v = 0.0;
@@ -73,22 +77,27 @@ __global__ void __launch_bounds__(kThreads) reduce_partials_kernel(const double*
   }
 }
 
-// w += sign * sum_k coef[k] V_k
+// w = (w + sign * sum_k coef[k] V_k) * scale   (scale == nullptr: 1)
 __global__ void __launch_bounds__(kThreads) multi_axpy_kernel(double* __restrict__ w, const double* __restrict__ V,
                                                               size_t ld, int count, const double* __restrict__ coef,
-                                                              double sign, size_t n) {
+                                                              double sign, size_t n, const double* __restrict__ scale,
+                                                              const int* __restrict__ run_if) {
+  if (run_if != nullptr && *run_if == 0) return;
   __shared__ double c[128];
   for (int k = threadIdx.x; k < count; k += kThreads) c[k] = sign * coef[k];
   __syncthreads();
+  const double sc = (scale != nullptr) ? *scale : 1.0;
   for (size_t e = blockIdx.x * (size_t)kThreads + threadIdx.x; e < n; e += (size_t)gridDim.x * kThreads) {
     double acc = w[e];
     for (int k = 0; k < count; ++k) acc = fma(c[k], V[(size_t)k * ld + e], acc);
-    w[e] = acc;
+    w[e] = (scale != nullptr) ? acc * sc : acc;
   }
 }
 
 __global__ void __launch_bounds__(kThreads) scale_kernel(double* __restrict__ dst, const double* __restrict__ src,
-                                                         const double* __restrict__ denom, size_t n) {
+                                                         const double* __restrict__ denom, size_t n,
+                                                         const int* __restrict__ run_if) {
+  if (run_if != nullptr && *run_if == 0) return;
   const double d = *denom;
   const double inv = (d != 0.0) ? 1.0 / d : 0.0;
   for (size_t e = blockIdx.x * (size_t)kThreads + threadIdx.x; e < n; e += (size_t)gridDim.x * kThreads)
@@ -101,7 +110,8 @@ __global__ void __launch_bounds__(kThreads) scale_kernel(double* __restrict__ ds
 __global__ void givens_kernel(int j, int ldh, double* __restrict__ H, double* __restrict__ cs,
                               double* __restrict__ sn, double* __restrict__ g, const double* __restrict__ h1,
                               const double* __restrict__ h2, const double* __restrict__ hn2,
-                              double* __restrict__ hn_out, double r0, double* __restrict__ rel_out) {
+                              double* __restrict__ hn_out, const double* __restrict__ r0p,
+                              double* __restrict__ rel_out) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double* col = H + (size_t)j * ldh;
   for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
@@ -127,8 +137,32 @@ __global__ void givens_kernel(int j, int ldh, double* __restrict__ H, double* __
   col[j + 1] = 0.0;
   g[j + 1] = -s * g[j];
   g[j] = c * g[j];
-  rel_out[0] = fabs(g[j + 1]) / r0;
+  rel_out[0] = fabs(g[j + 1]) / *r0p;
   rel_out[1] = hn;
+}
+
+// Classical Gram-Schmidt with the selective re-orthogonalisation test of Daniel,
+// Gragg, Kaufman and Stewart: after one pass w' = w - V h1 the norm follows from
+// ||w'||^2 = ||w||^2 - ||h1||^2 (h1 holds V^T w, its entry j+1 holds ||w||^2).  If
+// ||w'|| >= eta ||w|| the pass was enough: redo = 0, hn2 = ||w'||^2, inv = 1/||w'||
+// (w' is normalised in the same sweep) and h2 = 0.  Otherwise redo = 1 and the
+// second pass runs (inv = 1: the normalisation comes after it).  One thread.
+__global__ void orth_decide_kernel(int j, double* __restrict__ h1, double* __restrict__ h2, double eta2,
+                                   int* __restrict__ redo, double* __restrict__ hn2, double* __restrict__ inv) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double wn2 = h1[j + 1];
+  double hh = 0.0;
+  for (int i = 0; i <= j; ++i) hh += h1[i] * h1[i];
+  const double wp2 = wn2 - hh;
+  for (int i = 0; i <= j + 1; ++i) h2[i] = 0.0;
+  if (wp2 >= eta2 * wn2 && wp2 > 0.0) {
+    *redo = 0;
+    *hn2 = wp2;
+    *inv = 1.0 / sqrt(wp2);
+  } else {
+    *redo = 1;
+    *inv = 1.0;
+  }
 }
 
 // y = R^{-1} g for the J x J upper-triangular R stored column-major in H.  One thread.
@@ -169,22 +203,26 @@ int grid_for(size_t n) {
 int krylov_partial_blocks() { return kPartialBlocks; }
 
 void launch_multidot(cudaStream_t st, const double* V, size_t ld, int count, const double* w, size_t n,
-                     double* partial) {
+                     double* partial, const int* run_if) {
   dim3 g(kPartialBlocks, (count + kGroup - 1) / kGroup);
-  multidot_kernel<<<g, kThreads, 0, st>>>(V, ld, count, w, n, partial);
+  multidot_kernel<<<g, kThreads, 0, st>>>(V, ld, count, w, n, partial, run_if);
 }
-void launch_reduce_partials(cudaStream_t st, const double* partial, int count, double* out) {
-  reduce_partials_kernel<<<count, kThreads, 0, st>>>(partial, kPartialBlocks, out);
+void launch_reduce_partials(cudaStream_t st, const double* partial, int count, double* out, const int* run_if) {
+  reduce_partials_kernel<<<count, kThreads, 0, st>>>(partial, kPartialBlocks, out, run_if);
 }
 void launch_multi_axpy(cudaStream_t st, double* w, const double* V, size_t ld, int count, const double* coef,
-                       double sign, size_t n) {
-  multi_axpy_kernel<<<grid_for(n), kThreads, 0, st>>>(w, V, ld, count, coef, sign, n);
+                       double sign, size_t n, const double* scale, const int* run_if) {
+  multi_axpy_kernel<<<grid_for(n), kThreads, 0, st>>>(w, V, ld, count, coef, sign, n, scale, run_if);
 }
-void launch_scale(cudaStream_t st, double* dst, const double* src, const double* denom, size_t n) {
-  scale_kernel<<<grid_for(n), kThreads, 0, st>>>(dst, src, denom, n);
+void launch_scale(cudaStream_t st, double* dst, const double* src, const double* denom, size_t n, const int* run_if) {
+  scale_kernel<<<grid_for(n), kThreads, 0, st>>>(dst, src, denom, n, run_if);
+}
+void launch_orth_decide(cudaStream_t st, int j, double* h1, double* h2, double eta2, int* redo, double* hn2,
+                        double* inv) {
+  orth_decide_kernel<<<1, 32, 0, st>>>(j, h1, h2, eta2, redo, hn2, inv);
 }
 void launch_givens(cudaStream_t st, int j, int ldh, double* H, double* cs, double* sn, double* g, const double* h1,
-                   const double* h2, const double* hn2, double* hn_out, double r0, double* rel_out) {
+                   const double* h2, const double* hn2, double* hn_out, const double* r0, double* rel_out) {
   givens_kernel<<<1, 32, 0, st>>>(j, ldh, H, cs, sn, g, h1, h2, hn2, hn_out, r0, rel_out);
 }
 void launch_trisolve(cudaStream_t st, int J, int ldh, const double* H, const double* g, double* y) {

@@ -49,6 +49,43 @@ __global__ void __launch_bounds__(kBX* kBY) jacobi_kernel(int nx, const C* __res
   }
 }
 
+// The same sweep with B_i = M + sigma_i K stored as its own stencil record per
+// stage (stage-major: record of stage i at rec + i * rstride): 9 products per
+// node instead of separate mass and stiffness stencils.  Used by the FP64
+// V-cycle, whose arithmetic (not its memory traffic) bounds it on GB300.
+template <typename T, typename C, int S>
+__global__ void __launch_bounds__(kBX* kBY) jacobi_rec_kernel(int nx, const C* __restrict__ rec, size_t rstride,
+                                                              const C* __restrict__ dinv, int dstride,
+                                                              const T* __restrict__ xin, const T* __restrict__ b,
+                                                              T* __restrict__ xout) {
+  const int ix = 1 + blockIdx.x * kBX + threadIdx.x;
+  const int iy = 1 + blockIdx.y * kBY + threadIdx.y;
+  if (ix > nx - 2 || iy > nx - 2) return;
+  const int p = ix + nx * iy;
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    const C bi = ld<C>(b + (size_t)p * S + i);
+    const C di = dinv[(size_t)p * dstride + i];
+    const C bx = k_apply<S, C>(rec + (size_t)i * rstride, xin, p, nx, i);
+    st(xout + (size_t)p * S + i, ld<C>(xin + (size_t)p * S + i) + di * (bi - bx));
+  }
+}
+
+template <typename T, typename C, int S>
+__global__ void __launch_bounds__(kBX* kBY) residual_rec_kernel(int nx, const C* __restrict__ rec, size_t rstride,
+                                                                const T* __restrict__ x, const T* __restrict__ b,
+                                                                T* __restrict__ r) {
+  const int ix = 1 + blockIdx.x * kBX + threadIdx.x;
+  const int iy = 1 + blockIdx.y * kBY + threadIdx.y;
+  if (ix > nx - 2 || iy > nx - 2) return;
+  const int p = ix + nx * iy;
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    const C bx = k_apply<S, C>(rec + (size_t)i * rstride, x, p, nx, i);
+    st(r + (size_t)p * S + i, ld<C>(b + (size_t)p * S + i) - bx);
+  }
+}
+
 // r = b - B x on interior nodes.
 template <typename T, typename C, int S>
 __global__ void __launch_bounds__(kBX* kBY) residual_kernel(int nx, const C* __restrict__ cf, C hm, Vec8 sigma,
@@ -183,6 +220,18 @@ void MG2<T, C>::jacobi(int S, cudaStream_t st, int nx, const C* cf, double hm, c
                        int dstride, const T* xin, const T* b, T* xout) {
   dim3 g = interior_grid(nx), blk(kBX, kBY);
   IRK_DISPATCH_S(S, jacobi_kernel<T, C, SS><<<g, blk, 0, st>>>(nx, cf, (C)hm, sigma, dinv, dstride, xin, b, xout));
+}
+template <typename T, typename C>
+void MG2<T, C>::jacobi_rec(int S, cudaStream_t st, int nx, const C* rec, size_t rstride, const C* dinv, int dstride,
+                           const T* xin, const T* b, T* xout) {
+  dim3 g = interior_grid(nx), blk(kBX, kBY);
+  IRK_DISPATCH_S(S, jacobi_rec_kernel<T, C, SS><<<g, blk, 0, st>>>(nx, rec, rstride, dinv, dstride, xin, b, xout));
+}
+template <typename T, typename C>
+void MG2<T, C>::residual_rec(int S, cudaStream_t st, int nx, const C* rec, size_t rstride, const T* x, const T* b,
+                             T* r) {
+  dim3 g = interior_grid(nx), blk(kBX, kBY);
+  IRK_DISPATCH_S(S, residual_rec_kernel<T, C, SS><<<g, blk, 0, st>>>(nx, rec, rstride, x, b, r));
 }
 template <typename T, typename C>
 void MG2<T, C>::residual(int S, cudaStream_t st, int nx, const C* cf, double hm, const Vec8& sigma, const T* x,

@@ -33,7 +33,8 @@ class Solver:
 
     def __init__(self, n_cells: int, tableau, dt: float, *, kappa=None, levels: int = 1, dim: int = 2,
                  precond: str = "lower", vcycle: str = "fp64", nu_pre: int = 2, nu_post: int = 2,
-                 omega: float = 2.0 / 3.0, rtol: float = 1e-10, restart: int = 50, maxit: int = 500, stream=None):
+                 omega: float = 2.0 / 3.0, rtol: float = 1e-10, restart: int = 50, maxit: int = 500,
+                 orth: str = "cgs2", stream=None):
         A = np.ascontiguousarray(tableau.A, dtype=np.float64)
         self.s = int(A.shape[0])
         self.N, self.dim, self.dt = int(n_cells), int(dim), float(dt)
@@ -58,6 +59,7 @@ class Solver:
         opt.vcycle_prec = L.PREC[vcycle]
         opt.nu_pre, opt.nu_post, opt.omega = int(nu_pre), int(nu_post), float(omega)
         opt.rtol, opt.restart, opt.maxit = float(rtol), int(restart), int(maxit)
+        opt.orth = L.ORTH[orth]
         self.options = opt
         self.stream = stream if stream is not None else _current_stream()
         h = C.c_void_p()

@@ -22,7 +22,7 @@ def test_default_options():
 
     opt = L.irk_options()
     L.lib.irk_default_options(C.byref(opt))
-    assert (opt.precond, opt.vcycle_prec, opt.nu_pre, opt.nu_post, opt.restart) == (1, 0, 2, 2, 50)
+    assert (opt.precond, opt.vcycle_prec, opt.nu_pre, opt.nu_post, opt.restart, opt.orth) == (1, 0, 2, 2, 50, 0)
     assert abs(opt.omega - 2 / 3) < 1e-15 and opt.rtol == 1e-10
 
 
@@ -65,6 +65,7 @@ def _create(N=8, levels=1, A=None, s=2, dt=0.1, **opt_over):
         (dict(restart=0), "restart"),
         (dict(omega=2.5), "omega"),
         (dict(precond=7), "precond"),
+        (dict(orth=5), "orth"),
     ],
 )
 def test_create_rejects_bad_input(kwargs, needle):

@@ -118,7 +118,8 @@ def test_vcycle_levels_single_stage(levels):
 # ----------------------------------------------------------------------------
 @pytest.mark.parametrize("kind", ["diag", "lower", "upper"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
-def test_solve_matches_direct_and_iteration_count(kind, prec):
+@pytest.mark.parametrize("orth", ["cgs2", "dgks"])
+def test_solve_matches_direct_and_iteration_count(kind, prec, orth):
     N, levels, s, dt = 64, 3, 3, 1 / 64
     kap = W.lognormal_kappa(2, N, 0.5, seed=9)
     d = fem.Discretisation(2, N, kap)
@@ -127,7 +128,7 @@ def test_solve_matches_direct_and_iteration_count(kind, prec):
     r_int = d.to_interior(r_full, s)
     k_ref = rk.KroneckerSolver(d.M, d.K, ot.A, dt).solve(r_int)
     with Solver(N, product_tableau("RadauIIA", s), dt, kappa=kap, levels=levels, precond=kind, vcycle=prec,
-                rtol=1e-12) as sv:
+                rtol=1e-12, orth=orth) as sv:
         k = torch.empty(sv.n_nodes * s, dtype=torch.float64, device="cuda")
         st = sv.solve(dev(r_full), k)
         k = host(k)
@@ -194,6 +195,42 @@ def test_other_tableaux(name, s):
     u, _ = manufactured_run(N, name, s, dt, steps, 2, "lower", "fp64", kappa=kap)
     d, uN = oracle_run(N, name, s, dt, steps, kappa=kap)
     assert rel(d.to_interior(u), uN) < 1e-10
+
+
+@pytest.mark.parametrize("orth", ["cgs2", "dgks"])
+def test_restarted_fgmres(orth):
+    """A short restart length forces several restart cycles; the result still matches the direct solve."""
+    N, levels, s, dt = 48, 2, 3, 1 / 32
+    kap = W.lognormal_kappa(2, N, 0.5, seed=30)
+    d = fem.Discretisation(2, N, kap)
+    ot = oracle_tableau("RadauIIA", s)
+    r_full = W.random_nodal(2, N, seed=31, s=s)
+    k_ref = rk.KroneckerSolver(d.M, d.K, ot.A, dt).solve(d.to_interior(r_full, s))
+    with Solver(N, product_tableau("RadauIIA", s), dt, kappa=kap, levels=levels, precond="diag", restart=4,
+                rtol=1e-12, orth=orth) as sv:
+        k = np.empty(sv.n_nodes * s)
+        st = sv.solve(r_full, k)
+    assert st["converged"] and st["fgmres_its"] > 4
+    assert rel(d.to_interior(k, s), k_ref) < 1e-10
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16"])
+def test_graph_replay_equals_eager_launches(prec, monkeypatch):
+    """Each Arnoldi step runs as a captured CUDA graph; eager launches give the same bits."""
+    N, s, dt = 64, 3, 1 / 64
+    kap = W.lognormal_kappa(2, N, 0.5, seed=32)
+    tab = product_tableau("RadauIIA", s)
+    u0 = W.sine_initial(2, N)
+    f = W.sine_load_space(2, N)
+    outs = []
+    for env in ("0", "1"):
+        monkeypatch.setenv("IRK_NO_GRAPHS", env)
+        with Solver(N, tab, dt, kappa=kap, levels=3, precond="lower", vcycle=prec) as sv:
+            u = dev(u0)
+            for n in range(3):  # later steps replay the graphs captured in the first
+                sv.step(u, u, f_space=dev(f), f_coef=[W.sine_load_time(2, (n + c) * dt) for c in tab.c])
+            outs.append(host(u))
+    assert np.array_equal(outs[0], outs[1])
 
 
 def test_stages_out_and_host_pointers():
