@@ -52,11 +52,18 @@ extern "C" {
 #define IRK_PC_DIAG 0  /* P_D = I (x) M + dt D (x) K          (eq. pcbjac, AI form)   */
 #define IRK_PC_LOWER 1 /* P_L = I (x) M + dt (L + D) (x) K    (eq. pcbgs, AI form)    */
 #define IRK_PC_UPPER 2 /* P_U = I (x) M + dt (U + D) (x) K    (Sec. 3.1)              */
+#define IRK_PC_RANA_LD 3 /* I (x) M + dt (L D) (x) K with A = L D U, L unit lower, U unit
+                            upper: the Rana-type preconditioner (eq. pcranald, AI form)   */
 
 /* Arnoldi orthogonalisation (the paper does not fix one) */
 #define IRK_ORTH_CGS2 0 /* classical Gram-Schmidt, always two passes                       */
 #define IRK_ORTH_DGKS 1 /* classical Gram-Schmidt, second pass only when ||w'|| < ||w||/sqrt(2)
                            (Daniel-Gragg-Kaufman-Stewart test), norm by Pythagoras otherwise   */
+
+/* outer solver */
+#define IRK_SOLVER_FGMRES 0  /* FGMRES on the whole stage system (any tableau)                    */
+#define IRK_SOLVER_DIRK_CG 1 /* lower-triangular A with a_ii > 0 (DIRK, Sec. 2.3): the stages one
+                                after another, each by CG preconditioned with one V-cycle         */
 
 /* storage / arithmetic of the multigrid V-cycles inside the FP64 FGMRES */
 #define IRK_PREC_FP64 0 /* vectors and arithmetic in double                         */
@@ -91,10 +98,12 @@ typedef struct {
   int restart;      /* FGMRES restart length m (default 50) */
   int maxit;        /* total FGMRES iterations allowed per solve (default 500) */
   int orth;         /* IRK_ORTH_* (default IRK_ORTH_CGS2) */
+  int solver;       /* IRK_SOLVER_* (default IRK_SOLVER_FGMRES) */
 } irk_options;
 
 typedef struct {
-  int fgmres_its;   /* Arnoldi steps (= preconditioner applications) of the last solve */
+  int fgmres_its;   /* Krylov iterations of the last solve: FGMRES Arnoldi steps, or CG
+                       iterations summed over the stages for IRK_SOLVER_DIRK_CG */
   int vcycles;      /* single-block V-cycles applied in the last solve */
   double rel_resid; /* final ||r||_2 / ||r_0||_2 estimate of the last solve */
   int converged;    /* 1 if rel_resid <= rtol */
@@ -136,6 +145,10 @@ int irk_solve(irk_handle* h, const double* r, double* k, irk_stats* stats);
 
 /* y = (I (x) M + dt A (x) K) x for stage vectors (transpose != 0: A^T instead of A). */
 int irk_apply_operator(irk_handle* h, const double* x, double* y, int transpose);
+
+/* y = M x for nodal vectors (the Q1 mass matrix; boundary entries of x read as 0,
+ * of y written as 0).  Used for M-weighted objectives such as 1/2 ||u - u*||_M^2. */
+int irk_apply_mass(irk_handle* h, const double* x, double* y);
 
 /* z = P^{-1} v: one application of the configured block preconditioner, each
  * block approximated by one V-cycle (transpose != 0: the transposed

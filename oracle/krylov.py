@@ -9,7 +9,9 @@ additive splitting A = L + D + U of the Butcher matrix gives
 
 * P_D = I (x) M + dt D (x) K        (block Jacobi, the AI form of eq. pcbjac),
 * P_L = I (x) M + dt (L + D) (x) K  (block Gauss-Seidel, the AI form of eq. pcbgs),
-* P_U = I (x) M + dt (U + D) (x) K  (the upper-triangular variant named in Sec. 3.1).
+* P_U = I (x) M + dt (U + D) (x) K  (the upper-triangular variant named in Sec. 3.1),
+* P_LD = I (x) M + dt (L D) (x) K with A = L D U (the Rana-type preconditioner, eq. pcranald):
+  ``BlockPreconditioner("lower", rana_ld(A), ...)``.
 
 (The paper writes them for the IA form; the AI ones are the same preconditioners
 up to a block scaling by D^{-1} or (L+D)^{-1}.)  Applying P_L^{-1} is a forward
@@ -55,6 +57,27 @@ class BlockPreconditioner:
             z[i] = self.solves[i](rhs)
             done.append(i)
         return z.reshape(-1)
+
+
+def ldu(A: np.ndarray):
+    """A = L D U without pivoting (L unit lower, D diagonal, U unit upper), by Gaussian elimination."""
+    A = np.asarray(A, dtype=np.float64)
+    s = A.shape[0]
+    L = np.eye(s)
+    W = A.copy()
+    for k in range(s):
+        for i in range(k + 1, s):
+            L[i, k] = W[i, k] / W[k, k]
+            W[i, :] -= L[i, k] * W[k, :]
+    D = np.diag(np.diag(W))
+    U = np.linalg.solve(D, W)
+    return L, D, U
+
+
+def rana_ld(A: np.ndarray) -> np.ndarray:
+    """The triangular approximation A_LD = L D of the Rana-type preconditioner (Sec. 3.1, eq. pcranald)."""
+    L, D, _ = ldu(A)
+    return L @ D
 
 
 def fgmres(apply_A, b: np.ndarray, precond, rtol: float = 1e-10, restart: int = 50, maxit: int = 500, x0=None,

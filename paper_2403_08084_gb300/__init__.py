@@ -9,5 +9,6 @@ from . import _lib
 from ._lib import IRKError
 from .solver import Solver
 from . import tableaux
+from . import adjoint
 
-__all__ = ["Solver", "IRKError", "tableaux", "_lib"]
+__all__ = ["Solver", "IRKError", "tableaux", "adjoint", "_lib"]

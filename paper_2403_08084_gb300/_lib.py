@@ -17,9 +17,10 @@ LIB_PATH = os.path.join(_PKG, "libirk.so")
 HEADER = os.path.join(os.path.dirname(_PKG), "include", "irk.h")
 
 IRK_OK, IRK_EINVAL, IRK_ENOMEM, IRK_ECUDA, IRK_ENOCONV, IRK_ENONFINITE = 0, -1, -2, -3, -4, -5
-PC = {"diag": 0, "lower": 1, "upper": 2}
+PC = {"diag": 0, "lower": 1, "upper": 2, "rana_ld": 3}
 PREC = {"fp64": 0, "fp32": 1, "bf16": 2}
 ORTH = {"cgs2": 0, "dgks": 1}
+SOLVER = {"fgmres": 0, "dirk_cg": 1}
 MAX_STAGES = 4
 _ERRNAMES = {-1: "IRK_EINVAL", -2: "IRK_ENOMEM", -3: "IRK_ECUDA", -4: "IRK_ENOCONV", -5: "IRK_ENONFINITE"}
 
@@ -42,7 +43,7 @@ class irk_tableau(C.Structure):
 class irk_options(C.Structure):
     _fields_ = [("precond", C.c_int), ("vcycle_prec", C.c_int), ("nu_pre", C.c_int), ("nu_post", C.c_int),
                 ("omega", C.c_double), ("rtol", C.c_double), ("restart", C.c_int), ("maxit", C.c_int),
-                ("orth", C.c_int)]
+                ("orth", C.c_int), ("solver", C.c_int)]
 
 
 class irk_stats(C.Structure):
@@ -82,6 +83,7 @@ _SIGNATURES = {
     "irk_step": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, C.POINTER(irk_stats)]),
     "irk_solve": (C.c_int, [_P, _P, _P, C.POINTER(irk_stats)]),
     "irk_apply_operator": (C.c_int, [_P, _P, _P, C.c_int]),
+    "irk_apply_mass": (C.c_int, [_P, _P, _P]),
     "irk_apply_preconditioner": (C.c_int, [_P, _P, _P, C.c_int]),
     "irk_apply_preconditioner_noalloc": (C.c_int, [_P, _P, _P, C.c_int]),
     "irk_step_adjoint": (C.c_int, [_P, _P, _P, _P, _P, _P, C.POINTER(irk_stats)]),

@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <mutex>
 #include <new>
 #include <string>
@@ -59,9 +60,10 @@ int fail(int code, const char* fmt, ...) {
 size_t prec_bytes(int prec) { return prec == IRK_PREC_FP64 ? 8 : (prec == IRK_PREC_FP32 ? 4 : 2); }
 
 struct Level {
-  int N = 0, nx = 0;
+  int N = 0, nx = 0, dim = 2;
   size_t nn = 0;
-  double hm = 0.0;  // h^2 / 36
+  double hm = 0.0;  // h^2 / 36 (2D mass stencil scale)
+  double mcls[4] = {0, 0, 0, 0}, kcls[4] = {0, 0, 0, 0};  // 3D: Q1 mass / stiffness class values
   std::vector<double> cf_host;
   double* cf_d = nullptr;     // stencil records, double
   float* cf_f = nullptr;      // stencil records, float
@@ -82,11 +84,12 @@ struct DevBuf {
 }  // namespace
 
 struct irk_handle {
-  int dim = 2, N = 0, s = 0, L = 0;
+  int dim = 2, N = 0, s = 0, L = 0;  // dim: 2 (quads, per-cell kappa) or 3 (hexahedra, kappa = 1)
   double dt = 0.0;
   irk_options opt{};
   cudaStream_t st = nullptr;
   std::vector<double> A, b, c, kappa;
+  std::vector<double> Ap;  // the preconditioner's approximation of A: tril(A), or L D from A = L D U
   std::vector<Level> lev;
   // coarsest-level exact solve
   int nint = 0;
@@ -113,6 +116,8 @@ struct irk_handle {
     int vcycles = 0;
   };
   std::vector<IterGraph> graphs[2];
+  std::vector<IterGraph> cg_graphs[2];  // one per stage and direction (DIRK solver)
+  double *cg_x = nullptr, *cg_r = nullptr, *cg_z = nullptr, *cg_p = nullptr, *cg_q = nullptr, *cg_b = nullptr;
   cudaStream_t cap_stream = nullptr;
   bool use_graphs = true;
   // instrumentation
@@ -269,7 +274,8 @@ inline double n_int(int nx) { return (double)(nx - 2) * (double)(nx - 2); }
 // ----------------------------------------------------------------------------
 int validate(const irk_mesh* mesh, const irk_tableau* tab, double dt, const irk_options* opt) {
   if (!mesh || !tab || !opt) return fail(IRK_EINVAL, "null mesh, tableau or options");
-  if (mesh->dim != 2) return fail(IRK_EINVAL, "dim = %d: this build supports dim = 2", mesh->dim);
+  if (mesh->dim != 2 && mesh->dim != 3) return fail(IRK_EINVAL, "dim = %d: must be 2 or 3", mesh->dim);
+  if (mesh->dim == 3 && mesh->kappa) return fail(IRK_EINVAL, "dim = 3 supports kappa = 1 only (pass NULL)");
   const int N = mesh->n_cells, L = mesh->levels;
   if (N < 2 || N > 16384) return fail(IRK_EINVAL, "n_cells = %d out of range [2, 16384]", N);
   if (L < 1 || L > 14) return fail(IRK_EINVAL, "levels = %d out of range [1, 14]", L);
@@ -277,7 +283,9 @@ int validate(const irk_mesh* mesh, const irk_tableau* tab, double dt, const irk_
   if (N % div != 0) return fail(IRK_EINVAL, "n_cells = %d not divisible by 2^(levels-1) = %d", N, div);
   const int Nc = N / div;
   if (Nc < 2) return fail(IRK_EINVAL, "coarsest level has %d cells per axis (< 2)", Nc);
-  if (Nc > 64) return fail(IRK_EINVAL, "coarsest level has %d cells per axis (> 64): add levels", Nc);
+  if (mesh->dim == 2 && Nc > 64) return fail(IRK_EINVAL, "coarsest level has %d cells per axis (> 64): add levels", Nc);
+  if (mesh->dim == 3 && Nc > 16) return fail(IRK_EINVAL, "coarsest level has %d cells per axis (> 16): add levels", Nc);
+  if (mesh->dim == 3 && N > 1024) return fail(IRK_EINVAL, "n_cells = %d too large for dim = 3", N);
   if (mesh->kappa) {
     const size_t nc = (size_t)N * N;
     for (size_t i = 0; i < nc; ++i)
@@ -302,7 +310,7 @@ int validate(const irk_mesh* mesh, const irk_tableau* tab, double dt, const irk_
   }
   if (std::fabs(bsum - 1.0) > 1e-6) return fail(IRK_EINVAL, "sum(b) = %.17g != 1", bsum);
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(IRK_EINVAL, "dt = %g must be positive", dt);
-  if (opt->precond < IRK_PC_DIAG || opt->precond > IRK_PC_UPPER) return fail(IRK_EINVAL, "bad precond %d", opt->precond);
+  if (opt->precond < IRK_PC_DIAG || opt->precond > IRK_PC_RANA_LD) return fail(IRK_EINVAL, "bad precond %d", opt->precond);
   if (opt->vcycle_prec < IRK_PREC_FP64 || opt->vcycle_prec > IRK_PREC_BF16)
     return fail(IRK_EINVAL, "bad vcycle_prec %d", opt->vcycle_prec);
   if (opt->nu_pre < 1 || opt->nu_post < 1 || opt->nu_pre > 16 || opt->nu_post > 16)
@@ -312,14 +320,45 @@ int validate(const irk_mesh* mesh, const irk_tableau* tab, double dt, const irk_
   if (opt->restart < 1 || opt->restart > 100) return fail(IRK_EINVAL, "restart = %d not in [1, 100]", opt->restart);
   if (opt->maxit < 1) return fail(IRK_EINVAL, "maxit = %d < 1", opt->maxit);
   if (opt->orth != IRK_ORTH_CGS2 && opt->orth != IRK_ORTH_DGKS) return fail(IRK_EINVAL, "bad orth %d", opt->orth);
+  if (opt->solver != IRK_SOLVER_FGMRES && opt->solver != IRK_SOLVER_DIRK_CG)
+    return fail(IRK_EINVAL, "bad solver %d", opt->solver);
+  if (opt->solver == IRK_SOLVER_DIRK_CG) {
+    for (int i = 0; i < s; ++i) {
+      if (!(tab->A[i * s + i] > 0.0)) return fail(IRK_EINVAL, "DIRK solver needs a_ii > 0 (a_%d%d = %g)", i, i, tab->A[i * s + i]);
+      for (int j = i + 1; j < s; ++j)
+        if (tab->A[i * s + j] != 0.0) return fail(IRK_EINVAL, "DIRK solver needs a lower-triangular A (a_%d%d != 0)", i, j);
+    }
+  }
   return IRK_OK;
 }
 
 // Build the hierarchy's host data and upload it (also used by irk_set_kappa).
+int build_operators_3d(irk_handle* h, const std::vector<double>& sigma) {
+  const int s = h->s;
+  for (Level& Lv : h->lev) q1_classes_3d(1.0 / Lv.N, Lv.mcls, Lv.kcls);
+  Level& Lc = h->lev[h->L - 1];
+  std::vector<int> map;
+  interior_nodes_3d(Lc.N, map);
+  const int nint = (int)map.size();
+  std::vector<double> all((size_t)s * nint * nint), inv;
+  for (int i = 0; i < s; ++i) {
+    if (!dense_block_inverse_3d(Lc.N, Lc.mcls, Lc.kcls, sigma[i], map, inv))
+      return fail(IRK_EINVAL, "coarsest block %d (sigma = %g) is singular", i, sigma[i]);
+    std::copy(inv.begin(), inv.end(), all.begin() + (size_t)i * nint * nint);
+  }
+  std::vector<float> allf(all.begin(), all.end());
+  CK(cudaMemcpyAsync(h->cmap, map.data(), map.size() * sizeof(int), cudaMemcpyHostToDevice, h->st));
+  CK(cudaMemcpyAsync(h->binv_d, all.data(), all.size() * 8, cudaMemcpyHostToDevice, h->st));
+  CK(cudaMemcpyAsync(h->binv_f, allf.data(), allf.size() * 4, cudaMemcpyHostToDevice, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return IRK_OK;
+}
+
 int build_operators(irk_handle* h) {
   const int s = h->s;
   std::vector<double> sigma(s);
-  for (int i = 0; i < s; ++i) sigma[i] = h->dt * h->A[i * s + i];
+  for (int i = 0; i < s; ++i) sigma[i] = h->dt * h->Ap[i * s + i];
+  if (h->dim == 3) return build_operators_3d(h, sigma);
   for (int l = 0; l < h->L; ++l) {
     Level& Lv = h->lev[l];
     if (l == 0)
@@ -376,6 +415,10 @@ void destroy(irk_handle* h) {
   for (auto& gv : h->graphs)
     for (auto& G : gv)
       if (G.exec) cudaGraphExecDestroy(G.exec);
+  for (auto& gv : h->cg_graphs)
+    for (auto& G : gv)
+      if (G.exec) cudaGraphExecDestroy(G.exec);
+  dfree(h->cg_x), dfree(h->cg_r), dfree(h->cg_z), dfree(h->cg_p), dfree(h->cg_q), dfree(h->cg_b);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->pinned) cudaFreeHost(h->pinned);
   delete h;
@@ -388,6 +431,7 @@ int create(irk_handle** out, const irk_mesh* mesh, const irk_tableau* tab, doubl
   TRY(validate(mesh, tab, dt, opt));
   irk_handle* h = new irk_handle();
   h->N = mesh->n_cells;
+  h->dim = mesh->dim;
   h->L = mesh->levels;
   h->s = tab->s;
   h->dt = dt;
@@ -395,9 +439,34 @@ int create(irk_handle** out, const irk_mesh* mesh, const irk_tableau* tab, doubl
   h->st = (cudaStream_t)stream;
   const int s = h->s;
   h->A.assign(tab->A, tab->A + s * s);
+  h->Ap = h->A;
+  if (opt->precond == IRK_PC_RANA_LD) {
+    // A = L D U (L unit lower, U unit upper, no pivoting); the preconditioner uses L D (Sec. 3.1, eq. pcranald)
+    std::vector<double> Lm(s * s, 0.0), Um(s * s, 0.0);  // Doolittle: A = Lm Um, Um upper with diagonal D
+    for (int i = 0; i < s; ++i) {
+      for (int j = i; j < s; ++j) {
+        double v = h->A[i * s + j];
+        for (int k = 0; k < i; ++k) v -= Lm[i * s + k] * Um[k * s + j];
+        Um[i * s + j] = v;
+      }
+      Lm[i * s + i] = 1.0;
+      for (int r = i + 1; r < s; ++r) {
+        double v = h->A[r * s + i];
+        for (int k = 0; k < i; ++k) v -= Lm[r * s + k] * Um[k * s + i];
+        if (Um[i * s + i] == 0.0) {
+          destroy(h);
+          return fail(IRK_EINVAL, "A has a zero leading principal minor: no L D U factorisation");
+        }
+        Lm[r * s + i] = v / Um[i * s + i];
+      }
+    }
+    for (int i = 0; i < s; ++i)
+      for (int j = 0; j < s; ++j) h->Ap[i * s + j] = (j <= i) ? Lm[i * s + j] * Um[j * s + j] : 0.0;
+  }
   h->b.assign(tab->b, tab->b + s);
   h->c.assign(tab->c, tab->c + s);
   if (mesh->kappa) h->kappa.assign(mesh->kappa, mesh->kappa + (size_t)h->N * h->N);
+  const int dim = h->dim;
   auto bail = [&](int code) {
     destroy(h);
     return code;
@@ -408,14 +477,18 @@ int create(irk_handle** out, const irk_mesh* mesh, const irk_tableau* tab, doubl
     Level& Lv = h->lev[l];
     Lv.N = h->N >> l;
     Lv.nx = Lv.N + 1;
-    Lv.nn = (size_t)Lv.nx * Lv.nx;
+    Lv.dim = dim;
+    Lv.nn = (size_t)Lv.nx * Lv.nx * (dim == 3 ? Lv.nx : 1);
     const double hh = 1.0 / Lv.N;
     Lv.hm = hh * hh / 36.0;
     int r = IRK_OK;
-    if (opt->vcycle_prec == IRK_PREC_FP64 && (r = dalloc(&Lv.brec_d, Lv.nn * kCoef2 * s * 8))) return bail(r);
-    if ((r = dalloc(&Lv.cf_d, Lv.nn * kCoef2 * 8)) || (r = dalloc(&Lv.cf_f, Lv.nn * kCoef2 * 4)) ||
-        (r = dalloc(&Lv.dinv_d, Lv.nn * s * 8)) || (r = dalloc(&Lv.dinv_f, Lv.nn * s * 4)) ||
-        (r = dalloc(&Lv.xa, Lv.nn * s * vb)) || (r = dalloc(&Lv.xb, Lv.nn * s * vb)) ||
+    if (dim == 2) {  // stencil records (3D uses constant class values instead)
+      if (opt->vcycle_prec == IRK_PREC_FP64 && (r = dalloc(&Lv.brec_d, Lv.nn * kCoef2 * s * 8))) return bail(r);
+      if ((r = dalloc(&Lv.cf_d, Lv.nn * kCoef2 * 8)) || (r = dalloc(&Lv.cf_f, Lv.nn * kCoef2 * 4)) ||
+          (r = dalloc(&Lv.dinv_d, Lv.nn * s * 8)) || (r = dalloc(&Lv.dinv_f, Lv.nn * s * 4)))
+        return bail(r);
+    }
+    if ((r = dalloc(&Lv.xa, Lv.nn * s * vb)) || (r = dalloc(&Lv.xb, Lv.nn * s * vb)) ||
         (r = dalloc(&Lv.b, Lv.nn * s * vb)) || (r = dalloc(&Lv.r, Lv.nn * s * vb)))
       return bail(r);
     // boundary entries of every level vector stay zero for the handle's lifetime
@@ -424,12 +497,12 @@ int create(irk_handle** out, const irk_mesh* mesh, const irk_tableau* tab, doubl
       return bail(fail(IRK_ECUDA, "cudaMemsetAsync failed"));
   }
   const int Nc = h->lev[h->L - 1].N;
-  h->nint = (Nc - 1) * (Nc - 1);
+  h->nint = (Nc - 1) * (Nc - 1) * (dim == 3 ? Nc - 1 : 1);
   int r = IRK_OK;
   if ((r = dalloc(&h->cmap, (size_t)h->nint * sizeof(int))) ||
       (r = dalloc(&h->binv_d, (size_t)s * h->nint * h->nint * 8)) ||
       (r = dalloc(&h->binv_f, (size_t)s * h->nint * h->nint * 4)) ||
-      (r = dalloc(&h->kappa_d, (size_t)h->N * h->N * 8)))
+      (r = dalloc(&h->kappa_d, dim == 2 ? (size_t)h->N * h->N * 8 : 16)))
     return bail(r);
   h->ne = h->lev[0].nn * s;
   h->m = opt->restart;
@@ -455,6 +528,18 @@ int create(irk_handle** out, const irk_mesh* mesh, const irk_tableau* tab, doubl
   }
   h->graphs[0].resize(h->m);
   h->graphs[1].resize(h->m);
+  h->cg_graphs[0].resize(s);
+  h->cg_graphs[1].resize(s);
+  if (opt->solver == IRK_SOLVER_DIRK_CG) {
+    const size_t nb = h->lev[0].nn * 8;
+    if ((r = dalloc(&h->cg_x, nb)) || (r = dalloc(&h->cg_r, nb)) || (r = dalloc(&h->cg_z, nb)) ||
+        (r = dalloc(&h->cg_p, nb)) || (r = dalloc(&h->cg_q, nb)) || (r = dalloc(&h->cg_b, nb)))
+      return bail(r);
+    if (cudaMemsetAsync(h->cg_x, 0, nb, h->st) || cudaMemsetAsync(h->cg_r, 0, nb, h->st) ||
+        cudaMemsetAsync(h->cg_z, 0, nb, h->st) || cudaMemsetAsync(h->cg_p, 0, nb, h->st) ||
+        cudaMemsetAsync(h->cg_q, 0, nb, h->st) || cudaMemsetAsync(h->cg_b, 0, nb, h->st))
+      return bail(fail(IRK_ECUDA, "cudaMemsetAsync failed"));
+  }
   if (const char* e = getenv("IRK_NO_GRAPHS")) h->use_graphs = (e[0] == '\0' || e[0] == '0');
   *out = h;
   return IRK_OK;
@@ -493,16 +578,37 @@ struct Prec<__nv_bfloat16, float> {
 template <typename T, typename C>
 T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2) {
   using MG = MG2<T, C>;
+  using MG3T = MG3<T, C>;
   using P = Prec<T, C>;
   const int s = h->s, L = h->L;
+  const bool d3 = (h->dim == 3);
   const double p = sizeof(T), c = sizeof(C);
   Vec8 sig{};
-  for (int i = 0; i < S; ++i) sig.v[i] = h->dt * h->A[(st0 + i) * s + (st0 + i)];
+  for (int i = 0; i < S; ++i) sig.v[i] = h->dt * h->Ap[(st0 + i) * s + (st0 + i)];
   cudaStream_t st = h->st;
   const T* bl = b0;
   std::vector<T*> cur(L, nullptr);
+  auto interior = [&](const Level& Lv) {
+    const double m = Lv.nx - 2;
+    return d3 ? m * m * m : m * m;
+  };
+  // 3D: class values of B_i = M + sigma_i K and omega / B_i(centre), per level
+  auto classes = [&](const Level& Lv, Cls4& bc, Vec8& dv) {
+    for (int i = 0; i < S; ++i) {
+      for (int k = 0; k < 4; ++k) bc.v[i][k] = Lv.mcls[k] + sig.v[i] * Lv.kcls[k];
+      dv.v[i] = h->opt.omega / bc.v[i][0];
+    }
+  };
   auto sweep = [&](Level& Lv, const C* cf, const C* dinv, const T* xin, const T* b, T* xout) {
-    const double n = n_int(Lv.nx);
+    const double n = interior(Lv);
+    if (d3) {
+      Cls4 bc{};
+      Vec8 dv{};
+      classes(Lv, bc, dv);
+      KScope k(h, IRK_K_JACOBI, n * S * (xin ? 3 : 2) * p, (xin ? 34.0 : 1.0) * n * S);
+      MG3T::jacobi(S, st, Lv.nx, bc, dv, xin, b, xout);
+      return;
+    }
     const C* rec = P::rec(Lv);
     if (xin == nullptr) {
       KScope k(h, IRK_K_JACOBI, n * S * (2 * p + c), n * S);
@@ -518,8 +624,8 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2) {
   for (int l = 0; l < L - 1; ++l) {
     Level& Lv = h->lev[l];
     Level& Lc = h->lev[l + 1];
-    const C* cf = P::cf(Lv);
-    const C* dinv = P::dinv(Lv) + st0;
+    const C* cf = d3 ? nullptr : P::cf(Lv);
+    const C* dinv = d3 ? nullptr : P::dinv(Lv) + st0;
     // choose the two buffers so that the last of the nu1 + nu2 sweeps lands in `last`
     T* last = (l == 0 && x0) ? x0 : (T*)Lv.xa;
     T* other = (l == 0 && x0) ? (T*)Lv.xa : (T*)Lv.xb;
@@ -533,15 +639,25 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2) {
     sweep(Lv, cf, dinv, nullptr, bl, bufs[w]);
     for (int k = 1; k < nu1; ++k, w ^= 1) sweep(Lv, cf, dinv, bufs[w], bl, bufs[w ^ 1]);
     cur[l] = bufs[w];
-    const double nf = n_int(Lv.nx), nc = n_int(Lc.nx);
-    if (const C* rec = P::rec(Lv)) {
-      KScope k(h, IRK_K_RESIDUAL, nf * S * (3 * p + kCoef2 * c), 18.0 * nf * S);
-      MG::residual_rec(S, st, Lv.nx, rec + (size_t)st0 * Lv.nn * kCoef2, Lv.nn * kCoef2, cur[l], bl, (T*)Lv.r);
+    const double nf = interior(Lv), nc = interior(Lc);
+    if (d3) {
+      Cls4 bc{};
+      Vec8 dv{};
+      classes(Lv, bc, dv);
+      {
+        KScope k(h, IRK_K_RESIDUAL, nf * S * 3 * p, 33.0 * nf * S);
+        MG3T::residual(S, st, Lv.nx, bc, cur[l], bl, (T*)Lv.r);
+      }
+      KScope k(h, IRK_K_RESTRICT, (nf + nc) * S * p, 30.0 * nc * S);
+      MG3T::restrict_(S, st, Lv.nx, (const T*)Lv.r, Lc.nx, (T*)Lc.b);
     } else {
-      KScope k(h, IRK_K_RESIDUAL, nf * (3 * S * p + kCoef2 * c), 31.0 * nf * S);
-      MG::residual(S, st, Lv.nx, cf, Lv.hm, sig, cur[l], bl, (T*)Lv.r);
-    }
-    {
+      if (const C* rec = P::rec(Lv)) {
+        KScope k(h, IRK_K_RESIDUAL, nf * S * (3 * p + kCoef2 * c), 18.0 * nf * S);
+        MG::residual_rec(S, st, Lv.nx, rec + (size_t)st0 * Lv.nn * kCoef2, Lv.nn * kCoef2, cur[l], bl, (T*)Lv.r);
+      } else {
+        KScope k(h, IRK_K_RESIDUAL, nf * (3 * S * p + kCoef2 * c), 31.0 * nf * S);
+        MG::residual(S, st, Lv.nx, cf, Lv.hm, sig, cur[l], bl, (T*)Lv.r);
+      }
       KScope k(h, IRK_K_RESTRICT, (nf + nc) * S * p, 12.0 * nc * S);
       MG::restrict_(S, st, Lv.nx, (const T*)Lv.r, Lc.nx, (T*)Lc.b);
     }
@@ -553,19 +669,25 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2) {
     const C* binv = P::binv(h) + (size_t)st0 * h->nint * h->nint;
     const double ni = h->nint;
     KScope k(h, IRK_K_COARSE, S * ni * ni * c + 2 * S * ni * p, 2.0 * S * ni * ni);
-    MG::coarse_solve(S, st, h->nint, binv, h->cmap, bl, xc);
+    if (d3)
+      MG3T::coarse_solve(S, st, h->nint, binv, h->cmap, bl, xc);
+    else
+      MG::coarse_solve(S, st, h->nint, binv, h->cmap, bl, xc);
     cur[L - 1] = xc;
   }
   for (int l = L - 2; l >= 0; --l) {
     Level& Lv = h->lev[l];
     Level& Lc = h->lev[l + 1];
-    const C* cf = P::cf(Lv);
-    const C* dinv = P::dinv(Lv) + st0;
+    const C* cf = d3 ? nullptr : P::cf(Lv);
+    const C* dinv = d3 ? nullptr : P::dinv(Lv) + st0;
     const T* bfine = (l == 0) ? b0 : (const T*)Lv.b;
-    const double nf = n_int(Lv.nx), nc = n_int(Lc.nx);
+    const double nf = interior(Lv), nc = interior(Lc);
     {
-      KScope k(h, IRK_K_PROLONG, (nc + 2 * nf) * S * p, 5.0 * nf * S);
-      MG::prolong_add(S, st, Lc.nx, cur[l + 1], Lv.nx, cur[l]);
+      KScope k(h, IRK_K_PROLONG, (nc + 2 * nf) * S * p, (d3 ? 9.0 : 5.0) * nf * S);
+      if (d3)
+        MG3T::prolong_add(S, st, Lc.nx, cur[l + 1], Lv.nx, cur[l]);
+      else
+        MG::prolong_add(S, st, Lc.nx, cur[l + 1], Lv.nx, cur[l]);
     }
     T* last = (l == 0 && x0) ? x0 : (T*)Lv.xa;
     T* other = (l == 0 && x0) ? (T*)Lv.xa : (T*)Lv.xb;
@@ -609,27 +731,36 @@ int precond_apply(irk_handle* h, const double* v, double* z, bool transpose) {
     return IRK_OK;
   }
   // triangular sweep: lower (forward) or upper (backward) in the effective matrix
-  bool lower = (h->opt.precond == IRK_PC_LOWER);
+  bool lower = (h->opt.precond == IRK_PC_LOWER || h->opt.precond == IRK_PC_RANA_LD);
   if (transpose) lower = !lower;
-  const C* cf = Prec<T, C>::cf(L0);
-  const double n = n_int(L0.nx);
+  const bool d3 = (h->dim == 3);
+  const C* cf = d3 ? nullptr : Prec<T, C>::cf(L0);
+  const double n = d3 ? (double)(L0.nx - 2) * (L0.nx - 2) * (L0.nx - 2) : n_int(L0.nx);
+  Cls4 kc{};
+  for (int k = 0; k < 4; ++k) kc.v[0][k] = L0.kcls[k];
   for (int step = 0; step < s; ++step) {
     const int i = lower ? step : s - 1 - step;
     Vec8 cj{};
     int done = 0;
     for (int j = 0; j < s; ++j) {
       const bool solved = lower ? (j < i) : (j > i);
-      const double a = transpose ? h->A[j * s + i] : h->A[i * s + j];
+      const double a = transpose ? h->Ap[j * s + i] : h->Ap[i * s + j];
       cj.v[j] = solved ? h->dt * a : 0.0;
       done += (solved && a != 0.0) ? 1 : 0;
     }
     {  // single-stage right-hand side in level-0 b (precision T)
-      KScope k(h, IRK_K_BLOCK_RHS, n * (8 + done * 8 + kCoef2 * c + p), 19.0 * done * n);
-      MG::block_rhs(s, st, L0.nx, cf, v, z, i, cj, (T*)L0.b);
+      KScope k(h, IRK_K_BLOCK_RHS, n * (8 + done * 8 + (d3 ? 0 : kCoef2 * c) + p), (d3 ? 32.0 : 19.0) * done * n);
+      if (d3)
+        MG3<T, C>::block_rhs(s, st, L0.nx, kc, v, z, i, cj, (T*)L0.b);
+      else
+        MG::block_rhs(s, st, L0.nx, cf, v, z, i, cj, (T*)L0.b);
     }
     T* x = vcycle<T, C>(h, 1, i, (const T*)L0.b, nullptr, nu1, nu2);
     KScope k(h, IRK_K_OTHER, n * (p + 8), 0);
-    MG::scatter_stage(s, st, L0.nx, x, i, z);
+    if (d3)
+      MG3<T, C>::scatter_stage(s, st, L0.nx, x, i, z);
+    else
+      MG::scatter_stage(s, st, L0.nx, x, i, z);
   }
   CK_LAUNCH();
   return IRK_OK;
@@ -651,9 +782,22 @@ Mat4 mixing(const irk_handle* h, bool transpose) {
   return m;
 }
 
+Cls4 mass_stiff_classes(const Level& L0) {
+  Cls4 mk{};
+  for (int k = 0; k < 4; ++k) mk.v[0][k] = L0.mcls[k], mk.v[1][k] = L0.kcls[k];
+  return mk;
+}
+
 int apply_operator(irk_handle* h, const double* x, double* y, bool transpose) {
   const Level& L0 = h->lev[0];
   const int s = h->s;
+  if (h->dim == 3) {
+    const double m = L0.nx - 2;
+    KScope k(h, IRK_K_STAGE_APPLY, (double)L0.nn * 16.0 * s, m * m * m * s * (38.0 + 2.0 * s));
+    launch_stage_apply3(s, h->st, L0.nx, mass_stiff_classes(L0), mixing(h, transpose), x, y);
+    CK_LAUNCH();
+    return IRK_OK;
+  }
   KScope k(h, IRK_K_STAGE_APPLY, (double)L0.nn * (16.0 * s + 8.0 * kCoef2), n_int(L0.nx) * s * (28.0 + 2.0 * s));
   launch_stage_apply(s, h->st, L0.nx, L0.cf_d, L0.hm, mixing(h, transpose), x, y);
   CK_LAUNCH();
@@ -757,11 +901,10 @@ int arnoldi_step(irk_handle* h, int j, bool transpose) {
   return IRK_OK;
 }
 
-// Capture arnoldi_step(j) on the private capture stream and instantiate it.  The
-// instrumentation counters the capture produced are kept as the graph's per-replay
-// increment (the capture itself runs nothing).
-int capture_arnoldi_step(irk_handle* h, int j, bool transpose) {
-  auto& G = h->graphs[transpose ? 1 : 0][j];
+// Capture body() on the private capture stream into G and instantiate it.  The
+// instrumentation counters the capture produced are kept as the graph's
+// per-replay increment (the capture itself runs nothing).
+int capture_graph(irk_handle* h, irk_handle::IterGraph& G, const std::function<int()>& body) {
   const irk_perf before = h->perf;
   const int vc_before = h->vcycles;
   cudaStream_t saved = h->st;
@@ -771,12 +914,14 @@ int capture_arnoldi_step(irk_handle* h, int j, bool transpose) {
     h->st = saved;
     return fail(IRK_ECUDA, "cudaStreamBeginCapture failed: %s", cudaGetErrorString(e));
   }
-  const int rc = arnoldi_step(h, j, transpose);
+  const int rc = body();
   cudaGraph_t graph = nullptr;
   e = cudaStreamEndCapture(h->st, &graph);
   h->st = saved;
   if (rc != IRK_OK) {
     if (graph) cudaGraphDestroy(graph);
+    h->perf = before;
+    h->vcycles = vc_before;
     return rc;
   }
   if (e != cudaSuccess) return fail(IRK_ECUDA, "cudaStreamEndCapture failed: %s", cudaGetErrorString(e));
@@ -800,11 +945,10 @@ int capture_arnoldi_step(irk_handle* h, int j, bool transpose) {
   return IRK_OK;
 }
 
-// Run Arnoldi step j: replay its graph (eager launches while kernels are being timed).
-int run_arnoldi_step(irk_handle* h, int j, bool transpose) {
-  if (!h->use_graphs || h->perf_mask != 0) return arnoldi_step(h, j, transpose);
-  auto& G = h->graphs[transpose ? 1 : 0][j];
-  if (!G.exec) TRY(capture_arnoldi_step(h, j, transpose));
+// Run body() through its cached graph G (eager launches while kernels are being timed).
+int run_graph(irk_handle* h, irk_handle::IterGraph& G, const std::function<int()>& body) {
+  if (!h->use_graphs || h->perf_mask != 0) return body();
+  if (!G.exec) TRY(capture_graph(h, G, body));
   CK(cudaGraphLaunch(G.exec, h->st));
   h->perf.launches += G.delta.launches;
   for (int c = 0; c < IRK_K_COUNT; ++c) {
@@ -814,6 +958,10 @@ int run_arnoldi_step(irk_handle* h, int j, bool transpose) {
   }
   h->vcycles += G.vcycles;
   return IRK_OK;
+}
+
+int run_arnoldi_step(irk_handle* h, int j, bool transpose) {
+  return run_graph(h, h->graphs[transpose ? 1 : 0][j], [h, j, transpose] { return arnoldi_step(h, j, transpose); });
 }
 
 int fgmres(irk_handle* h, const double* rhs, double* x, bool transpose, irk_stats* stats) {
@@ -878,6 +1026,175 @@ int fgmres(irk_handle* h, const double* rhs, double* x, bool transpose, irk_stat
   return IRK_OK;
 }
 
+// ----------------------------------------------------------------------------
+// DIRK path: for lower-triangular A the stage system is block lower triangular,
+// so the stages follow one after another (Sec. 2.3):
+//   (M + dt a_ii K) k_i = r_i - dt sum_{j<i} a_ij K k_j,
+// each solved by conjugate gradients preconditioned with one V-cycle of the same
+// block (symmetric positive definite: the V(nu, nu) cycle with Jacobi smoothing is
+// symmetric; with nu_pre != nu_post CG still runs but loses that guarantee).
+// transpose: the adjoint system, upper triangular in A^T, runs the stages backwards.
+// ----------------------------------------------------------------------------
+template <typename T, typename C>
+void cg_precondition(irk_handle* h, int i, const double* r, double* z, bool transpose) {
+  const int nu1 = transpose ? h->opt.nu_post : h->opt.nu_pre;
+  const int nu2 = transpose ? h->opt.nu_pre : h->opt.nu_post;
+  if constexpr (std::is_same<T, double>::value) {
+    vcycle<T, C>(h, 1, i, r, z, nu1, nu2);
+  } else {
+    using MG = MG2<T, C>;
+    Level& L0 = h->lev[0];
+    const double n = (double)L0.nn, p = sizeof(T);
+    {
+      KScope k(h, IRK_K_OTHER, n * (8 + p), 0);
+      MG::cast_to(h->st, r, (T*)L0.b, L0.nn);
+    }
+    T* x = vcycle<T, C>(h, 1, i, (const T*)L0.b, nullptr, nu1, nu2);
+    KScope k(h, IRK_K_OTHER, n * (8 + p), 0);
+    MG::cast_from(h->st, x, z, L0.nn);
+  }
+}
+
+void cg_prec(irk_handle* h, int i, const double* r, double* z, bool transpose) {
+  switch (h->opt.vcycle_prec) {
+    case IRK_PREC_FP64: cg_precondition<double, double>(h, i, r, z, transpose); break;
+    case IRK_PREC_FP32: cg_precondition<float, float>(h, i, r, z, transpose); break;
+    default: cg_precondition<__nv_bfloat16, float>(h, i, r, z, transpose); break;
+  }
+}
+
+// dot(a, b) of single-stage vectors into scal[slot]
+void dot1(irk_handle* h, const double* a, const double* b, int slot) {
+  const size_t n = h->lev[0].nn;
+  {
+    KScope k(h, IRK_K_MULTIDOT, 16.0 * n, 2.0 * n);
+    launch_multidot(h->st, a, 0, 1, b, n, h->partial);
+  }
+  KScope k(h, IRK_K_OTHER, 0, 0);
+  launch_reduce_partials(h->st, h->partial, 1, h->scal + slot);
+}
+
+void block_apply(irk_handle* h, int i, const double* x, double* y) {
+  const Level& L0 = h->lev[0];
+  const double sigma = h->dt * h->A[i * h->s + i];
+  if (h->dim == 3) {
+    const double m = L0.nx - 2;
+    KScope k(h, IRK_K_OTHER, 16.0 * L0.nn, 38.0 * m * m * m);
+    launch_block_apply3(h->st, L0.nx, mass_stiff_classes(L0), sigma, x, y);
+  } else {
+    KScope k(h, IRK_K_OTHER, 16.0 * L0.nn + 8.0 * kCoef2 * L0.nn, 31.0 * n_int(L0.nx));
+    launch_block_apply(h->st, L0.nx, L0.cf_d, L0.hm, sigma, x, y);
+  }
+}
+
+// One PCG iteration for stage i; ends by copying ||r||^2 to pinned host memory.
+// scal: 10 rz, 11 pq, 12 alpha, 13 beta, 14 rr, 15 rz_new.
+int cg_iteration(irk_handle* h, int i, bool transpose) {
+  cudaStream_t st = h->st;
+  const size_t n = h->lev[0].nn;
+  block_apply(h, i, h->cg_p, h->cg_q);
+  dot1(h, h->cg_p, h->cg_q, 11);
+  {
+    KScope k(h, IRK_K_OTHER, 0, 0);
+    launch_cg_alpha(st, h->scal + 10, h->scal + 11, h->scal + 12);
+  }
+  {
+    KScope k(h, IRK_K_AXPY, 48.0 * n, 4.0 * n);
+    launch_cg_update_xr(st, h->cg_x, h->cg_r, h->cg_p, h->cg_q, h->scal + 12, n);
+  }
+  dot1(h, h->cg_r, h->cg_r, 14);
+  CK_LAUNCH();
+  CK(cudaMemcpyAsync(h->pinned + 4, h->scal + 14, 8, cudaMemcpyDeviceToHost, st));
+  cg_prec(h, i, h->cg_r, h->cg_z, transpose);
+  dot1(h, h->cg_r, h->cg_z, 15);
+  {
+    KScope k(h, IRK_K_OTHER, 0, 0);
+    launch_cg_beta(st, h->scal + 15, h->scal + 10, h->scal + 13);
+  }
+  {
+    KScope k(h, IRK_K_AXPY, 24.0 * n, 2.0 * n);
+    launch_cg_update_p(st, h->cg_p, h->cg_z, h->scal + 13, n);
+  }
+  CK_LAUNCH();
+  return IRK_OK;
+}
+
+int dirk_solve(irk_handle* h, const double* rhs, double* k, bool transpose, irk_stats* stats) {
+  cudaStream_t st = h->st;
+  const int s = h->s;
+  Level& L0 = h->lev[0];
+  const size_t nn = L0.nn;
+  h->vcycles = 0;
+  CK(cudaMemsetAsync(k, 0, h->ne * 8, st));
+  int its = 0;
+  double worst = 0.0;
+  bool conv = true;
+  Cls4 kc{};
+  for (int c = 0; c < 4; ++c) kc.v[0][c] = L0.kcls[c];
+  for (int step = 0; step < s; ++step) {
+    const int i = transpose ? s - 1 - step : step;
+    Vec8 cj{};
+    for (int j = 0; j < s; ++j) {
+      const bool solved = transpose ? (j > i) : (j < i);
+      cj.v[j] = solved ? h->dt * (transpose ? h->A[j * s + i] : h->A[i * s + j]) : 0.0;
+    }
+    {  // b = r_i - dt sum_j a_ij K k_j
+      KScope kk(h, IRK_K_BLOCK_RHS, (double)nn * 8 * (2 + s), 19.0 * s * (double)nn);
+      if (h->dim == 3)
+        MG3<double, double>::block_rhs(s, st, L0.nx, kc, rhs, k, i, cj, h->cg_b);
+      else
+        MG2<double, double>::block_rhs(s, st, L0.nx, L0.cf_d, rhs, k, i, cj, h->cg_b);
+    }
+    dot1(h, h->cg_b, h->cg_b, 14);
+    CK_LAUNCH();
+    CK(cudaMemcpyAsync(h->pinned + 4, h->scal + 14, 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const double bb = h->pinned[4];
+    if (!std::isfinite(bb)) return fail(IRK_ENONFINITE, "stage %d right-hand side norm is %g", i, bb);
+    double rel = 0.0;
+    if (bb > 0.0) {
+      CK(cudaMemsetAsync(h->cg_x, 0, nn * 8, st));
+      CK(cudaMemcpyAsync(h->cg_r, h->cg_b, nn * 8, cudaMemcpyDeviceToDevice, st));
+      cg_prec(h, i, h->cg_r, h->cg_z, transpose);
+      CK(cudaMemcpyAsync(h->cg_p, h->cg_z, nn * 8, cudaMemcpyDeviceToDevice, st));
+      dot1(h, h->cg_r, h->cg_z, 10);
+      int it = 0;
+      rel = 1.0;
+      while (it < h->opt.maxit) {
+        auto& G = h->cg_graphs[transpose ? 1 : 0][i];
+        TRY(run_graph(h, G, [h, i, transpose] { return cg_iteration(h, i, transpose); }));
+        CK(cudaStreamSynchronize(st));
+        ++it;
+        rel = std::sqrt(std::max(h->pinned[4], 0.0) / bb);
+        if (!std::isfinite(h->pinned[4])) return fail(IRK_ENONFINITE, "CG residual is %g", h->pinned[4]);
+        if (rel <= h->opt.rtol) break;
+      }
+      its += it;
+      if (rel > h->opt.rtol) conv = false;
+    }
+    worst = std::max(worst, rel);
+    KScope kk(h, IRK_K_OTHER, (double)nn * 16, 0);
+    if (h->dim == 3)
+      MG3<double, double>::scatter_stage(s, st, L0.nx, h->cg_x, i, k);
+    else
+      MG2<double, double>::scatter_stage(s, st, L0.nx, h->cg_x, i, k);
+  }
+  CK_LAUNCH();
+  if (stats) {
+    stats->fgmres_its = its;
+    stats->vcycles = h->vcycles;
+    stats->rel_resid = worst;
+    stats->converged = conv ? 1 : 0;
+  }
+  if (!conv) return fail(IRK_ENOCONV, "CG stopped at maxit = %d with relative residual %g", h->opt.maxit, worst);
+  return IRK_OK;
+}
+
+int solve(irk_handle* h, const double* rhs, double* k, bool transpose, irk_stats* stats) {
+  if (h->opt.solver == IRK_SOLVER_DIRK_CG) return dirk_solve(h, rhs, k, transpose, stats);
+  return fgmres(h, rhs, k, transpose, stats);
+}
+
 }  // namespace
 
 // ============================================================================
@@ -896,6 +1213,7 @@ void irk_default_options(irk_options* o) {
   o->restart = 50;
   o->maxit = 500;
   o->orth = IRK_ORTH_CGS2;
+  o->solver = IRK_SOLVER_FGMRES;
 }
 
 const char* irk_last_error(void) { return g_err.c_str(); }
@@ -936,6 +1254,7 @@ int irk_destroy(irk_handle* h) {
 
 int irk_set_kappa(irk_handle* h, const double* kappa) {
   if (!h) return fail(IRK_EINVAL, "null handle");
+  if (h->dim != 2) return fail(IRK_EINVAL, "irk_set_kappa: dim = 3 supports kappa = 1 only");
   if (!kappa) return fail(IRK_EINVAL, "null kappa");
   try {
     const size_t nc = (size_t)h->N * h->N;
@@ -959,6 +1278,26 @@ int irk_apply_operator(irk_handle* h, const double* x, double* y, int transpose)
   TRY(dev_in(h, x, bytes, 0, &xd));
   TRY(dev_out(h, y, bytes, 1, &yd, &yhost));
   TRY(apply_operator(h, (const double*)xd, (double*)yd, transpose != 0));
+  if (yhost) TRY(dev_out_finish(h, y, yd, bytes));
+  CK(cudaStreamSynchronize(h->st));
+  return IRK_OK;
+}
+
+int irk_apply_mass(irk_handle* h, const double* x, double* y) {
+  if (!h || !x || !y) return fail(IRK_EINVAL, "null argument");
+  if (h->dim != 2) return fail(IRK_EINVAL, "irk_apply_mass is implemented for dim = 2");
+  const Level& L0 = h->lev[0];
+  const size_t bytes = L0.nn * 8;
+  const void* xd;
+  void* yd;
+  bool yhost;
+  TRY(dev_in(h, x, bytes, 0, &xd));
+  TRY(dev_out(h, y, bytes, 1, &yd, &yhost));
+  {
+    KScope k(h, IRK_K_OTHER, 16.0 * L0.nn, 11.0 * n_int(L0.nx));
+    launch_mass_apply(h->st, L0.nx, L0.hm, (const double*)xd, (double*)yd);
+  }
+  CK_LAUNCH();
   if (yhost) TRY(dev_out_finish(h, y, yd, bytes));
   CK(cudaStreamSynchronize(h->st));
   return IRK_OK;
@@ -989,7 +1328,7 @@ int irk_solve(irk_handle* h, const double* r, double* k, irk_stats* stats) {
   bool khost;
   TRY(dev_in(h, r, bytes, 0, &rd));
   TRY(dev_out(h, k, bytes, 1, &kd, &khost));
-  const int rc = fgmres(h, (const double*)rd, (double*)kd, false, stats);
+  const int rc = solve(h, (const double*)rd, (double*)kd, false, stats);
   if (rc != IRK_OK && rc != IRK_ENOCONV) return rc;
   if (khost) TRY(dev_out_finish(h, k, kd, bytes));
   CK(cudaStreamSynchronize(h->st));
@@ -1015,17 +1354,24 @@ int irk_step(irk_handle* h, const double* u_n, const double* f_space, const doub
     const double nn_d = (double)nn;
     KScope k(h, IRK_K_OTHER, nn_d * (8 + 8 + 8.0 * kCoef2 + 8.0 * s + (fsd ? 8.0 * s : 0.0)),
              n_int(h->lev[0].nx) * (17.0 + 2.0 * s));
-    launch_rhs(s, h->st, h->lev[0].nx, h->lev[0].cf_d, (const double*)ud, (const double*)fd, fc,
-               (const double*)fsd, h->rhs);
+    if (h->dim == 3)
+      launch_rhs3(s, h->st, h->lev[0].nx, mass_stiff_classes(h->lev[0]), (const double*)ud, (const double*)fd, fc,
+                  (const double*)fsd, h->rhs);
+    else
+      launch_rhs(s, h->st, h->lev[0].nx, h->lev[0].cf_d, (const double*)ud, (const double*)fd, fc,
+                 (const double*)fsd, h->rhs);
   }
   CK_LAUNCH();
-  const int rc = fgmres(h, h->rhs, h->k, false, stats);
+  const int rc = solve(h, h->rhs, h->k, false, stats);
   if (rc != IRK_OK && rc != IRK_ENOCONV) return rc;
   Vec8 bdt{};
   for (int i = 0; i < s; ++i) bdt.v[i] = h->dt * h->b[i];
   {
     KScope k(h, IRK_K_OTHER, (double)nn * (16.0 + 8.0 * s), 2.0 * s * n_int(h->lev[0].nx));
-    launch_rk_update(s, h->st, h->lev[0].nx, (const double*)ud, h->k, bdt, (double*)outd);
+    if (h->dim == 3)
+      launch_rk_update3(s, h->st, h->lev[0].nx, (const double*)ud, h->k, bdt, (double*)outd);
+    else
+      launch_rk_update(s, h->st, h->lev[0].nx, (const double*)ud, h->k, bdt, (double*)outd);
   }
   CK_LAUNCH();
   if (kd) CK(cudaMemcpyAsync(kd, h->k, sb, cudaMemcpyDeviceToDevice, h->st));
@@ -1038,6 +1384,7 @@ int irk_step(irk_handle* h, const double* u_n, const double* f_space, const doub
 int irk_step_adjoint(irk_handle* h, const double* u_n, const double* stages, const double* lam_np1, double* lam_n,
                      double* grad_accum, irk_stats* stats) {
   if (!h || !u_n || !stages || !lam_np1 || !lam_n) return fail(IRK_EINVAL, "null argument");
+  if (h->dim != 2) return fail(IRK_EINVAL, "irk_step_adjoint is implemented for dim = 2");
   const int s = h->s;
   const size_t nn = h->lev[0].nn, nb = nn * 8, sb = h->ne * 8, gb = (size_t)h->N * h->N * 8;
   const void *ud, *kd, *ld;
@@ -1065,7 +1412,7 @@ int irk_step_adjoint(irk_handle* h, const double* u_n, const double* stages, con
     launch_rhs(s, h->st, h->lev[0].nx, h->lev[0].cf_d, nullptr, (const double*)ld, fc, nullptr, h->rhs);
   }
   CK_LAUNCH();
-  const int rc = fgmres(h, h->rhs, h->k, true, stats);  // h->k = mu
+  const int rc = solve(h, h->rhs, h->k, true, stats);  // h->k = mu
   if (rc != IRK_OK && rc != IRK_ENOCONV) return rc;
   if (gd) {
     Mat4 dtA = mixing(h, false);

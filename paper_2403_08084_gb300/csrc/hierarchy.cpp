@@ -231,4 +231,73 @@ bool dense_block_inverse_2d(int N, const std::vector<double>& cf, double hm, dou
   return true;
 }
 
+void q1_classes_3d(double h, double mass[4], double stiff[4]) {
+  // 1D linear elements: m(0) = 4h/6, m(1) = h/6; k(0) = 2/h, k(1) = -1/h.  The Q1 matrices are
+  // M = m (x) m (x) m and K = k (x) m (x) m + m (x) k (x) m + m (x) m (x) k.
+  const double m0 = 4.0 * h / 6.0, m1 = h / 6.0, k0 = 2.0 / h, k1 = -1.0 / h;
+  for (int nz = 0; nz <= 3; ++nz) {
+    const int z = 3 - nz;
+    mass[nz] = std::pow(m1, nz) * std::pow(m0, z);
+    double kv = 0.0;
+    if (nz > 0) kv += nz * k1 * std::pow(m1, nz - 1) * std::pow(m0, z);
+    if (z > 0) kv += z * k0 * std::pow(m1, nz) * std::pow(m0, z - 1);
+    stiff[nz] = kv;
+  }
+}
+
+void interior_nodes_3d(int N, std::vector<int>& map) {
+  const int n = N + 1;
+  map.clear();
+  for (int iz = 1; iz < n - 1; ++iz)
+    for (int iy = 1; iy < n - 1; ++iy)
+      for (int ix = 1; ix < n - 1; ++ix) map.push_back(ix + n * (iy + n * iz));
+}
+
+bool dense_block_inverse_3d(int N, const double mass[4], const double stiff[4], double sigma,
+                            const std::vector<int>& map, std::vector<double>& inv) {
+  const int n = N + 1, m = n - 2;
+  const int cnt = (int)map.size();
+  auto idx = [&](int ix, int iy, int iz) { return (ix - 1) + m * ((iy - 1) + m * (iz - 1)); };
+  std::vector<double> B((size_t)cnt * cnt, 0.0);
+  for (int iz = 1; iz <= m; ++iz)
+    for (int iy = 1; iy <= m; ++iy)
+      for (int ix = 1; ix <= m; ++ix) {
+        const int r = idx(ix, iy, iz);
+        for (int dz = -1; dz <= 1; ++dz)
+          for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+              const int jx = ix + dx, jy = iy + dy, jz = iz + dz;
+              if (!interior(jx, jy, n) || jz < 1 || jz > m) continue;
+              const int cls = (dx != 0) + (dy != 0) + (dz != 0);
+              B[(size_t)r * cnt + idx(jx, jy, jz)] = mass[cls] + sigma * stiff[cls];
+            }
+      }
+  // Gauss-Jordan with partial pivoting (the coarsest 3D level is small)
+  inv.assign((size_t)cnt * cnt, 0.0);
+  for (int r = 0; r < cnt; ++r) inv[(size_t)r * cnt + r] = 1.0;
+  for (int k = 0; k < cnt; ++k) {
+    int piv = k;
+    double best = std::fabs(B[(size_t)k * cnt + k]);
+    for (int r = k + 1; r < cnt; ++r)
+      if (std::fabs(B[(size_t)r * cnt + k]) > best) best = std::fabs(B[(size_t)r * cnt + k]), piv = r;
+    if (!(best > 0.0) || !std::isfinite(best)) return false;
+    if (piv != k)
+      for (int c = 0; c < cnt; ++c) {
+        std::swap(B[(size_t)k * cnt + c], B[(size_t)piv * cnt + c]);
+        std::swap(inv[(size_t)k * cnt + c], inv[(size_t)piv * cnt + c]);
+      }
+    const double d = 1.0 / B[(size_t)k * cnt + k];
+    for (int c = 0; c < cnt; ++c) B[(size_t)k * cnt + c] *= d, inv[(size_t)k * cnt + c] *= d;
+    for (int r = 0; r < cnt; ++r) {
+      if (r == k) continue;
+      const double f = B[(size_t)r * cnt + k];
+      if (f == 0.0) continue;
+      for (int c = 0; c < cnt; ++c) B[(size_t)r * cnt + c] -= f * B[(size_t)k * cnt + c];
+      for (int c = 0; c < cnt; ++c) inv[(size_t)r * cnt + c] -= f * inv[(size_t)k * cnt + c];
+    }
+  }
+  (void)map;
+  return true;
+}
+
 }  // namespace irk

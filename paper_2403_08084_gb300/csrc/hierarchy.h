@@ -31,4 +31,14 @@ void interior_nodes_2d(int N, std::vector<int>& map);
 bool dense_block_inverse_2d(int N, const std::vector<double>& cf, double hm, double sigma,
                             const std::vector<int>& map, std::vector<double>& inv);
 
+// 3D, kappa = 1: values of the Q1 mass and stiffness 27-point stencils on a grid
+// of spacing h by offset class (number of nonzero offset coordinates 0..3).
+void q1_classes_3d(double h, double mass[4], double stiff[4]);
+
+// Interior node ids of an N^3-cell grid and the dense inverse of M + sigma K
+// (constant-coefficient classes) restricted to them.
+void interior_nodes_3d(int N, std::vector<int>& map);
+bool dense_block_inverse_3d(int N, const double mass[4], const double stiff[4], double sigma,
+                            const std::vector<int>& map, std::vector<double>& inv);
+
 }  // namespace irk

@@ -11,6 +11,12 @@ namespace irk {
 struct Vec8;
 struct Mat4;
 
+// 3D constant-coefficient stencils: per stage, the values of the four offset classes
+// (centre, 6 faces, 12 edges, 8 corners) of a 27-point Q1 stencil.
+struct Cls4 {
+  double v[4][4];
+};
+
 // Multigrid kernels for one precision: storage T, arithmetic C (mg2d.cuh).
 template <typename T, typename C>
 struct MG2 {
@@ -33,6 +39,27 @@ struct MG2 {
   static void coarse_solve(int S, cudaStream_t st, int nint, const C* binv, const int* map, const T* b, T* x);
 };
 
+// 3D multigrid kernels (mg3d.cuh), constant-coefficient stencils.
+template <typename T, typename C>
+struct MG3 {
+  static void jacobi(int S, cudaStream_t st, int n, const Cls4& bc, const Vec8& dinv, const T* xin, const T* b,
+                     T* xout);
+  static void residual(int S, cudaStream_t st, int n, const Cls4& bc, const T* x, const T* b, T* r);
+  static void restrict_(int S, cudaStream_t st, int nf, const T* rf, int nc, T* bc);
+  static void prolong_add(int S, cudaStream_t st, int nc, const T* ec, int nf, T* xf);
+  static void block_rhs(int SF, cudaStream_t st, int n, const Cls4& kc, const double* v, const double* z, int i,
+                        const Vec8& cj, T* out);
+  static void scatter_stage(int SF, cudaStream_t st, int n, const T* x, int i, double* z);
+  static void coarse_solve(int S, cudaStream_t st, int nint, const C* binv, const int* map, const T* b, T* x);
+};
+
+// FP64 3D stage-operator kernels (op3d.cu); mc / kc: mass / stiffness class values in v[0].
+void launch_stage_apply3(int S, cudaStream_t st, int n, const Cls4& mk, const Mat4& mix, const double* x, double* y);
+void launch_rhs3(int S, cudaStream_t st, int n, const Cls4& mk, const double* u, const double* fsp,
+                 const Vec8& fcoef, const double* fst, double* r);
+void launch_block_apply3(cudaStream_t st, int n, const Cls4& mk, double sigma, const double* x, double* y);
+void launch_rk_update3(int S, cudaStream_t st, int n, const double* u, const double* k, const Vec8& bdt, double* out);
+
 // FP64 stage-operator kernels (op2d.cu).
 void launch_stage_apply(int S, cudaStream_t st, int nx, const double* cf, double hm, const Mat4& mix, const double* x,
                         double* y);
@@ -42,6 +69,9 @@ void launch_rk_update(int S, cudaStream_t st, int nx, const double* u, const dou
                       double* out);
 void launch_adjoint_lambda(int S, cudaStream_t st, int nx, const double* cf, const double* lam_np1, const double* mu,
                            double* lam_n);
+void launch_block_apply(cudaStream_t st, int nx, const double* cf, double hm, double sigma, const double* x,
+                        double* y);
+void launch_mass_apply(cudaStream_t st, int nx, double hm, const double* x, double* y);
 void launch_cell_gradient(int S, cudaStream_t st, int N, const double* kappa, const double* u, const double* k,
                           const Mat4& dtA, const double* mu, double* grad);
 
@@ -62,6 +92,11 @@ void launch_givens(cudaStream_t st, int j, int ldh, double* H, double* cs, doubl
                    const double* h2, const double* hn2, double* hn_out, const double* r0, double* rel_out);
 void launch_trisolve(cudaStream_t st, int J, int ldh, const double* H, const double* g, double* y);
 void launch_sqrt_scalar(cudaStream_t st, const double* in, double* out);
+void launch_cg_alpha(cudaStream_t st, const double* rz, const double* pq, double* alpha);
+void launch_cg_beta(cudaStream_t st, const double* rz_new, double* rz_old, double* beta);
+void launch_cg_update_xr(cudaStream_t st, double* x, double* r, const double* p, const double* q, const double* alpha,
+                         size_t n);
+void launch_cg_update_p(cudaStream_t st, double* p, const double* z, const double* beta, size_t n);
 void launch_sub(cudaStream_t st, double* out, const double* a, const double* b, size_t n);
 void launch_init_g(cudaStream_t st, double* g, int m1, const double* beta);
 

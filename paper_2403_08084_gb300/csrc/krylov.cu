@@ -193,6 +193,37 @@ __global__ void init_g_kernel(double* __restrict__ g, int m1, const double* __re
   for (int i = threadIdx.x; i < m1; i += blockDim.x) g[i] = (i == 0) ? *beta : 0.0;
 }
 
+// Conjugate-gradient pieces with scalars kept on the device.
+__global__ void cg_alpha_kernel(const double* __restrict__ rz, const double* __restrict__ pq,
+                                double* __restrict__ alpha) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *alpha = (*pq != 0.0) ? *rz / *pq : 0.0;
+}
+__global__ void cg_beta_kernel(const double* __restrict__ rz_new, double* __restrict__ rz_old,
+                               double* __restrict__ beta) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    *beta = (*rz_old != 0.0) ? *rz_new / *rz_old : 0.0;
+    *rz_old = *rz_new;
+  }
+}
+// x += alpha p, r -= alpha q
+__global__ void __launch_bounds__(kThreads) cg_update_xr_kernel(double* __restrict__ x, double* __restrict__ r,
+                                                                const double* __restrict__ p,
+                                                                const double* __restrict__ q,
+                                                                const double* __restrict__ alpha, size_t n) {
+  const double a = *alpha;
+  for (size_t e = blockIdx.x * (size_t)kThreads + threadIdx.x; e < n; e += (size_t)gridDim.x * kThreads) {
+    x[e] = fma(a, p[e], x[e]);
+    r[e] = fma(-a, q[e], r[e]);
+  }
+}
+// p = z + beta p
+__global__ void __launch_bounds__(kThreads) cg_update_p_kernel(double* __restrict__ p, const double* __restrict__ z,
+                                                               const double* __restrict__ beta, size_t n) {
+  const double b = *beta;
+  for (size_t e = blockIdx.x * (size_t)kThreads + threadIdx.x; e < n; e += (size_t)gridDim.x * kThreads)
+    p[e] = fma(b, p[e], z[e]);
+}
+
 int grid_for(size_t n) {
   size_t b = (n + kThreads - 1) / kThreads;
   if (b > (size_t)kPartialBlocks) b = kPartialBlocks;
@@ -230,6 +261,19 @@ void launch_trisolve(cudaStream_t st, int J, int ldh, const double* H, const dou
 }
 void launch_sub(cudaStream_t st, double* out, const double* a, const double* b, size_t n) {
   sub_kernel<<<grid_for(n), kThreads, 0, st>>>(out, a, b, n);
+}
+void launch_cg_alpha(cudaStream_t st, const double* rz, const double* pq, double* alpha) {
+  cg_alpha_kernel<<<1, 32, 0, st>>>(rz, pq, alpha);
+}
+void launch_cg_beta(cudaStream_t st, const double* rz_new, double* rz_old, double* beta) {
+  cg_beta_kernel<<<1, 32, 0, st>>>(rz_new, rz_old, beta);
+}
+void launch_cg_update_xr(cudaStream_t st, double* x, double* r, const double* p, const double* q, const double* alpha,
+                         size_t n) {
+  cg_update_xr_kernel<<<grid_for(n), kThreads, 0, st>>>(x, r, p, q, alpha, n);
+}
+void launch_cg_update_p(cudaStream_t st, double* p, const double* z, const double* beta, size_t n) {
+  cg_update_p_kernel<<<grid_for(n), kThreads, 0, st>>>(p, z, beta, n);
 }
 void launch_sqrt_scalar(cudaStream_t st, const double* in, double* out) { sqrt_scalar_kernel<<<1, 32, 0, st>>>(in, out); }
 void launch_init_g(cudaStream_t st, double* g, int m1, const double* beta) { init_g_kernel<<<1, 128, 0, st>>>(g, m1, beta); }

@@ -119,6 +119,34 @@ __global__ void adjoint_lambda_kernel(int nx, const double* __restrict__ cf, con
   lam0[p] = v;
 }
 
+// y = (M + sigma K) x for one internal single-stage vector (boundary entries zero).
+__global__ void block_apply_kernel(int nx, const double* __restrict__ cf, double hm, double sigma,
+                                   const double* __restrict__ x, double* __restrict__ y) {
+  const int ix = 1 + blockIdx.x * BX + threadIdx.x;
+  const int iy = 1 + blockIdx.y * BY + threadIdx.y;
+  if (ix > nx - 2 || iy > nx - 2) return;
+  const int p = ix + nx * iy;
+  y[p] = hm * m_apply_unscaled<1, double>(x, p, nx, 0) + sigma * k_apply<1, double>(cf, x, p, nx, 0);
+}
+
+// y = M x for a caller-supplied nodal vector (boundary entries of x read as 0).
+__global__ void mass_apply_kernel(int nx, double hm, const double* __restrict__ x, double* __restrict__ y) {
+  const int ix = blockIdx.x * BX + threadIdx.x;
+  const int iy = blockIdx.y * BY + threadIdx.y;
+  if (ix >= nx || iy >= nx) return;
+  double v = 0.0;
+  if (interior2(ix, iy, nx)) {
+    auto X = [&](int dx, int dy) {
+      const int jx = ix + dx, jy = iy + dy;
+      return interior2(jx, jy, nx) ? x[jx + nx * jy] : 0.0;
+    };
+    const double edge = X(-1, 0) + X(1, 0) + X(0, -1) + X(0, 1);
+    const double corner = X(-1, -1) + X(1, -1) + X(-1, 1) + X(1, 1);
+    v = hm * (16.0 * X(0, 0) + 4.0 * edge + corner);
+  }
+  y[ix + nx * iy] = v;
+}
+
 // grad[c] += -kappa_c sum_i mu_i|_c^T K_e U_i|_c, U_i = u_n + sum_j (dt a_ij) k_j, with the
 // unit-diffusivity bilinear element matrix K_e = [[4,-1,-1,-2],[-1,4,-2,-1],[-1,-2,4,-1],[-2,-1,-1,4]]/6
 // (corners ordered (0,0), (1,0), (0,1), (1,1)).  One thread per cell, no atomics.
@@ -185,6 +213,14 @@ void launch_rk_update(int S, cudaStream_t st, int nx, const double* u, const dou
 void launch_adjoint_lambda(int S, cudaStream_t st, int nx, const double* cf, const double* lam_np1, const double* mu,
                            double* lam_n) {
   IRK_DISPATCH_S(S, adjoint_lambda_kernel<SS><<<all_nodes_grid(nx), dim3(BX, BY), 0, st>>>(nx, cf, lam_np1, mu, lam_n));
+}
+void launch_block_apply(cudaStream_t st, int nx, const double* cf, double hm, double sigma, const double* x,
+                        double* y) {
+  dim3 g((nx - 2 + BX - 1) / BX, (nx - 2 + BY - 1) / BY);
+  block_apply_kernel<<<g, dim3(BX, BY), 0, st>>>(nx, cf, hm, sigma, x, y);
+}
+void launch_mass_apply(cudaStream_t st, int nx, double hm, const double* x, double* y) {
+  mass_apply_kernel<<<all_nodes_grid(nx), dim3(BX, BY), 0, st>>>(nx, hm, x, y);
 }
 void launch_cell_gradient(int S, cudaStream_t st, int N, const double* kappa, const double* u, const double* k,
                           const Mat4& dtA, const double* mu, double* grad) {

@@ -34,7 +34,7 @@ class Solver:
     def __init__(self, n_cells: int, tableau, dt: float, *, kappa=None, levels: int = 1, dim: int = 2,
                  precond: str = "lower", vcycle: str = "fp64", nu_pre: int = 2, nu_post: int = 2,
                  omega: float = 2.0 / 3.0, rtol: float = 1e-10, restart: int = 50, maxit: int = 500,
-                 orth: str = "cgs2", stream=None):
+                 orth: str = "cgs2", solver: str = "fgmres", stream=None):
         A = np.ascontiguousarray(tableau.A, dtype=np.float64)
         self.s = int(A.shape[0])
         self.N, self.dim, self.dt = int(n_cells), int(dim), float(dt)
@@ -60,6 +60,7 @@ class Solver:
         opt.nu_pre, opt.nu_post, opt.omega = int(nu_pre), int(nu_post), float(omega)
         opt.rtol, opt.restart, opt.maxit = float(rtol), int(restart), int(maxit)
         opt.orth = L.ORTH[orth]
+        opt.solver = L.SOLVER[solver]
         self.options = opt
         self.stream = stream if stream is not None else _current_stream()
         h = C.c_void_p()
@@ -118,6 +119,12 @@ class Solver:
         L.check(L.lib.irk_apply_operator(self._h, L.ptr(x, count=ns), L.ptr(y, count=ns), int(transpose)))
 
     apply_operator = irk_apply_operator
+
+    def irk_apply_mass(self, x, y) -> None:
+        nn = self.n_nodes
+        L.check(L.lib.irk_apply_mass(self._h, L.ptr(x, count=nn), L.ptr(y, count=nn)))
+
+    apply_mass = irk_apply_mass
 
     def irk_apply_preconditioner(self, v, z, transpose: bool = False) -> None:
         ns = self.n_nodes * self.s

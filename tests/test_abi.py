@@ -66,6 +66,7 @@ def _create(N=8, levels=1, A=None, s=2, dt=0.1, **opt_over):
         (dict(omega=2.5), "omega"),
         (dict(precond=7), "precond"),
         (dict(orth=5), "orth"),
+        (dict(solver=1), "lower-triangular"),
     ],
 )
 def test_create_rejects_bad_input(kwargs, needle):

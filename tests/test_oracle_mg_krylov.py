@@ -152,3 +152,33 @@ def test_fgmres_vcycle_matches_direct():
         x, its, rel, _ = krylov.fgmres(lambda v: S @ v, b, P, rtol=1e-12)
         assert rel <= 1e-12
         assert np.linalg.norm(x - xd) <= 1e-9 * np.linalg.norm(xd)
+
+
+@pytest.mark.parametrize("s", [2, 3, 4])
+def test_ldu_factorisation(s):
+    A = T.radau_iia(s).A
+    L, D, U = krylov.ldu(A)
+    assert np.allclose(L @ D @ U, A, atol=1e-15)
+    assert np.allclose(np.diag(L), 1) and np.allclose(np.diag(U), 1)
+    assert np.allclose(np.triu(L, 1), 0) and np.allclose(np.tril(U, -1), 0)
+    # for a lower-triangular (DIRK) tableau, L D = A: the Rana preconditioner is P_L
+    assert np.allclose(krylov.rana_ld(T.alexander().A), T.alexander().A, atol=1e-15)
+
+
+def test_rana_ld_iterations_vs_block_gauss_seidel():
+    """Sec. 3.1 / 4.1: with exact blocks P_LD needs fewer iterations than P_L, and its count grows more
+    slowly with s (the paper reports it flat for the IA form; in the AI form used here it grows, but
+    less than P_L's)."""
+    its = {}
+    for s in (2, 3, 4):
+        tab = T.radau_iia(s)
+        dt = 0.05
+        d, S = kron_setup(tab, N=16, dt=dt)
+        b = np.random.default_rng(9).standard_normal(S.shape[0])
+        for name, Am in (("lower", tab.A), ("rana", krylov.rana_ld(tab.A))):
+            solves = [mg.ExactBlock(d.M, d.K, dt * Am[i, i]) for i in range(s)]
+            P = krylov.BlockPreconditioner("lower", Am, d.K, dt, solves)
+            its[(name, s)] = krylov.fgmres(lambda v: S @ v, b, P, rtol=1e-10)[1]
+    for s in (2, 3, 4):
+        assert its[("rana", s)] < its[("lower", s)]
+    assert its[("rana", 4)] - its[("rana", 2)] < its[("lower", 4)] - its[("lower", 2)]
