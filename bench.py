@@ -45,9 +45,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="heat2d-1024-radau3", choices=sorted(W.WORKLOADS))
-    ap.add_argument("--precond", default="lower", choices=["diag", "lower", "upper"])
+    ap.add_argument("--precond", default="lower", choices=["diag", "lower", "upper", "rana_ld"])
     ap.add_argument("--vcycle", default=None, choices=["fp64", "fp32", "bf16"])
     ap.add_argument("--orth", default="cgs2", choices=["cgs2", "dgks"])
+    ap.add_argument("--tableau", default=None, help="override, e.g. GaussLegendre:4 or Alexander:3")
+    ap.add_argument("--restart", type=int, default=50, help="FGMRES restart length (Krylov basis size)")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -147,16 +149,40 @@ def ncu_traffic(kernel_class: str, workload: str):
 
 
 # ----------------------------------------------------------------------------
+# multi-rank aggregation (replicas: no collective on the data path)
+# ----------------------------------------------------------------------------
+def max_over_ranks(ms: float, device: str) -> float:
+    """The slowest rank's time, so that the aggregate throughput counts every rank's work."""
+    import torch
+    import torch.distributed as td
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    td.barrier()
+    return float(t.item())
+
+
+def aggregate(world: int, steps: int, ms_max: float) -> float:
+    """Whole-job time-steps/s: every rank ran ``steps`` steps of its own replica."""
+    return world * steps / (ms_max / 1e3)
+
+
+# ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
-def make_solver(wl, precond, vcycle, orth="cgs2"):
+RESTART = 50
+
+
+def make_solver(wl, precond, vcycle, orth="cgs2", tableau=None):
     from paper_2403_08084_gb300 import Solver
     from paper_2403_08084_gb300 import tableaux as PT
 
-    tab = PT.by_name(wl.tableau, wl.s)
+    name, s = tableau or (wl.tableau, wl.s)
+    tab = PT.by_name(name, s)
     kap = W.lognormal_kappa(wl.dim, wl.N, 0.5, wl.kappa_seed) if wl.kappa_seed is not None else None
-    sv = Solver(wl.N, tab, wl.dt, kappa=kap, levels=wl.levels, precond=precond, vcycle=vcycle, rtol=wl.rtol,
-                orth=orth)
+    solver = "dirk_cg" if name.lower() == "alexander" else "fgmres"
+    sv = Solver(wl.N, tab, wl.dt, dim=wl.dim, kappa=kap, levels=wl.levels, precond=precond, vcycle=vcycle,
+                rtol=wl.rtol, orth=orth, solver=solver, restart=RESTART)
     return sv, tab
 
 
@@ -182,7 +208,11 @@ def gpu_arm(args, rank, world):
     dist = world > 1
     if dist:
         import torch.distributed as td
-    sv, tab = make_solver(wl, precond, vcycle, args.orth)
+    tab_override = None
+    if args.tableau:
+        name, _, s_ = args.tableau.partition(":")
+        tab_override = (name, int(s_ or 3))
+    sv, tab = make_solver(wl, precond, vcycle, args.orth, tab_override)
     nn = (wl.N + 1) ** wl.dim
     u0 = torch.from_numpy(W.sine_initial(wl.dim, wl.N)).cuda()
     f = torch.from_numpy(W.sine_load_space(wl.dim, wl.N)).cuda()
@@ -192,7 +222,7 @@ def gpu_arm(args, rank, world):
     # warm-up, then one instrumented step to find the kernel class that dominates device time
     run_steps(sv, tab, wl, u, f, 0, args.warmup)
     sv.perf_select([c for c in ("stage_apply", "jacobi", "residual", "restrict", "prolong", "coarse", "multidot",
-                                "axpy", "block_rhs")])
+                                "axpy", "block_rhs", "mg_coarse")])
     u.copy_(u0)
     run_steps(sv, tab, wl, u, f, 0, 1)
     prof = sv.perf_read()["classes"]
@@ -217,10 +247,7 @@ def gpu_arm(args, rank, world):
     clk = clocks.stop() if clocks else None
     ms = e0.elapsed_time(e1)
     if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        td.all_reduce(t, op=td.ReduceOp.MAX)
-        td.barrier()
-        ms = float(t.item())
+        ms = max_over_ranks(ms, "cuda")
     launches = sv.perf_read()["launches"]
     u_final = u.clone()
     # the same K steps again with CUDA events around every launch of the dominant kernel class
@@ -234,7 +261,7 @@ def gpu_arm(args, rank, world):
     sv.perf_select([])
     run_steps(sv, tab, wl, u5, f, 0, min(5, args.steps))
 
-    steps_per_s = world * args.steps / (ms / 1e3)
+    steps_per_s = aggregate(world, args.steps, ms)
     s = wl.s
     dof = (wl.N + 1) ** wl.dim
     its = [st["fgmres_its"] for st in stats]
@@ -274,9 +301,10 @@ def gpu_arm(args, rank, world):
         "vs_baseline": None,
         "dtype": "f64" if vcycle == "fp64" else f"f64 outer / {vcycle} V-cycles",
         "data": "synthetic",
-        "config": {"workload": wl.name, "mesh": f"{wl.N}x{wl.N} Q1", "dofs": dof, "stages": s,
-                   "tableau": f"{wl.tableau}({s})", "dt": wl.dt, "kappa": "lognormal sigma=0.5 seed %s" % wl.kappa_seed,
+        "config": {"workload": wl.name, "mesh": "x".join([str(wl.N)] * wl.dim) + " Q1", "dofs": dof, "stages": s,
+                   "tableau": tab_label(tab), "dt": wl.dt, "kappa": "lognormal sigma=0.5 seed %s" % wl.kappa_seed,
                    "precond": precond, "vcycle": vcycle, "levels": wl.levels, "rtol": wl.rtol, "orth": args.orth,
+                   "restart": args.restart,
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                    "l2_policy": "working set > L2: Krylov basis of ~its x 25 MB stage vectors per step"},
         "dof_stage_per_s": round(steps_per_s * dof * s, 1),
@@ -297,6 +325,10 @@ def gpu_arm(args, rank, world):
         out["cpu_baseline"] = cpu_baseline_leg(wl)
     out["final_u_norm"] = float(torch.linalg.vector_norm(u_final).item())
     return out
+
+
+def tab_label(tab) -> str:
+    return tab.name
 
 
 def e2e_leg(sv, tab, wl, u0, args):
@@ -324,16 +356,24 @@ def e2e_leg(sv, tab, wl, u0, args):
 
 
 def variants_leg(wl, u5_ref, args, vcycle0, precond0):
-    """Other preconditioner / V-cycle precision pairs on the same workload (5 steps each)."""
+    """Other preconditioners / V-cycle precisions / tableaux on the same workload (5 steps each)."""
     import torch
 
     res = {}
     nsteps = min(5, args.steps)
-    for precond, vcycle, orth in (("diag", "fp64", "cgs2"), ("lower", "fp64", "dgks"), ("lower", "fp32", "cgs2"),
-                                  ("lower", "bf16", "cgs2"), ("diag", "fp32", "cgs2")):
-        if (precond, vcycle, orth) == (precond0, vcycle0, args.orth):
+    if wl.dim == 2:
+        runs = [("diag", "fp64", "cgs2", None), ("rana_ld", "fp64", "cgs2", None), ("lower", "fp64", "dgks", None),
+                ("lower", "fp32", "cgs2", None), ("lower", "bf16", "cgs2", None), ("diag", "fp32", "cgs2", None),
+                ("rana_ld", "fp32", "cgs2", None), ("lower", "fp64", "cgs2", ("Alexander", 3)),
+                ("lower", "fp32", "cgs2", ("Alexander", 3))]
+    else:
+        runs = [("lower", "fp64", "cgs2", None), ("lower", "fp32", "cgs2", None), ("lower", "bf16", "cgs2", None),
+                ("rana_ld", "fp32", "cgs2", None), ("lower", "fp32", "cgs2", ("GaussLegendre", 2)),
+                ("lower", "fp32", "cgs2", ("GaussLegendre", 4)), ("lower", "bf16", "cgs2", ("GaussLegendre", 4))]
+    for precond, vcycle, orth, tabo in runs:
+        if (precond, vcycle, orth, tabo) == (precond0, vcycle0, args.orth, None):
             continue
-        sv, tab = make_solver(wl, precond, vcycle, orth)
+        sv, tab = make_solver(wl, precond, vcycle, orth, tabo)
         u0 = torch.from_numpy(W.sine_initial(wl.dim, wl.N)).cuda()
         f = torch.from_numpy(W.sine_load_space(wl.dim, wl.N)).cuda()
         u = u0.clone()
@@ -345,35 +385,44 @@ def variants_leg(wl, u5_ref, args, vcycle0, precond0):
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         un = u.cpu().numpy()
-        res[f"{precond}/{vcycle}/{orth}"] = {
-            "steps_per_s": round(nsteps / dt, 4), "ms_per_step": round(dt * 1e3 / nsteps, 3),
-            "fgmres_its_per_step": round(sum(s["fgmres_its"] for s in stats) / nsteps, 2),
-            "rel_l2_vs_headline_after_5_steps": float(np.linalg.norm(un - u5_ref) / np.linalg.norm(u5_ref))}
+        key = f"{precond}/{vcycle}/{orth}" + (f"/{tab.name}" if tabo else "")
+        entry = {"steps_per_s": round(nsteps / dt, 4), "ms_per_step": round(dt * 1e3 / nsteps, 3),
+                 "krylov_its_per_step": round(sum(s["fgmres_its"] for s in stats) / nsteps, 2)}
+        if tabo is None:
+            entry["rel_l2_vs_headline_after_5_steps"] = float(np.linalg.norm(un - u5_ref) / np.linalg.norm(u5_ref))
+        else:
+            entry["note"] = "different tableau: a different time discretisation, not compared with the headline state"
+        res[key] = entry
         sv.close()
     return res
 
 
 def cpu_baseline_leg(wl):
-    """One time step of the same workload through the oracle's FGMRES + V-cycle restatement."""
+    """One time step of the same workload through the oracle's FGMRES + V-cycle restatement
+    (3D: on a 64^3 sample, scaled to the full DOF count)."""
     from oracle import fem, krylov, mg, rk
     from oracle import tableaux as OT
 
-    kap = W.lognormal_kappa(wl.dim, wl.N, 0.5, wl.kappa_seed) if wl.kappa_seed is not None else None
-    d = fem.Discretisation(wl.dim, wl.N, kap)
-    h = mg.Hierarchy(d, wl.levels)
+    N = wl.N if wl.dim == 2 else min(wl.N, 64)
+    levels = wl.levels - int(round(np.log2(wl.N // N)))
+    kap = W.lognormal_kappa(wl.dim, N, 0.5, wl.kappa_seed) if wl.kappa_seed is not None else None
+    d = fem.Discretisation(wl.dim, N, kap)
+    h = mg.Hierarchy(d, levels)
     ot = OT.by_name(wl.tableau, wl.s)
     solves = [mg.VCycle(h, wl.dt * ot.A[i, i]) for i in range(wl.s)]
     S = rk.kronecker_operator(d.M, d.K, ot.A, wl.dt)
     P = krylov.BlockPreconditioner("lower", ot.A, d.K, wl.dt, solves)
-    u0 = d.to_interior(W.sine_initial(wl.dim, wl.N))
-    Fs = d.to_interior(W.sine_load_space(wl.dim, wl.N))
+    u0 = d.to_interior(W.sine_initial(wl.dim, N))
+    Fs = d.to_interior(W.sine_load_space(wl.dim, N))
     t0 = time.perf_counter()
     r = np.stack([W.sine_load_time(wl.dim, c * wl.dt) * Fs for c in ot.c]) - (d.K @ u0)[None, :]
     k, its, _, _ = krylov.fgmres(lambda v: S @ v, r.reshape(-1), P, rtol=wl.rtol)
     u1 = u0 + wl.dt * (ot.b @ k.reshape(wl.s, -1))
     dt = time.perf_counter() - t0
-    return {"value": round(1.0 / dt, 5), "unit": "time-steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"1 time step of {wl.name} at full size (oracle FGMRES + sparse V-cycle, P_L, FP64; "
+    scale = ((N + 1) / (wl.N + 1)) ** wl.dim
+    where = "at full size" if N == wl.N else f"on a {N}^{wl.dim} sample, steps/s scaled by the DOF ratio {scale:.4f}"
+    return {"value": round(scale / dt, 6), "unit": "time-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"1 time step of {wl.name} {where} (oracle FGMRES + sparse V-cycle, P_L, FP64; "
                       f"{its} its; setup excluded)", "seconds": round(dt, 2), "u_norm": float(np.linalg.norm(u1))}
 
 
@@ -387,15 +436,18 @@ def reference_arm(args):
     wl = W.WORKLOADS[args.workload]
     # bounded sample: the same workload on a mesh with 1/4 of the nodes (one fewer level), so that
     # every step is a few seconds of CPU work; throughput is scaled to the full DOF count
-    Ns = max(wl.N // 2, 32)
-    lv = max(1, wl.levels - (1 if Ns < wl.N else 0))
+    Ns = max(wl.N // 2, 32) if wl.dim == 2 else min(wl.N, 64)
+    lv = max(1, wl.levels - int(round(np.log2(wl.N // Ns))))
     kap = W.lognormal_kappa(wl.dim, Ns, 0.5, wl.kappa_seed) if wl.kappa_seed is not None else None
     d = fem.Discretisation(wl.dim, Ns, kap)
     h = mg.Hierarchy(d, lv)
     ot = OT.by_name(wl.tableau, wl.s)
-    solves = [mg.VCycle(h, wl.dt * ot.A[i, i]) for i in range(wl.s)]
+    kind, Ap = args.precond, ot.A
+    if kind == "rana_ld":
+        kind, Ap = "lower", krylov.rana_ld(ot.A)
+    solves = [mg.VCycle(h, wl.dt * Ap[i, i]) for i in range(wl.s)]
     S = rk.kronecker_operator(d.M, d.K, ot.A, wl.dt)
-    P = krylov.BlockPreconditioner(args.precond, ot.A, d.K, wl.dt, solves)
+    P = krylov.BlockPreconditioner(kind, Ap, d.K, wl.dt, solves)
     u0 = d.to_interior(W.sine_initial(wl.dim, Ns))
     Fs = d.to_interior(W.sine_load_space(wl.dim, Ns))
 
@@ -416,7 +468,7 @@ def reference_arm(args):
     dt = time.perf_counter() - t0
     scale = ((Ns + 1) ** wl.dim) / ((wl.N + 1) ** wl.dim)
     value = args.steps / dt * scale
-    sample = (f"each step: one RK step of {wl.name} on a {Ns}x{Ns} mesh ({lv} levels), oracle FGMRES + sparse "
+    sample = (f"each step: one RK step of {wl.name} on a {Ns}^{wl.dim} mesh ({lv} levels), oracle FGMRES + sparse "
               f"V-cycle, P_{args.precond[0].upper()}, FP64; steps/s scaled by the DOF ratio {scale:.4f}")
     return {
         "impl": "reference",
@@ -432,7 +484,8 @@ def reference_arm(args):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": wl.name, "mesh": f"{wl.N}x{wl.N} Q1", "precond": args.precond, "sample_mesh": Ns},
+        "config": {"workload": wl.name, "mesh": "x".join([str(wl.N)] * wl.dim) + " Q1", "precond": args.precond,
+                   "sample_mesh": Ns},
         "fgmres_its_per_step": round(sum(its) / len(its), 2),
         "cpu_baseline": {"value": round(value, 6), "unit": "time-steps/s", "cores": 1, "kind": "oracle",
                          "sample": sample},
@@ -441,7 +494,9 @@ def reference_arm(args):
 
 
 def main():
+    global RESTART
     args = parse()
+    RESTART = args.restart
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":

@@ -184,16 +184,17 @@ int irk_apply_preconditioner_noalloc(irk_handle* h, const double* v, double* z, 
 
 /* Kernel classes counted by the built-in instrumentation. */
 #define IRK_K_STAGE_APPLY 0 /* stage operator (FP64)                        */
-#define IRK_K_JACOBI 1      /* weighted-Jacobi sweep                         */
-#define IRK_K_RESIDUAL 2    /* multigrid residual                            */
-#define IRK_K_RESTRICT 3    /* full-weighting restriction                    */
-#define IRK_K_PROLONG 4     /* bilinear prolongation + correction            */
+#define IRK_K_JACOBI 1      /* weighted-Jacobi sweep, finest level           */
+#define IRK_K_RESIDUAL 2    /* multigrid residual, finest level              */
+#define IRK_K_RESTRICT 3    /* restriction from the finest level             */
+#define IRK_K_PROLONG 4     /* prolongation + correction into the finest level */
 #define IRK_K_COARSE 5      /* coarsest-level dense solve                    */
 #define IRK_K_MULTIDOT 6    /* Arnoldi multi-dot partial sums                */
 #define IRK_K_AXPY 7        /* Arnoldi / solution multi-axpy                 */
 #define IRK_K_BLOCK_RHS 8   /* triangular-preconditioner block right side    */
 #define IRK_K_OTHER 9       /* reductions, scaling, Givens, casts, RHS, update */
-#define IRK_K_COUNT 10
+#define IRK_K_MG_COARSE 10  /* smoothing, residual and transfers on the coarser levels */
+#define IRK_K_COUNT 11
 
 typedef struct {
   long long launches;                   /* kernels launched since the last irk_perf_select */

@@ -55,13 +55,14 @@ class irk_stats(C.Structure):
 
 
 K_CLASSES = ["stage_apply", "jacobi", "residual", "restrict", "prolong", "coarse", "multidot", "axpy",
-             "block_rhs", "other"]
+             "block_rhs", "other", "mg_coarse"]
+_NK = len(K_CLASSES)
 
 
 class irk_perf(C.Structure):
-    _fields_ = [("launches", C.c_longlong), ("class_launches", C.c_longlong * 10), ("class_bytes", C.c_double * 10),
-                ("class_flops", C.c_double * 10), ("timed_launches", C.c_longlong * 10),
-                ("timed_ms", C.c_double * 10), ("timed_bytes", C.c_double * 10), ("timed_flops", C.c_double * 10)]
+    _fields_ = [("launches", C.c_longlong), ("class_launches", C.c_longlong * _NK), ("class_bytes", C.c_double * _NK),
+                ("class_flops", C.c_double * _NK), ("timed_launches", C.c_longlong * _NK),
+                ("timed_ms", C.c_double * _NK), ("timed_bytes", C.c_double * _NK), ("timed_flops", C.c_double * _NK)]
 
     def as_dict(self) -> dict:
         out = {"launches": int(self.launches), "classes": {}}

@@ -599,25 +599,28 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2) {
       dv.v[i] = h->opt.omega / bc.v[i][0];
     }
   };
+  // finest-level launches keep their class; every launch on a coarser level is IRK_K_MG_COARSE
+  auto cls = [&](const Level& Lv, int fine_class) { return (&Lv == &h->lev[0]) ? fine_class : IRK_K_MG_COARSE; };
   auto sweep = [&](Level& Lv, const C* cf, const C* dinv, const T* xin, const T* b, T* xout) {
     const double n = interior(Lv);
+    const int kj = cls(Lv, IRK_K_JACOBI);
     if (d3) {
       Cls4 bc{};
       Vec8 dv{};
       classes(Lv, bc, dv);
-      KScope k(h, IRK_K_JACOBI, n * S * (xin ? 3 : 2) * p, (xin ? 34.0 : 1.0) * n * S);
+      KScope k(h, kj, n * S * (xin ? 3 : 2) * p, (xin ? 34.0 : 1.0) * n * S);
       MG3T::jacobi(S, st, Lv.nx, bc, dv, xin, b, xout);
       return;
     }
     const C* rec = P::rec(Lv);
     if (xin == nullptr) {
-      KScope k(h, IRK_K_JACOBI, n * S * (2 * p + c), n * S);
+      KScope k(h, kj, n * S * (2 * p + c), n * S);
       MG::jacobi(S, st, Lv.nx, cf, Lv.hm, sig, dinv, s, xin, b, xout);
     } else if (rec != nullptr) {  // B_i records: 9 products + 2 per node and stage
-      KScope k(h, IRK_K_JACOBI, n * S * (3 * p + c + kCoef2 * c), 20.0 * n * S);
+      KScope k(h, kj, n * S * (3 * p + c + kCoef2 * c), 20.0 * n * S);
       MG::jacobi_rec(S, st, Lv.nx, rec + (size_t)st0 * Lv.nn * kCoef2, Lv.nn * kCoef2, dinv, s, xin, b, xout);
     } else {
-      KScope k(h, IRK_K_JACOBI, n * (S * (3 * p + c) + kCoef2 * c), 33.0 * n * S);
+      KScope k(h, kj, n * (S * (3 * p + c) + kCoef2 * c), 33.0 * n * S);
       MG::jacobi(S, st, Lv.nx, cf, Lv.hm, sig, dinv, s, xin, b, xout);
     }
   };
@@ -645,20 +648,20 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2) {
       Vec8 dv{};
       classes(Lv, bc, dv);
       {
-        KScope k(h, IRK_K_RESIDUAL, nf * S * 3 * p, 33.0 * nf * S);
+        KScope k(h, cls(Lv, IRK_K_RESIDUAL), nf * S * 3 * p, 33.0 * nf * S);
         MG3T::residual(S, st, Lv.nx, bc, cur[l], bl, (T*)Lv.r);
       }
-      KScope k(h, IRK_K_RESTRICT, (nf + nc) * S * p, 30.0 * nc * S);
+      KScope k(h, cls(Lv, IRK_K_RESTRICT), (nf + nc) * S * p, 30.0 * nc * S);
       MG3T::restrict_(S, st, Lv.nx, (const T*)Lv.r, Lc.nx, (T*)Lc.b);
     } else {
       if (const C* rec = P::rec(Lv)) {
-        KScope k(h, IRK_K_RESIDUAL, nf * S * (3 * p + kCoef2 * c), 18.0 * nf * S);
+        KScope k(h, cls(Lv, IRK_K_RESIDUAL), nf * S * (3 * p + kCoef2 * c), 18.0 * nf * S);
         MG::residual_rec(S, st, Lv.nx, rec + (size_t)st0 * Lv.nn * kCoef2, Lv.nn * kCoef2, cur[l], bl, (T*)Lv.r);
       } else {
-        KScope k(h, IRK_K_RESIDUAL, nf * (3 * S * p + kCoef2 * c), 31.0 * nf * S);
+        KScope k(h, cls(Lv, IRK_K_RESIDUAL), nf * (3 * S * p + kCoef2 * c), 31.0 * nf * S);
         MG::residual(S, st, Lv.nx, cf, Lv.hm, sig, cur[l], bl, (T*)Lv.r);
       }
-      KScope k(h, IRK_K_RESTRICT, (nf + nc) * S * p, 12.0 * nc * S);
+      KScope k(h, cls(Lv, IRK_K_RESTRICT), (nf + nc) * S * p, 12.0 * nc * S);
       MG::restrict_(S, st, Lv.nx, (const T*)Lv.r, Lc.nx, (T*)Lc.b);
     }
     bl = (const T*)Lc.b;
@@ -683,7 +686,7 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2) {
     const T* bfine = (l == 0) ? b0 : (const T*)Lv.b;
     const double nf = interior(Lv), nc = interior(Lc);
     {
-      KScope k(h, IRK_K_PROLONG, (nc + 2 * nf) * S * p, (d3 ? 9.0 : 5.0) * nf * S);
+      KScope k(h, cls(Lv, IRK_K_PROLONG), (nc + 2 * nf) * S * p, (d3 ? 9.0 : 5.0) * nf * S);
       if (d3)
         MG3T::prolong_add(S, st, Lc.nx, cur[l + 1], Lv.nx, cur[l]);
       else
