@@ -97,6 +97,7 @@ struct irk_handle {
   double* binv_d = nullptr;
   float* binv_f = nullptr;
   double* kappa_d = nullptr;
+  float* kappa_f = nullptr;  // 2D: per-cell kappa for the FP32 / BF16 finest-level kernels
   // Krylov space
   size_t ne = 0;  // entries of a stage vector
   int m = 0;
@@ -396,6 +397,9 @@ int build_operators(irk_handle* h) {
   CK(cudaMemcpyAsync(h->binv_f, allf.data(), allf.size() * 4, cudaMemcpyHostToDevice, h->st));
   if (!h->kappa.empty())
     CK(cudaMemcpyAsync(h->kappa_d, h->kappa.data(), h->kappa.size() * 8, cudaMemcpyHostToDevice, h->st));
+  std::vector<float> kf((size_t)h->N * h->N, 1.0f);
+  if (!h->kappa.empty()) std::copy(h->kappa.begin(), h->kappa.end(), kf.begin());
+  CK(cudaMemcpyAsync(h->kappa_f, kf.data(), kf.size() * 4, cudaMemcpyHostToDevice, h->st));
   CK(cudaStreamSynchronize(h->st));
   return IRK_OK;
 }
@@ -406,7 +410,7 @@ void destroy(irk_handle* h) {
     dfree(Lv.cf_d), dfree(Lv.cf_f), dfree(Lv.brec_d), dfree(Lv.dinv_d), dfree(Lv.dinv_f);
     dfree(Lv.xa), dfree(Lv.xb), dfree(Lv.b), dfree(Lv.r);
   }
-  dfree(h->cmap), dfree(h->binv_d), dfree(h->binv_f), dfree(h->kappa_d);
+  dfree(h->cmap), dfree(h->binv_d), dfree(h->binv_f), dfree(h->kappa_d), dfree(h->kappa_f);
   dfree(h->V), dfree(h->Z), dfree(h->H), dfree(h->cs), dfree(h->sn), dfree(h->g), dfree(h->y);
   dfree(h->h1), dfree(h->h2), dfree(h->partial), dfree(h->scal), dfree(h->iflag);
   dfree(h->rhs), dfree(h->k), dfree(h->tmp);
@@ -502,7 +506,8 @@ int create(irk_handle** out, const irk_mesh* mesh, const irk_tableau* tab, doubl
   if ((r = dalloc(&h->cmap, (size_t)h->nint * sizeof(int))) ||
       (r = dalloc(&h->binv_d, (size_t)s * h->nint * h->nint * 8)) ||
       (r = dalloc(&h->binv_f, (size_t)s * h->nint * h->nint * 4)) ||
-      (r = dalloc(&h->kappa_d, dim == 2 ? (size_t)h->N * h->N * 8 : 16)))
+      (r = dalloc(&h->kappa_d, dim == 2 ? (size_t)h->N * h->N * 8 : 16)) ||
+      (dim == 2 && (r = dalloc(&h->kappa_f, (size_t)h->N * h->N * 4))))
     return bail(r);
   h->ne = h->lev[0].nn * s;
   h->m = opt->restart;
@@ -601,9 +606,19 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2) {
   };
   // finest-level launches keep their class; every launch on a coarser level is IRK_K_MG_COARSE
   auto cls = [&](const Level& Lv, int fine_class) { return (&Lv == &h->lev[0]) ? fine_class : IRK_K_MG_COARSE; };
+  // FP32 / BF16, 2D: the finest level forms its stencil from per-cell kappa
+  constexpr bool f32c = std::is_same<C, float>::value;
+  auto use_kappa = [&](const Level& Lv) { return f32c && !d3 && &Lv == &h->lev[0]; };
   auto sweep = [&](Level& Lv, const C* cf, const C* dinv, const T* xin, const T* b, T* xout) {
     const double n = interior(Lv);
     const int kj = cls(Lv, IRK_K_JACOBI);
+    if constexpr (f32c) {
+      if (use_kappa(Lv)) {
+        KScope k(h, kj, n * S * (xin ? 3 : 2) * p + n * 4.0, (xin ? 40.0 : 4.0) * n * S);
+        MG2K<T, C>::jacobi(S, st, Lv.nx, (const C*)h->kappa_f, Lv.hm, sig, h->opt.omega, xin, b, xout, 0);
+        return;
+      }
+    }
     if (d3) {
       Cls4 bc{};
       Vec8 dv{};
@@ -639,8 +654,39 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2) {
       bufs[0] = other, bufs[1] = last;
     }
     int w = 0;
-    sweep(Lv, cf, dinv, nullptr, bl, bufs[w]);
-    for (int k = 1; k < nu1; ++k, w ^= 1) sweep(Lv, cf, dinv, bufs[w], bl, bufs[w ^ 1]);
+    // two sweeps from zero fused into one pass: always for FP32 / BF16; for FP64 only on the
+    // coarse levels (on the finest level it would add FP64 work to an FP64-pipe-bound sweep)
+    const bool fuse2 = nu1 >= 2 && (!std::is_same<C, double>::value || l > 0);
+    int k0 = 1;
+    if (fuse2) {
+      const double n = interior(Lv);
+      if constexpr (f32c) {
+        if (use_kappa(Lv)) {
+          KScope kk(h, cls(Lv, IRK_K_JACOBI), n * S * 2 * p + n * 4.0, 60.0 * n * S);
+          MG2K<T, C>::jacobi(S, st, Lv.nx, (const C*)h->kappa_f, Lv.hm, sig, h->opt.omega, nullptr, bl, bufs[1], 1);
+        }
+      }
+      if (use_kappa(Lv)) {
+        // done above
+      } else if (d3) {
+        Cls4 bc{};
+        Vec8 dv{};
+        classes(Lv, bc, dv);
+        KScope kk(h, cls(Lv, IRK_K_JACOBI), n * S * 2 * p, 36.0 * n * S);
+        MG3T::jacobi2z(S, st, Lv.nx, bc, dv, bl, bufs[1]);
+      } else {
+        const C* rec = P::rec(Lv);
+        KScope kk(h, cls(Lv, IRK_K_JACOBI), n * S * (2 * p + c + kCoef2 * c) + (rec ? 0.0 : n * kCoef2 * c),
+                  (rec ? 30.0 : 42.0) * n * S);
+        MG::jacobi2z(S, st, Lv.nx, cf, Lv.hm, sig, rec ? rec + (size_t)st0 * Lv.nn * kCoef2 : nullptr,
+                     Lv.nn * kCoef2, dinv, s, bl, bufs[1]);
+      }
+      w = 1;
+      k0 = 2;
+    } else {
+      sweep(Lv, cf, dinv, nullptr, bl, bufs[w]);
+    }
+    for (int k = k0; k < nu1; ++k, w ^= 1) sweep(Lv, cf, dinv, bufs[w], bl, bufs[w ^ 1]);
     cur[l] = bufs[w];
     const double nf = interior(Lv), nc = interior(Lc);
     if (d3) {
@@ -654,7 +700,16 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2) {
       KScope k(h, cls(Lv, IRK_K_RESTRICT), (nf + nc) * S * p, 30.0 * nc * S);
       MG3T::restrict_(S, st, Lv.nx, (const T*)Lv.r, Lc.nx, (T*)Lc.b);
     } else {
-      if (const C* rec = P::rec(Lv)) {
+      bool done = false;
+      if constexpr (f32c) {
+        if (use_kappa(Lv)) {
+          KScope k(h, cls(Lv, IRK_K_RESIDUAL), nf * S * 3 * p + nf * 4.0, 36.0 * nf * S);
+          MG2K<T, C>::residual(S, st, Lv.nx, (const C*)h->kappa_f, Lv.hm, sig, cur[l], bl, (T*)Lv.r);
+          done = true;
+        }
+      }
+      if (done) {
+      } else if (const C* rec = P::rec(Lv)) {
         KScope k(h, cls(Lv, IRK_K_RESIDUAL), nf * S * (3 * p + kCoef2 * c), 18.0 * nf * S);
         MG::residual_rec(S, st, Lv.nx, rec + (size_t)st0 * Lv.nn * kCoef2, Lv.nn * kCoef2, cur[l], bl, (T*)Lv.r);
       } else {
@@ -753,10 +808,13 @@ int precond_apply(irk_handle* h, const double* v, double* z, bool transpose) {
     }
     {  // single-stage right-hand side in level-0 b (precision T)
       KScope k(h, IRK_K_BLOCK_RHS, n * (8 + done * 8 + (d3 ? 0 : kCoef2 * c) + p), (d3 ? 32.0 : 19.0) * done * n);
-      if (d3)
+      if (d3) {
         MG3<T, C>::block_rhs(s, st, L0.nx, kc, v, z, i, cj, (T*)L0.b);
-      else
+      } else if constexpr (std::is_same<C, float>::value) {
+        MG2K<T, C>::block_rhs(s, st, L0.nx, (const C*)h->kappa_f, v, z, i, cj, (T*)L0.b);
+      } else {
         MG::block_rhs(s, st, L0.nx, cf, v, z, i, cj, (T*)L0.b);
+      }
     }
     T* x = vcycle<T, C>(h, 1, i, (const T*)L0.b, nullptr, nu1, nu2);
     KScope k(h, IRK_K_OTHER, n * (p + 8), 0);
@@ -856,18 +914,22 @@ int arnoldi_step(irk_handle* h, int j, bool transpose) {
   TRY(precond(h, vj, zj, transpose));
   TRY(apply_operator(h, zj, w, transpose));
   if (h->opt.orth == IRK_ORTH_CGS2) {
-    // classical Gram-Schmidt, twice
+    // classical Gram-Schmidt, twice.  The second pass also sees w' itself (it sits in the
+    // slot of V_{j+1}), so it returns ||w'||^2; the Givens kernel takes ||w''|| by
+    // Pythagoras and the second update normalises in the same sweep.
     multidot(h, h->V, ne, j + 1, w, h->h1);
     multi_axpy(h, w, h->V, ne, j + 1, h->h1, -1.0);
-    multidot(h, h->V, ne, j + 1, w, h->h2);
-    multi_axpy(h, w, h->V, ne, j + 1, h->h2, -1.0);
-    // ||w||^2 -> scal[3]; Givens (hn -> scal[4], rel -> scal[5], hn -> scal[6]); w /= ||w||
-    multidot(h, w, 0, 1, w, h->scal + 3);
+    multidot(h, h->V, ne, j + 2, w, h->h2);
     {
       KScope k(h, IRK_K_OTHER, 0, 0);
-      launch_givens(st, j, ldh, h->H, h->cs, h->sn, h->g, h->h1, h->h2, h->scal + 3, h->scal + 4, r0p, h->scal + 5);
+      launch_givens(st, j, ldh, h->H, h->cs, h->sn, h->g, h->h1, h->h2, nullptr, h->scal + 4, r0p, h->scal + 5, 1,
+                    h->scal + 8);
     }
-    scale(h, w, w, h->scal + 4);
+    {
+      const double n = (double)ne;
+      KScope k(h, IRK_K_AXPY, (j + 3.0) * n * 8, 2.0 * (j + 1) * n + n);
+      launch_multi_axpy(st, w, h->V, ne, j + 1, h->h2, -1.0, ne, h->scal + 8);
+    }
   } else {
     // one pass with ||w||^2 (V_{j+1} is w itself), DGKS test, normalisation fused
     multidot(h, h->V, ne, j + 2, w, h->h1);

@@ -24,6 +24,9 @@ struct MG2 {
                      int dstride, const T* xin, const T* b, T* xout);
   static void residual(int S, cudaStream_t st, int nx, const C* cf, double hm, const Vec8& sigma, const T* x,
                        const T* b, T* r);
+  // two sweeps from a zero guess in one pass (rec != nullptr: B_i records, else hm M + sigma K)
+  static void jacobi2z(int S, cudaStream_t st, int nx, const C* cf, double hm, const Vec8& sigma, const C* rec,
+                       size_t rstride, const C* dinv, int dstride, const T* b, T* xout);
   // the same with B_i = M + sigma_i K stored per stage (stage-major records, stride rstride)
   static void jacobi_rec(int S, cudaStream_t st, int nx, const C* rec, size_t rstride, const C* dinv, int dstride,
                          const T* xin, const T* b, T* xout);
@@ -39,12 +42,25 @@ struct MG2 {
   static void coarse_solve(int S, cudaStream_t st, int nint, const C* binv, const int* map, const T* b, T* x);
 };
 
+// Finest-level 2D kernels forming the stencil from per-cell kappa (mg2d_kappa.cuh);
+// instantiated for the FP32 and BF16 V-cycles.
+template <typename T, typename C>
+struct MG2K {
+  static void jacobi(int S, cudaStream_t st, int nx, const C* kap, double hm, const Vec8& sigma, double omega,
+                     const T* xin, const T* b, T* xout, int two_from_zero);
+  static void residual(int S, cudaStream_t st, int nx, const C* kap, double hm, const Vec8& sigma, const T* x,
+                       const T* b, T* r);
+  static void block_rhs(int SF, cudaStream_t st, int nx, const C* kap, const double* v, const double* z, int i,
+                        const Vec8& cj, T* out);
+};
+
 // 3D multigrid kernels (mg3d.cuh), constant-coefficient stencils.
 template <typename T, typename C>
 struct MG3 {
   static void jacobi(int S, cudaStream_t st, int n, const Cls4& bc, const Vec8& dinv, const T* xin, const T* b,
                      T* xout);
   static void residual(int S, cudaStream_t st, int n, const Cls4& bc, const T* x, const T* b, T* r);
+  static void jacobi2z(int S, cudaStream_t st, int n, const Cls4& bc, const Vec8& dinv, const T* b, T* xout);
   static void restrict_(int S, cudaStream_t st, int nf, const T* rf, int nc, T* bc);
   static void prolong_add(int S, cudaStream_t st, int nc, const T* ec, int nf, T* xf);
   static void block_rhs(int SF, cudaStream_t st, int n, const Cls4& kc, const double* v, const double* z, int i,
@@ -89,7 +105,8 @@ void launch_scale(cudaStream_t st, double* dst, const double* src, const double*
 void launch_orth_decide(cudaStream_t st, int j, double* h1, double* h2, double eta2, int* redo, double* hn2,
                         double* inv);
 void launch_givens(cudaStream_t st, int j, int ldh, double* H, double* cs, double* sn, double* g, const double* h1,
-                   const double* h2, const double* hn2, double* hn_out, const double* r0, double* rel_out);
+                   const double* h2, const double* hn2, double* hn_out, const double* r0, double* rel_out,
+                   int pythag = 0, double* inv_out = nullptr);
 void launch_trisolve(cudaStream_t st, int J, int ldh, const double* H, const double* g, double* y);
 void launch_sqrt_scalar(cudaStream_t st, const double* in, double* out);
 void launch_cg_alpha(cudaStream_t st, const double* rz, const double* pq, double* alpha);

@@ -5,6 +5,7 @@
 //
 // Reductions are deterministic: every block writes one partial sum per dot
 // product and a second kernel adds the partials in a fixed order.
+#include "common.cuh"
 #include "kernels.h"
 
 #include <cmath>
@@ -13,7 +14,7 @@ namespace irk {
 
 namespace {
 constexpr int kThreads = 256;
-constexpr int kPartialBlocks = 152 * 4;  // partial sums per dot product (4 blocks per SM)
+constexpr int kPartialBlocks = 152 * 8;  // partial sums per dot product (8 blocks per SM)
 constexpr int kGroup = 8;                // dot products accumulated per pass over w
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -22,12 +23,25 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Accumulate G dot products V_{k0+g} . w over this thread's elements (G known at compile
+// time: no predicated-off FP64 work for partial groups).
+template <int G>
+__device__ __forceinline__ void multidot_accumulate(const double* __restrict__ V, size_t ld, int k0,
+                                                    const double* __restrict__ w, size_t n, double acc[kGroup]) {
+  for (size_t e = blockIdx.x * (size_t)kThreads + threadIdx.x; e < n; e += (size_t)gridDim.x * kThreads) {
+    const double we = w[e];
+#pragma unroll
+    for (int g = 0; g < G; ++g) acc[g] = fma(V[(size_t)(k0 + g) * ld + e], we, acc[g]);
+  }
+}
+
 // partial[k * nb + blockIdx.x] = sum over this block's elements of V_k[e] w[e],
 // for k = blockIdx.y * kGroup + g < count.
 __global__ void __launch_bounds__(kThreads) multidot_kernel(const double* __restrict__ V, size_t ld, int count,
                                                             const double* __restrict__ w, size_t n,
                                                             double* __restrict__ partial,
                                                             const int* __restrict__ run_if) {
+  IRK_PDL_ENTRY;
   if (run_if != nullptr && *run_if == 0) return;
   __shared__ double red[kThreads / 32][kGroup];
   const int k0 = blockIdx.y * kGroup;
@@ -35,25 +49,33 @@ __global__ void __launch_bounds__(kThreads) multidot_kernel(const double* __rest
   double acc[kGroup];
 #pragma unroll
   for (int g = 0; g < kGroup; ++g) acc[g] = 0.0;
-  for (size_t e = blockIdx.x * (size_t)kThreads + threadIdx.x; e < n; e += (size_t)gridDim.x * kThreads) {
-    const double we = w[e];
-#pragma unroll
-    for (int g = 0; g < kGroup; ++g)
-      if (g < kn) acc[g] = fma(V[(size_t)(k0 + g) * ld + e], we, acc[g]);
+  switch (kn) {
+    case 1: multidot_accumulate<1>(V, ld, k0, w, n, acc); break;
+    case 2: multidot_accumulate<2>(V, ld, k0, w, n, acc); break;
+    case 3: multidot_accumulate<3>(V, ld, k0, w, n, acc); break;
+    case 4: multidot_accumulate<4>(V, ld, k0, w, n, acc); break;
+    case 5: multidot_accumulate<5>(V, ld, k0, w, n, acc); break;
+    case 6: multidot_accumulate<6>(V, ld, k0, w, n, acc); break;
+    case 7: multidot_accumulate<7>(V, ld, k0, w, n, acc); break;
+    default: multidot_accumulate<8>(V, ld, k0, w, n, acc); break;
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int g = 0; g < kGroup; ++g) {
-    const double v = warp_sum(acc[g]);
-    if (lane == 0) red[warp][g] = v;
+    if (g < kn) {
+      const double v = warp_sum(acc[g]);
+      if (lane == 0) red[warp][g] = v;
+    }
   }
   __syncthreads();
   if (warp == 0) {
 #pragma unroll
     for (int g = 0; g < kGroup; ++g) {
-      double v = (lane < kThreads / 32) ? red[lane][g] : 0.0;
-      v = warp_sum(v);
-      if (lane == 0 && g < kn) partial[(size_t)(k0 + g) * gridDim.x + blockIdx.x] = v;
+      if (g < kn) {
+        double v = (lane < kThreads / 32) ? red[lane][g] : 0.0;
+        v = warp_sum(v);
+        if (lane == 0) partial[(size_t)(k0 + g) * gridDim.x + blockIdx.x] = v;
+      }
     }
   }
 }
@@ -61,6 +83,7 @@ __global__ void __launch_bounds__(kThreads) multidot_kernel(const double* __rest
 __global__ void __launch_bounds__(kThreads) reduce_partials_kernel(const double* __restrict__ partial, int nb,
                                                                    double* __restrict__ out,
                                                                    const int* __restrict__ run_if) {
+  IRK_PDL_ENTRY;
   if (run_if != nullptr && *run_if == 0) return;
   __shared__ double red[kThreads / 32];
   const int k = blockIdx.x;
@@ -82,6 +105,7 @@ __global__ void __launch_bounds__(kThreads) multi_axpy_kernel(double* __restrict
                                                               size_t ld, int count, const double* __restrict__ coef,
                                                               double sign, size_t n, const double* __restrict__ scale,
                                                               const int* __restrict__ run_if) {
+  IRK_PDL_ENTRY;
   if (run_if != nullptr && *run_if == 0) return;
   __shared__ double c[128];
   for (int k = threadIdx.x; k < count; k += kThreads) c[k] = sign * coef[k];
@@ -97,6 +121,7 @@ __global__ void __launch_bounds__(kThreads) multi_axpy_kernel(double* __restrict
 __global__ void __launch_bounds__(kThreads) scale_kernel(double* __restrict__ dst, const double* __restrict__ src,
                                                          const double* __restrict__ denom, size_t n,
                                                          const int* __restrict__ run_if) {
+  IRK_PDL_ENTRY;
   if (run_if != nullptr && *run_if == 0) return;
   const double d = *denom;
   const double inv = (d != 0.0) ? 1.0 / d : 0.0;
@@ -107,15 +132,26 @@ __global__ void __launch_bounds__(kThreads) scale_kernel(double* __restrict__ ds
 // Column j of the Hessenberg matrix is h1 + h2 (the two Gram-Schmidt passes) with
 // subdiagonal hn = sqrt(hn2); apply the earlier rotations, form the new one,
 // update g and report |g_{j+1}| / r0.  One thread.
+// pythag != 0: hn2 is not used; ||w''||^2 = ||w'||^2 - sum_i h2[i]^2 with ||w'||^2 in
+// h2[j + 1] (the second pass saw w' itself as basis vector j + 1), and inv_out = 1 / ||w''||
+// lets the second update normalise in the same sweep.
 __global__ void givens_kernel(int j, int ldh, double* __restrict__ H, double* __restrict__ cs,
                               double* __restrict__ sn, double* __restrict__ g, const double* __restrict__ h1,
                               const double* __restrict__ h2, const double* __restrict__ hn2,
                               double* __restrict__ hn_out, const double* __restrict__ r0p,
-                              double* __restrict__ rel_out) {
+                              double* __restrict__ rel_out, int pythag, double* __restrict__ inv_out) {
+  IRK_PDL_ENTRY;
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double* col = H + (size_t)j * ldh;
   for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
-  const double hn2v = *hn2;
+  double hn2v;
+  if (pythag) {
+    double q = 0.0;
+    for (int i = 0; i <= j; ++i) q += h2[i] * h2[i];
+    hn2v = h2[j + 1] - q;
+  } else {
+    hn2v = *hn2;
+  }
   const double hn = (hn2v < 0.0) ? 0.0 : sqrt(hn2v);  // NaN stays NaN (fmax would hide it)
   col[j + 1] = hn;
   *hn_out = hn;
@@ -139,6 +175,7 @@ __global__ void givens_kernel(int j, int ldh, double* __restrict__ H, double* __
   g[j] = c * g[j];
   rel_out[0] = fabs(g[j + 1]) / *r0p;
   rel_out[1] = hn;
+  if (inv_out != nullptr) *inv_out = (hn > 0.0) ? 1.0 / hn : 0.0;
 }
 
 // Classical Gram-Schmidt with the selective re-orthogonalisation test of Daniel,
@@ -149,6 +186,7 @@ __global__ void givens_kernel(int j, int ldh, double* __restrict__ H, double* __
 // second pass runs (inv = 1: the normalisation comes after it).  One thread.
 __global__ void orth_decide_kernel(int j, double* __restrict__ h1, double* __restrict__ h2, double eta2,
                                    int* __restrict__ redo, double* __restrict__ hn2, double* __restrict__ inv) {
+  IRK_PDL_ENTRY;
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const double wn2 = h1[j + 1];
   double hh = 0.0;
@@ -168,6 +206,7 @@ __global__ void orth_decide_kernel(int j, double* __restrict__ h1, double* __res
 // y = R^{-1} g for the J x J upper-triangular R stored column-major in H.  One thread.
 __global__ void trisolve_kernel(int J, int ldh, const double* __restrict__ H, const double* __restrict__ g,
                                 double* __restrict__ y) {
+  IRK_PDL_ENTRY;
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   for (int i = J - 1; i >= 0; --i) {
     double v = g[i];
@@ -178,11 +217,13 @@ __global__ void trisolve_kernel(int J, int ldh, const double* __restrict__ H, co
 
 __global__ void __launch_bounds__(kThreads) sub_kernel(double* __restrict__ out, const double* __restrict__ a,
                                                        const double* __restrict__ b, size_t n) {
+  IRK_PDL_ENTRY;
   for (size_t e = blockIdx.x * (size_t)kThreads + threadIdx.x; e < n; e += (size_t)gridDim.x * kThreads)
     out[e] = a[e] - b[e];
 }
 
 __global__ void sqrt_scalar_kernel(const double* __restrict__ in, double* __restrict__ out) {
+  IRK_PDL_ENTRY;
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     const double v = *in;
     *out = (v < 0.0) ? 0.0 : sqrt(v);  // NaN stays NaN
@@ -190,16 +231,19 @@ __global__ void sqrt_scalar_kernel(const double* __restrict__ in, double* __rest
 }
 
 __global__ void init_g_kernel(double* __restrict__ g, int m1, const double* __restrict__ beta) {
+  IRK_PDL_ENTRY;
   for (int i = threadIdx.x; i < m1; i += blockDim.x) g[i] = (i == 0) ? *beta : 0.0;
 }
 
 // Conjugate-gradient pieces with scalars kept on the device.
 __global__ void cg_alpha_kernel(const double* __restrict__ rz, const double* __restrict__ pq,
                                 double* __restrict__ alpha) {
+  IRK_PDL_ENTRY;
   if (threadIdx.x == 0 && blockIdx.x == 0) *alpha = (*pq != 0.0) ? *rz / *pq : 0.0;
 }
 __global__ void cg_beta_kernel(const double* __restrict__ rz_new, double* __restrict__ rz_old,
                                double* __restrict__ beta) {
+  IRK_PDL_ENTRY;
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     *beta = (*rz_old != 0.0) ? *rz_new / *rz_old : 0.0;
     *rz_old = *rz_new;
@@ -210,6 +254,7 @@ __global__ void __launch_bounds__(kThreads) cg_update_xr_kernel(double* __restri
                                                                 const double* __restrict__ p,
                                                                 const double* __restrict__ q,
                                                                 const double* __restrict__ alpha, size_t n) {
+  IRK_PDL_ENTRY;
   const double a = *alpha;
   for (size_t e = blockIdx.x * (size_t)kThreads + threadIdx.x; e < n; e += (size_t)gridDim.x * kThreads) {
     x[e] = fma(a, p[e], x[e]);
@@ -219,6 +264,7 @@ __global__ void __launch_bounds__(kThreads) cg_update_xr_kernel(double* __restri
 // p = z + beta p
 __global__ void __launch_bounds__(kThreads) cg_update_p_kernel(double* __restrict__ p, const double* __restrict__ z,
                                                                const double* __restrict__ beta, size_t n) {
+  IRK_PDL_ENTRY;
   const double b = *beta;
   for (size_t e = blockIdx.x * (size_t)kThreads + threadIdx.x; e < n; e += (size_t)gridDim.x * kThreads)
     p[e] = fma(b, p[e], z[e]);
@@ -236,46 +282,47 @@ int krylov_partial_blocks() { return kPartialBlocks; }
 void launch_multidot(cudaStream_t st, const double* V, size_t ld, int count, const double* w, size_t n,
                      double* partial, const int* run_if) {
   dim3 g(kPartialBlocks, (count + kGroup - 1) / kGroup);
-  multidot_kernel<<<g, kThreads, 0, st>>>(V, ld, count, w, n, partial, run_if);
+  launch_k(multidot_kernel, g, kThreads, 0, st, V, ld, count, w, n, partial, run_if);
 }
 void launch_reduce_partials(cudaStream_t st, const double* partial, int count, double* out, const int* run_if) {
-  reduce_partials_kernel<<<count, kThreads, 0, st>>>(partial, kPartialBlocks, out, run_if);
+  launch_k(reduce_partials_kernel, count, kThreads, 0, st, partial, kPartialBlocks, out, run_if);
 }
 void launch_multi_axpy(cudaStream_t st, double* w, const double* V, size_t ld, int count, const double* coef,
                        double sign, size_t n, const double* scale, const int* run_if) {
-  multi_axpy_kernel<<<grid_for(n), kThreads, 0, st>>>(w, V, ld, count, coef, sign, n, scale, run_if);
+  launch_k(multi_axpy_kernel, grid_for(n), kThreads, 0, st, w, V, ld, count, coef, sign, n, scale, run_if);
 }
 void launch_scale(cudaStream_t st, double* dst, const double* src, const double* denom, size_t n, const int* run_if) {
-  scale_kernel<<<grid_for(n), kThreads, 0, st>>>(dst, src, denom, n, run_if);
+  launch_k(scale_kernel, grid_for(n), kThreads, 0, st, dst, src, denom, n, run_if);
 }
 void launch_orth_decide(cudaStream_t st, int j, double* h1, double* h2, double eta2, int* redo, double* hn2,
                         double* inv) {
-  orth_decide_kernel<<<1, 32, 0, st>>>(j, h1, h2, eta2, redo, hn2, inv);
+  launch_k(orth_decide_kernel, 1, 32, 0, st, j, h1, h2, eta2, redo, hn2, inv);
 }
 void launch_givens(cudaStream_t st, int j, int ldh, double* H, double* cs, double* sn, double* g, const double* h1,
-                   const double* h2, const double* hn2, double* hn_out, const double* r0, double* rel_out) {
-  givens_kernel<<<1, 32, 0, st>>>(j, ldh, H, cs, sn, g, h1, h2, hn2, hn_out, r0, rel_out);
+                   const double* h2, const double* hn2, double* hn_out, const double* r0, double* rel_out, int pythag,
+                   double* inv_out) {
+  launch_k(givens_kernel, 1, 32, 0, st, j, ldh, H, cs, sn, g, h1, h2, hn2, hn_out, r0, rel_out, pythag, inv_out);
 }
 void launch_trisolve(cudaStream_t st, int J, int ldh, const double* H, const double* g, double* y) {
-  trisolve_kernel<<<1, 32, 0, st>>>(J, ldh, H, g, y);
+  launch_k(trisolve_kernel, 1, 32, 0, st, J, ldh, H, g, y);
 }
 void launch_sub(cudaStream_t st, double* out, const double* a, const double* b, size_t n) {
-  sub_kernel<<<grid_for(n), kThreads, 0, st>>>(out, a, b, n);
+  launch_k(sub_kernel, grid_for(n), kThreads, 0, st, out, a, b, n);
 }
 void launch_cg_alpha(cudaStream_t st, const double* rz, const double* pq, double* alpha) {
-  cg_alpha_kernel<<<1, 32, 0, st>>>(rz, pq, alpha);
+  launch_k(cg_alpha_kernel, 1, 32, 0, st, rz, pq, alpha);
 }
 void launch_cg_beta(cudaStream_t st, const double* rz_new, double* rz_old, double* beta) {
-  cg_beta_kernel<<<1, 32, 0, st>>>(rz_new, rz_old, beta);
+  launch_k(cg_beta_kernel, 1, 32, 0, st, rz_new, rz_old, beta);
 }
 void launch_cg_update_xr(cudaStream_t st, double* x, double* r, const double* p, const double* q, const double* alpha,
                          size_t n) {
-  cg_update_xr_kernel<<<grid_for(n), kThreads, 0, st>>>(x, r, p, q, alpha, n);
+  launch_k(cg_update_xr_kernel, grid_for(n), kThreads, 0, st, x, r, p, q, alpha, n);
 }
 void launch_cg_update_p(cudaStream_t st, double* p, const double* z, const double* beta, size_t n) {
-  cg_update_p_kernel<<<grid_for(n), kThreads, 0, st>>>(p, z, beta, n);
+  launch_k(cg_update_p_kernel, grid_for(n), kThreads, 0, st, p, z, beta, n);
 }
-void launch_sqrt_scalar(cudaStream_t st, const double* in, double* out) { sqrt_scalar_kernel<<<1, 32, 0, st>>>(in, out); }
-void launch_init_g(cudaStream_t st, double* g, int m1, const double* beta) { init_g_kernel<<<1, 128, 0, st>>>(g, m1, beta); }
+void launch_sqrt_scalar(cudaStream_t st, const double* in, double* out) { launch_k(sqrt_scalar_kernel, 1, 32, 0, st, in, out); }
+void launch_init_g(cudaStream_t st, double* g, int m1, const double* beta) { launch_k(init_g_kernel, 1, 128, 0, st, g, m1, beta); }
 
 }  // namespace irk

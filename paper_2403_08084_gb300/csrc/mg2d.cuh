@@ -25,10 +25,11 @@ inline dim3 interior_grid(int nx) {
 // dinv holds omega / diag(B) per node and stage with stride dstride; xin == nullptr
 // means a zero initial guess (x_out = omega D^{-1} b).
 template <typename T, typename C, int S>
-__global__ void __launch_bounds__(kBX* kBY) jacobi_kernel(int nx, const C* __restrict__ cf, C hm, Vec8 sigma,
+__global__ void __launch_bounds__(kBX* kBY) jacobi_kernel(int nx, const C* __restrict__ cf, C hm, VecT<C> sigma,
                                                           const C* __restrict__ dinv, int dstride,
                                                           const T* __restrict__ xin, const T* __restrict__ b,
                                                           T* __restrict__ xout) {
+  IRK_PDL_ENTRY;
   const int ix = 1 + blockIdx.x * kBX + threadIdx.x;
   const int iy = 1 + blockIdx.y * kBY + threadIdx.y;
   if (ix > nx - 2 || iy > nx - 2) return;
@@ -41,8 +42,7 @@ __global__ void __launch_bounds__(kBX* kBY) jacobi_kernel(int nx, const C* __res
     if (xin == nullptr) {
       xn = di * bi;
     } else {
-      const C sg = static_cast<C>(sigma.v[i]);
-      const C bx = hm * m_apply_unscaled<S, C>(xin, p, nx, i) + sg * k_apply<S, C>(cf, xin, p, nx, i);
+      const C bx = hm * m_apply_unscaled<S, C>(xin, p, nx, i) + sigma.v[i] * k_apply<S, C>(cf, xin, p, nx, i);
       xn = ld<C>(xin + (size_t)p * S + i) + di * (bi - bx);
     }
     st(xout + (size_t)p * S + i, xn);
@@ -58,6 +58,7 @@ __global__ void __launch_bounds__(kBX* kBY) jacobi_rec_kernel(int nx, const C* _
                                                               const C* __restrict__ dinv, int dstride,
                                                               const T* __restrict__ xin, const T* __restrict__ b,
                                                               T* __restrict__ xout) {
+  IRK_PDL_ENTRY;
   const int ix = 1 + blockIdx.x * kBX + threadIdx.x;
   const int iy = 1 + blockIdx.y * kBY + threadIdx.y;
   if (ix > nx - 2 || iy > nx - 2) return;
@@ -75,6 +76,7 @@ template <typename T, typename C, int S>
 __global__ void __launch_bounds__(kBX* kBY) residual_rec_kernel(int nx, const C* __restrict__ rec, size_t rstride,
                                                                 const T* __restrict__ x, const T* __restrict__ b,
                                                                 T* __restrict__ r) {
+  IRK_PDL_ENTRY;
   const int ix = 1 + blockIdx.x * kBX + threadIdx.x;
   const int iy = 1 + blockIdx.y * kBY + threadIdx.y;
   if (ix > nx - 2 || iy > nx - 2) return;
@@ -86,19 +88,45 @@ __global__ void __launch_bounds__(kBX* kBY) residual_rec_kernel(int nx, const C*
   }
 }
 
-// r = b - B x on interior nodes.
+// Two weighted-Jacobi sweeps from a zero initial guess in one pass:
+// x1 = D^{-1} omega b is formed on the fly at the stencil points, x2 = x1 + d (b - B x1).
+// rec == nullptr: B = hm M + sigma K from the stiffness records cf; else the B_i records.
 template <typename T, typename C, int S>
-__global__ void __launch_bounds__(kBX* kBY) residual_kernel(int nx, const C* __restrict__ cf, C hm, Vec8 sigma,
-                                                            const T* __restrict__ x, const T* __restrict__ b,
-                                                            T* __restrict__ r) {
+__global__ void __launch_bounds__(kBX* kBY) jacobi2z_kernel(int nx, const C* __restrict__ cf, C hm, VecT<C> sigma,
+                                                            const C* __restrict__ rec, size_t rstride,
+                                                            const C* __restrict__ dinv, int dstride,
+                                                            const T* __restrict__ b, T* __restrict__ xout) {
+  IRK_PDL_ENTRY;
   const int ix = 1 + blockIdx.x * kBX + threadIdx.x;
   const int iy = 1 + blockIdx.y * kBY + threadIdx.y;
   if (ix > nx - 2 || iy > nx - 2) return;
   const int p = ix + nx * iy;
 #pragma unroll
   for (int i = 0; i < S; ++i) {
-    const C sg = static_cast<C>(sigma.v[i]);
-    const C bx = hm * m_apply_unscaled<S, C>(x, p, nx, i) + sg * k_apply<S, C>(cf, x, p, nx, i);
+    auto X1 = [&](int q) { return dinv[(size_t)q * dstride + i] * ld<C>(b + (size_t)q * S + i); };
+    C bx;
+    if (rec != nullptr)
+      bx = k_apply_f<C>(rec + (size_t)i * rstride, p, nx, X1);
+    else
+      bx = hm * m_apply_unscaled_f<C>(p, nx, X1) + sigma.v[i] * k_apply_f<C>(cf, p, nx, X1);
+    const C bi = ld<C>(b + (size_t)p * S + i);
+    st(xout + (size_t)p * S + i, X1(p) + dinv[(size_t)p * dstride + i] * (bi - bx));
+  }
+}
+
+// r = b - B x on interior nodes.
+template <typename T, typename C, int S>
+__global__ void __launch_bounds__(kBX* kBY) residual_kernel(int nx, const C* __restrict__ cf, C hm, VecT<C> sigma,
+                                                            const T* __restrict__ x, const T* __restrict__ b,
+                                                            T* __restrict__ r) {
+  IRK_PDL_ENTRY;
+  const int ix = 1 + blockIdx.x * kBX + threadIdx.x;
+  const int iy = 1 + blockIdx.y * kBY + threadIdx.y;
+  if (ix > nx - 2 || iy > nx - 2) return;
+  const int p = ix + nx * iy;
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    const C bx = hm * m_apply_unscaled<S, C>(x, p, nx, i) + sigma.v[i] * k_apply<S, C>(cf, x, p, nx, i);
     st(r + (size_t)p * S + i, ld<C>(b + (size_t)p * S + i) - bx);
   }
 }
@@ -108,6 +136,7 @@ __global__ void __launch_bounds__(kBX* kBY) residual_kernel(int nx, const C* __r
 template <typename T, typename C, int S>
 __global__ void __launch_bounds__(kBX* kBY) restrict_kernel(int nxf, const T* __restrict__ rf, int nxc,
                                                             T* __restrict__ bc) {
+  IRK_PDL_ENTRY;
   const int I = 1 + blockIdx.x * kBX + threadIdx.x;
   const int J = 1 + blockIdx.y * kBY + threadIdx.y;
   if (I > nxc - 2 || J > nxc - 2) return;
@@ -126,6 +155,7 @@ __global__ void __launch_bounds__(kBX* kBY) restrict_kernel(int nxf, const T* __
 template <typename T, typename C, int S>
 __global__ void __launch_bounds__(kBX* kBY) prolong_add_kernel(int nxc, const T* __restrict__ ec, int nxf,
                                                                T* __restrict__ xf) {
+  IRK_PDL_ENTRY;
   const int ix = 1 + blockIdx.x * kBX + threadIdx.x;
   const int iy = 1 + blockIdx.y * kBY + threadIdx.y;
   if (ix > nxf - 2 || iy > nxf - 2) return;
@@ -144,8 +174,9 @@ __global__ void __launch_bounds__(kBX* kBY) prolong_add_kernel(int nxc, const T*
 template <typename T, typename C, int SF>
 __global__ void __launch_bounds__(kBX* kBY) block_rhs_kernel(int nx, const C* __restrict__ cf,
                                                              const double* __restrict__ v,
-                                                             const double* __restrict__ z, int i, Vec8 cj,
-                                                             T* __restrict__ out) {
+                                                             const double* __restrict__ z, int i, VecT<C> cj,
+                                                             unsigned used, T* __restrict__ out) {
+  IRK_PDL_ENTRY;
   const int ix = 1 + blockIdx.x * kBX + threadIdx.x;
   const int iy = 1 + blockIdx.y * kBY + threadIdx.y;
   if (ix > nx - 2 || iy > nx - 2) return;
@@ -153,7 +184,7 @@ __global__ void __launch_bounds__(kBX* kBY) block_rhs_kernel(int nx, const C* __
   C acc = static_cast<C>(v[(size_t)p * SF + i]);
 #pragma unroll
   for (int j = 0; j < SF; ++j) {
-    if (cj.v[j] != 0.0) acc -= static_cast<C>(cj.v[j]) * k_apply<SF, C>(cf, z, p, nx, j);
+    if (used & (1u << j)) acc -= cj.v[j] * k_apply<SF, C>(cf, z, p, nx, j);
   }
   st(out + p, acc);
 }
@@ -162,6 +193,7 @@ __global__ void __launch_bounds__(kBX* kBY) block_rhs_kernel(int nx, const C* __
 template <typename T, typename C, int SF>
 __global__ void __launch_bounds__(kBX* kBY) scatter_stage_kernel(int nx, const T* __restrict__ x, int i,
                                                                  double* __restrict__ z) {
+  IRK_PDL_ENTRY;
   const int ix = 1 + blockIdx.x * kBX + threadIdx.x;
   const int iy = 1 + blockIdx.y * kBY + threadIdx.y;
   if (ix > nx - 2 || iy > nx - 2) return;
@@ -171,11 +203,13 @@ __global__ void __launch_bounds__(kBX* kBY) scatter_stage_kernel(int nx, const T
 
 template <typename T, typename C>
 __global__ void cast_to_kernel(const double* __restrict__ src, T* __restrict__ dst, size_t n) {
+  IRK_PDL_ENTRY;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
     st(dst + e, static_cast<C>(src[e]));
 }
 template <typename T, typename C>
 __global__ void cast_from_kernel(const T* __restrict__ src, double* __restrict__ dst, size_t n) {
+  IRK_PDL_ENTRY;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
     dst[e] = static_cast<double>(ld<C>(src + e));
 }
@@ -186,6 +220,7 @@ __global__ void cast_from_kernel(const T* __restrict__ src, double* __restrict__
 template <typename T, typename C, int S>
 __global__ void coarse_solve_kernel(int nint, const C* __restrict__ binv, const int* __restrict__ map,
                                     const T* __restrict__ b, T* __restrict__ x) {
+  IRK_PDL_ENTRY;
   extern __shared__ unsigned char smem_raw[];
   C* bs = reinterpret_cast<C*>(smem_raw);
   const int i = blockIdx.y;
@@ -194,9 +229,17 @@ __global__ void coarse_solve_kernel(int nint, const C* __restrict__ binv, const 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const C* Bi = binv + (size_t)i * nint * nint;
   for (int r = blockIdx.x * nw + warp; r < nint; r += gridDim.x * nw) {
-    C acc = 0;
+    C a0 = 0, a1 = 0, a2 = 0, a3 = 0;  // independent chains keep several loads in flight
     const C* row = Bi + (size_t)r * nint;
-    for (int c = lane; c < nint; c += 32) acc += row[c] * bs[c];
+    int c = lane;
+    for (; c + 96 < nint; c += 128) {
+      a0 += row[c] * bs[c];
+      a1 += row[c + 32] * bs[c + 32];
+      a2 += row[c + 64] * bs[c + 64];
+      a3 += row[c + 96] * bs[c + 96];
+    }
+    for (; c < nint; c += 32) a0 += row[c] * bs[c];
+    C acc = (a0 + a1) + (a2 + a3);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) st(x + (size_t)map[r] * S + i, acc);
@@ -219,60 +262,73 @@ template <typename T, typename C>
 void MG2<T, C>::jacobi(int S, cudaStream_t st, int nx, const C* cf, double hm, const Vec8& sigma, const C* dinv,
                        int dstride, const T* xin, const T* b, T* xout) {
   dim3 g = interior_grid(nx), blk(kBX, kBY);
-  IRK_DISPATCH_S(S, jacobi_kernel<T, C, SS><<<g, blk, 0, st>>>(nx, cf, (C)hm, sigma, dinv, dstride, xin, b, xout));
+  const VecT<C> sg = to_vec<C>(sigma);
+  IRK_DISPATCH_S(S, launch_k(jacobi_kernel<T, C, SS>, g, blk, 0, st, nx, cf, (C)hm, sg, dinv, dstride, xin, b, xout));
+}
+template <typename T, typename C>
+void MG2<T, C>::jacobi2z(int S, cudaStream_t st, int nx, const C* cf, double hm, const Vec8& sigma, const C* rec,
+                         size_t rstride, const C* dinv, int dstride, const T* b, T* xout) {
+  dim3 g = interior_grid(nx), blk(kBX, kBY);
+  const VecT<C> sg = to_vec<C>(sigma);
+  IRK_DISPATCH_S(S, launch_k(jacobi2z_kernel<T, C, SS>, g, blk, 0, st, nx, cf, (C)hm, sg, rec, rstride, dinv, dstride, b, xout));
 }
 template <typename T, typename C>
 void MG2<T, C>::jacobi_rec(int S, cudaStream_t st, int nx, const C* rec, size_t rstride, const C* dinv, int dstride,
                            const T* xin, const T* b, T* xout) {
   dim3 g = interior_grid(nx), blk(kBX, kBY);
-  IRK_DISPATCH_S(S, jacobi_rec_kernel<T, C, SS><<<g, blk, 0, st>>>(nx, rec, rstride, dinv, dstride, xin, b, xout));
+  IRK_DISPATCH_S(S, launch_k(jacobi_rec_kernel<T, C, SS>, g, blk, 0, st, nx, rec, rstride, dinv, dstride, xin, b, xout));
 }
 template <typename T, typename C>
 void MG2<T, C>::residual_rec(int S, cudaStream_t st, int nx, const C* rec, size_t rstride, const T* x, const T* b,
                              T* r) {
   dim3 g = interior_grid(nx), blk(kBX, kBY);
-  IRK_DISPATCH_S(S, residual_rec_kernel<T, C, SS><<<g, blk, 0, st>>>(nx, rec, rstride, x, b, r));
+  IRK_DISPATCH_S(S, launch_k(residual_rec_kernel<T, C, SS>, g, blk, 0, st, nx, rec, rstride, x, b, r));
 }
 template <typename T, typename C>
 void MG2<T, C>::residual(int S, cudaStream_t st, int nx, const C* cf, double hm, const Vec8& sigma, const T* x,
                          const T* b, T* r) {
   dim3 g = interior_grid(nx), blk(kBX, kBY);
-  IRK_DISPATCH_S(S, residual_kernel<T, C, SS><<<g, blk, 0, st>>>(nx, cf, (C)hm, sigma, x, b, r));
+  const VecT<C> sg = to_vec<C>(sigma);
+  IRK_DISPATCH_S(S, launch_k(residual_kernel<T, C, SS>, g, blk, 0, st, nx, cf, (C)hm, sg, x, b, r));
 }
 template <typename T, typename C>
 void MG2<T, C>::restrict_(int S, cudaStream_t st, int nxf, const T* rf, int nxc, T* bc) {
   dim3 g = interior_grid(nxc), blk(kBX, kBY);
-  IRK_DISPATCH_S(S, restrict_kernel<T, C, SS><<<g, blk, 0, st>>>(nxf, rf, nxc, bc));
+  IRK_DISPATCH_S(S, launch_k(restrict_kernel<T, C, SS>, g, blk, 0, st, nxf, rf, nxc, bc));
 }
 template <typename T, typename C>
 void MG2<T, C>::prolong_add(int S, cudaStream_t st, int nxc, const T* ec, int nxf, T* xf) {
   dim3 g = interior_grid(nxf), blk(kBX, kBY);
-  IRK_DISPATCH_S(S, prolong_add_kernel<T, C, SS><<<g, blk, 0, st>>>(nxc, ec, nxf, xf));
+  IRK_DISPATCH_S(S, launch_k(prolong_add_kernel<T, C, SS>, g, blk, 0, st, nxc, ec, nxf, xf));
 }
 template <typename T, typename C>
 void MG2<T, C>::block_rhs(int SF, cudaStream_t st, int nx, const C* cf, const double* v, const double* z, int i,
                           const Vec8& cj, T* out) {
   dim3 g = interior_grid(nx), blk(kBX, kBY);
-  IRK_DISPATCH_S(SF, block_rhs_kernel<T, C, SS><<<g, blk, 0, st>>>(nx, cf, v, z, i, cj, out));
+  unsigned used = 0;
+  for (int j = 0; j < SF; ++j)
+    if (cj.v[j] != 0.0) used |= 1u << j;
+  const VecT<C> c = to_vec<C>(cj);
+  IRK_DISPATCH_S(SF, launch_k(block_rhs_kernel<T, C, SS>, g, blk, 0, st, nx, cf, v, z, i, c, used, out));
 }
 template <typename T, typename C>
 void MG2<T, C>::scatter_stage(int SF, cudaStream_t st, int nx, const T* x, int i, double* z) {
   dim3 g = interior_grid(nx), blk(kBX, kBY);
-  IRK_DISPATCH_S(SF, scatter_stage_kernel<T, C, SS><<<g, blk, 0, st>>>(nx, x, i, z));
+  IRK_DISPATCH_S(SF, launch_k(scatter_stage_kernel<T, C, SS>, g, blk, 0, st, nx, x, i, z));
 }
 template <typename T, typename C>
 void MG2<T, C>::cast_to(cudaStream_t st, const double* src, T* dst, size_t n) {
   int blocks = (int)((n + 255) / 256);
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
-  cast_to_kernel<T, C><<<blocks, 256, 0, st>>>(src, dst, n);
+  launch_k(cast_to_kernel<T, C>, blocks, 256, 0, st, src, dst, n);
 }
 template <typename T, typename C>
 void MG2<T, C>::cast_from(cudaStream_t st, const T* src, double* dst, size_t n) {
   int blocks = (int)((n + 255) / 256);
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
-  cast_from_kernel<T, C><<<blocks, 256, 0, st>>>(src, dst, n);
+  launch_k(cast_from_kernel<T, C>, blocks, 256, 0, st, src, dst, n);
 }
 template <typename T, typename C>
 void MG2<T, C>::coarse_solve(int S, cudaStream_t st, int nint, const C* binv, const int* map, const T* b, T* x) {
@@ -281,7 +337,7 @@ void MG2<T, C>::coarse_solve(int S, cudaStream_t st, int nint, const C* binv, co
   if (gx > 152 * 4) gx = 152 * 4;
   dim3 g(gx, S);
   size_t shm = sizeof(C) * (size_t)nint;
-  IRK_DISPATCH_S(S, coarse_solve_kernel<T, C, SS><<<g, threads, shm, st>>>(nint, binv, map, b, x));
+  IRK_DISPATCH_S(S, launch_k(coarse_solve_kernel<T, C, SS>, g, threads, shm, st, nint, binv, map, b, x));
 }
 
 }  // namespace irk

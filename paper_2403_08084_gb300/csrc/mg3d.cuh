@@ -53,9 +53,17 @@ __device__ __forceinline__ void class_sums3(const T* __restrict__ x, int p, int 
   out[3] = c;
 }
 
-template <typename C>
-__device__ __forceinline__ C class_apply(const double* w, const C s[4]) {
+template <typename C, typename W>
+__device__ __forceinline__ C class_apply(const W* w, const C s[4]) {
   return C(w[0]) * s[0] + C(w[1]) * s[1] + C(w[2]) * s[2] + C(w[3]) * s[3];
+}
+
+template <typename C>
+inline ClsT<C> to_cls(const Cls4& a) {
+  ClsT<C> r;
+  for (int i = 0; i < kMaxS; ++i)
+    for (int k = 0; k < 4; ++k) r.v[i][k] = static_cast<C>(a.v[i][k]);
+  return r;
 }
 
 #define IRK_3D_INDEX                                          \
@@ -67,27 +75,45 @@ __device__ __forceinline__ C class_apply(const double* w, const C s[4]) {
 
 // Weighted Jacobi x_out = x_in + d_i (b - B_i x_in); d_i = omega / B_i(centre) (constant per level).
 template <typename T, typename C, int S>
-__global__ void __launch_bounds__(k3X* k3Y* k3Z) jacobi3_kernel(int n, Cls4 bc, Vec8 dinv, const T* __restrict__ xin,
+__global__ void __launch_bounds__(k3X* k3Y* k3Z) jacobi3_kernel(int n, ClsT<C> bc, VecT<C> dinv, const T* __restrict__ xin,
                                                                 const T* __restrict__ b, T* __restrict__ xout) {
+  IRK_PDL_ENTRY;
   IRK_3D_INDEX
 #pragma unroll
   for (int i = 0; i < S; ++i) {
     const C bi = ld<C>(b + (size_t)p * S + i);
     C xn;
     if (xin == nullptr) {
-      xn = C(dinv.v[i]) * bi;
+      xn = dinv.v[i] * bi;
     } else {
       C cs[4];
       class_sums3<S, C>(xin, p, n, i, cs);
-      xn = cs[0] + C(dinv.v[i]) * (bi - class_apply<C>(bc.v[i], cs));
+      xn = cs[0] + dinv.v[i] * (bi - class_apply<C>(bc.v[i], cs));
     }
     st(xout + (size_t)p * S + i, xn);
   }
 }
 
+// Two Jacobi sweeps from zero in one pass: with the constant diagonal d of a level,
+// x1 = d b and B x1 = d B b, so x2 = d b + d (b - d B b).
 template <typename T, typename C, int S>
-__global__ void __launch_bounds__(k3X* k3Y* k3Z) residual3_kernel(int n, Cls4 bc, const T* __restrict__ x,
+__global__ void __launch_bounds__(k3X* k3Y* k3Z) jacobi2z3_kernel(int n, ClsT<C> bc, VecT<C> dinv,
+                                                                  const T* __restrict__ b, T* __restrict__ xout) {
+  IRK_PDL_ENTRY;
+  IRK_3D_INDEX
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    C cs[4];
+    class_sums3<S, C>(b, p, n, i, cs);
+    const C d = dinv.v[i];
+    st(xout + (size_t)p * S + i, d * cs[0] + d * (cs[0] - d * class_apply<C>(bc.v[i], cs)));
+  }
+}
+
+template <typename T, typename C, int S>
+__global__ void __launch_bounds__(k3X* k3Y* k3Z) residual3_kernel(int n, ClsT<C> bc, const T* __restrict__ x,
                                                                   const T* __restrict__ b, T* __restrict__ r) {
+  IRK_PDL_ENTRY;
   IRK_3D_INDEX
 #pragma unroll
   for (int i = 0; i < S; ++i) {
@@ -101,6 +127,7 @@ __global__ void __launch_bounds__(k3X* k3Y* k3Z) residual3_kernel(int n, Cls4 bc
 template <typename T, typename C, int S>
 __global__ void __launch_bounds__(k3X* k3Y* k3Z) restrict3_kernel(int nf, const T* __restrict__ rf, int n,
                                                                   T* __restrict__ bc) {
+  IRK_PDL_ENTRY;
   IRK_3D_INDEX
   const int q = 2 * ix + nf * (2 * iy + nf * 2 * iz);
   C cs[4];
@@ -115,6 +142,7 @@ __global__ void __launch_bounds__(k3X* k3Y* k3Z) restrict3_kernel(int nf, const 
 template <typename T, typename C, int S>
 __global__ void __launch_bounds__(k3X* k3Y* k3Z) prolong_add3_kernel(int nc, const T* __restrict__ ec, int n,
                                                                      T* __restrict__ xf) {
+  IRK_PDL_ENTRY;
   IRK_3D_INDEX
   const int I[2] = {ix >> 1, (ix + 1) >> 1}, J[2] = {iy >> 1, (iy + 1) >> 1}, K[2] = {iz >> 1, (iz + 1) >> 1};
 #pragma unroll
@@ -132,17 +160,18 @@ __global__ void __launch_bounds__(k3X* k3Y* k3Z) prolong_add3_kernel(int nc, con
 
 // out = v_i - sum_j cj[j] K z_j (triangular preconditioners), K given by its class values kc.
 template <typename T, typename C, int SF>
-__global__ void __launch_bounds__(k3X* k3Y* k3Z) block_rhs3_kernel(int n, Cls4 kc, const double* __restrict__ v,
-                                                                   const double* __restrict__ z, int i, Vec8 cj,
-                                                                   T* __restrict__ out) {
+__global__ void __launch_bounds__(k3X* k3Y* k3Z) block_rhs3_kernel(int n, ClsT<C> kc, const double* __restrict__ v,
+                                                                   const double* __restrict__ z, int i, VecT<C> cj,
+                                                                   unsigned used, T* __restrict__ out) {
+  IRK_PDL_ENTRY;
   IRK_3D_INDEX
   C acc = static_cast<C>(v[(size_t)p * SF + i]);
 #pragma unroll
   for (int j = 0; j < SF; ++j) {
-    if (cj.v[j] != 0.0) {
+    if (used & (1u << j)) {
       C cs[4];
       class_sums3<SF, C>(z, p, n, j, cs);
-      acc -= static_cast<C>(cj.v[j]) * class_apply<C>(kc.v[0], cs);
+      acc -= cj.v[j] * class_apply<C>(kc.v[0], cs);
     }
   }
   st(out + p, acc);
@@ -151,6 +180,7 @@ __global__ void __launch_bounds__(k3X* k3Y* k3Z) block_rhs3_kernel(int n, Cls4 k
 template <typename T, typename C, int SF>
 __global__ void __launch_bounds__(k3X* k3Y* k3Z) scatter_stage3_kernel(int n, const T* __restrict__ x, int i,
                                                                        double* __restrict__ z) {
+  IRK_PDL_ENTRY;
   IRK_3D_INDEX
   z[(size_t)p * SF + i] = static_cast<double>(ld<C>(x + p));
 }
@@ -158,6 +188,7 @@ __global__ void __launch_bounds__(k3X* k3Y* k3Z) scatter_stage3_kernel(int n, co
 template <typename T, typename C>
 __global__ void coarse_solve3_kernel(int nint, const C* __restrict__ binv, const int* __restrict__ map,
                                      const T* __restrict__ b, T* __restrict__ x, int S) {
+  IRK_PDL_ENTRY;
   extern __shared__ unsigned char smem3_raw[];
   C* bs = reinterpret_cast<C*>(smem3_raw);
   const int i = blockIdx.y;
@@ -166,9 +197,17 @@ __global__ void coarse_solve3_kernel(int nint, const C* __restrict__ binv, const
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const C* Bi = binv + (size_t)i * nint * nint;
   for (int r = blockIdx.x * nw + warp; r < nint; r += gridDim.x * nw) {
-    C acc = 0;
+    C a0 = 0, a1 = 0, a2 = 0, a3 = 0;  // independent chains keep several loads in flight
     const C* row = Bi + (size_t)r * nint;
-    for (int c = lane; c < nint; c += 32) acc += row[c] * bs[c];
+    int c = lane;
+    for (; c + 96 < nint; c += 128) {
+      a0 += row[c] * bs[c];
+      a1 += row[c + 32] * bs[c + 32];
+      a2 += row[c + 64] * bs[c + 64];
+      a3 += row[c + 96] * bs[c + 96];
+    }
+    for (; c < nint; c += 32) a0 += row[c] * bs[c];
+    C acc = (a0 + a1) + (a2 + a3);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) st(x + (size_t)map[r] * S + i, acc);
@@ -187,35 +226,49 @@ __global__ void coarse_solve3_kernel(int nint, const C* __restrict__ binv, const
 template <typename T, typename C>
 void MG3<T, C>::jacobi(int S, cudaStream_t st, int n, const Cls4& bc, const Vec8& dinv, const T* xin, const T* b,
                        T* xout) {
-  IRK_DISPATCH_S3(S, jacobi3_kernel<T, C, SS><<<interior_grid3(n), dim3(k3X, k3Y, k3Z), 0, st>>>(n, bc, dinv, xin, b, xout));
+  const ClsT<C> c = to_cls<C>(bc);
+  const VecT<C> d = to_vec<C>(dinv);
+  IRK_DISPATCH_S3(S, launch_k(jacobi3_kernel<T, C, SS>, interior_grid3(n), dim3(k3X, k3Y, k3Z), 0, st, n, c, d, xin, b, xout));
+}
+template <typename T, typename C>
+void MG3<T, C>::jacobi2z(int S, cudaStream_t st, int n, const Cls4& bc, const Vec8& dinv, const T* b, T* xout) {
+  const ClsT<C> c = to_cls<C>(bc);
+  const VecT<C> d = to_vec<C>(dinv);
+  IRK_DISPATCH_S3(S, launch_k(jacobi2z3_kernel<T, C, SS>, interior_grid3(n), dim3(k3X, k3Y, k3Z), 0, st, n, c, d, b, xout));
 }
 template <typename T, typename C>
 void MG3<T, C>::residual(int S, cudaStream_t st, int n, const Cls4& bc, const T* x, const T* b, T* r) {
-  IRK_DISPATCH_S3(S, residual3_kernel<T, C, SS><<<interior_grid3(n), dim3(k3X, k3Y, k3Z), 0, st>>>(n, bc, x, b, r));
+  const ClsT<C> c = to_cls<C>(bc);
+  IRK_DISPATCH_S3(S, launch_k(residual3_kernel<T, C, SS>, interior_grid3(n), dim3(k3X, k3Y, k3Z), 0, st, n, c, x, b, r));
 }
 template <typename T, typename C>
 void MG3<T, C>::restrict_(int S, cudaStream_t st, int nf, const T* rf, int nc, T* bc) {
-  IRK_DISPATCH_S3(S, restrict3_kernel<T, C, SS><<<interior_grid3(nc), dim3(k3X, k3Y, k3Z), 0, st>>>(nf, rf, nc, bc));
+  IRK_DISPATCH_S3(S, launch_k(restrict3_kernel<T, C, SS>, interior_grid3(nc), dim3(k3X, k3Y, k3Z), 0, st, nf, rf, nc, bc));
 }
 template <typename T, typename C>
 void MG3<T, C>::prolong_add(int S, cudaStream_t st, int nc, const T* ec, int nf, T* xf) {
-  IRK_DISPATCH_S3(S, prolong_add3_kernel<T, C, SS><<<interior_grid3(nf), dim3(k3X, k3Y, k3Z), 0, st>>>(nc, ec, nf, xf));
+  IRK_DISPATCH_S3(S, launch_k(prolong_add3_kernel<T, C, SS>, interior_grid3(nf), dim3(k3X, k3Y, k3Z), 0, st, nc, ec, nf, xf));
 }
 template <typename T, typename C>
 void MG3<T, C>::block_rhs(int SF, cudaStream_t st, int n, const Cls4& kc, const double* v, const double* z, int i,
                           const Vec8& cj, T* out) {
-  IRK_DISPATCH_S3(SF, block_rhs3_kernel<T, C, SS><<<interior_grid3(n), dim3(k3X, k3Y, k3Z), 0, st>>>(n, kc, v, z, i, cj, out));
+  unsigned used = 0;
+  for (int j = 0; j < SF; ++j)
+    if (cj.v[j] != 0.0) used |= 1u << j;
+  const ClsT<C> c = to_cls<C>(kc);
+  const VecT<C> w = to_vec<C>(cj);
+  IRK_DISPATCH_S3(SF, launch_k(block_rhs3_kernel<T, C, SS>, interior_grid3(n), dim3(k3X, k3Y, k3Z), 0, st, n, c, v, z, i, w, used, out));
 }
 template <typename T, typename C>
 void MG3<T, C>::scatter_stage(int SF, cudaStream_t st, int n, const T* x, int i, double* z) {
-  IRK_DISPATCH_S3(SF, scatter_stage3_kernel<T, C, SS><<<interior_grid3(n), dim3(k3X, k3Y, k3Z), 0, st>>>(n, x, i, z));
+  IRK_DISPATCH_S3(SF, launch_k(scatter_stage3_kernel<T, C, SS>, interior_grid3(n), dim3(k3X, k3Y, k3Z), 0, st, n, x, i, z));
 }
 template <typename T, typename C>
 void MG3<T, C>::coarse_solve(int S, cudaStream_t st, int nint, const C* binv, const int* map, const T* b, T* x) {
   const int threads = 256, rows_per_block = threads / 32;
   int gx = (nint + rows_per_block - 1) / rows_per_block;
   if (gx > 152 * 4) gx = 152 * 4;
-  coarse_solve3_kernel<T, C><<<dim3(gx, S), threads, sizeof(C) * (size_t)nint, st>>>(nint, binv, map, b, x, S);
+  launch_k(coarse_solve3_kernel<T, C>, dim3(gx, S), threads, sizeof(C) * (size_t)nint, st, nint, binv, map, b, x, S);
 }
 
 }  // namespace irk

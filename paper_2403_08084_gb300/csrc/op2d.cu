@@ -39,6 +39,7 @@ __device__ __forceinline__ double k_apply_masked(const double* __restrict__ cf, 
 template <int S>
 __global__ void __launch_bounds__(BX* BY) stage_apply_kernel(int nx, const double* __restrict__ cf, double hm, Mat4 mix,
                                                              const double* __restrict__ x, double* __restrict__ y) {
+  IRK_PDL_ENTRY;
   const int ix = blockIdx.x * BX + threadIdx.x;
   const int iy = blockIdx.y * BY + threadIdx.y;
   if (ix >= nx || iy >= nx) return;
@@ -65,6 +66,7 @@ template <int S>
 __global__ void __launch_bounds__(BX* BY) rhs_kernel(int nx, const double* __restrict__ cf, const double* __restrict__ u,
                                                      const double* __restrict__ fsp, Vec8 fcoef,
                                                      const double* __restrict__ fst, double* __restrict__ r) {
+  IRK_PDL_ENTRY;
   const int ix = blockIdx.x * BX + threadIdx.x;
   const int iy = blockIdx.y * BY + threadIdx.y;
   if (ix >= nx || iy >= nx) return;
@@ -88,6 +90,7 @@ __global__ void __launch_bounds__(BX* BY) rhs_kernel(int nx, const double* __res
 template <int S>
 __global__ void rk_update_kernel(int nx, const double* __restrict__ u, const double* __restrict__ k, Vec8 bdt,
                                  double* __restrict__ out) {
+  IRK_PDL_ENTRY;
   const int ix = blockIdx.x * BX + threadIdx.x;
   const int iy = blockIdx.y * BY + threadIdx.y;
   if (ix >= nx || iy >= nx) return;
@@ -105,6 +108,7 @@ __global__ void rk_update_kernel(int nx, const double* __restrict__ u, const dou
 template <int S>
 __global__ void adjoint_lambda_kernel(int nx, const double* __restrict__ cf, const double* __restrict__ lam1,
                                       const double* __restrict__ mu, double* __restrict__ lam0) {
+  IRK_PDL_ENTRY;
   const int ix = blockIdx.x * BX + threadIdx.x;
   const int iy = blockIdx.y * BY + threadIdx.y;
   if (ix >= nx || iy >= nx) return;
@@ -122,6 +126,7 @@ __global__ void adjoint_lambda_kernel(int nx, const double* __restrict__ cf, con
 // y = (M + sigma K) x for one internal single-stage vector (boundary entries zero).
 __global__ void block_apply_kernel(int nx, const double* __restrict__ cf, double hm, double sigma,
                                    const double* __restrict__ x, double* __restrict__ y) {
+  IRK_PDL_ENTRY;
   const int ix = 1 + blockIdx.x * BX + threadIdx.x;
   const int iy = 1 + blockIdx.y * BY + threadIdx.y;
   if (ix > nx - 2 || iy > nx - 2) return;
@@ -131,6 +136,7 @@ __global__ void block_apply_kernel(int nx, const double* __restrict__ cf, double
 
 // y = M x for a caller-supplied nodal vector (boundary entries of x read as 0).
 __global__ void mass_apply_kernel(int nx, double hm, const double* __restrict__ x, double* __restrict__ y) {
+  IRK_PDL_ENTRY;
   const int ix = blockIdx.x * BX + threadIdx.x;
   const int iy = blockIdx.y * BY + threadIdx.y;
   if (ix >= nx || iy >= nx) return;
@@ -154,6 +160,7 @@ template <int S>
 __global__ void cell_gradient_kernel(int N, const double* __restrict__ kappa, const double* __restrict__ u,
                                      const double* __restrict__ k, Mat4 dtA, const double* __restrict__ mu,
                                      double* __restrict__ grad) {
+  IRK_PDL_ENTRY;
   const int cx = blockIdx.x * BX + threadIdx.x;
   const int cy = blockIdx.y * BY + threadIdx.y;
   if (cx >= N || cy >= N) return;
@@ -200,32 +207,32 @@ __global__ void cell_gradient_kernel(int N, const double* __restrict__ kappa, co
 
 void launch_stage_apply(int S, cudaStream_t st, int nx, const double* cf, double hm, const Mat4& mix, const double* x,
                         double* y) {
-  IRK_DISPATCH_S(S, stage_apply_kernel<SS><<<all_nodes_grid(nx), dim3(BX, BY), 0, st>>>(nx, cf, hm, mix, x, y));
+  IRK_DISPATCH_S(S, launch_k(stage_apply_kernel<SS>, all_nodes_grid(nx), dim3(BX, BY), 0, st, nx, cf, hm, mix, x, y));
 }
 void launch_rhs(int S, cudaStream_t st, int nx, const double* cf, const double* u, const double* fsp,
                 const Vec8& fcoef, const double* fst, double* r) {
-  IRK_DISPATCH_S(S, rhs_kernel<SS><<<all_nodes_grid(nx), dim3(BX, BY), 0, st>>>(nx, cf, u, fsp, fcoef, fst, r));
+  IRK_DISPATCH_S(S, launch_k(rhs_kernel<SS>, all_nodes_grid(nx), dim3(BX, BY), 0, st, nx, cf, u, fsp, fcoef, fst, r));
 }
 void launch_rk_update(int S, cudaStream_t st, int nx, const double* u, const double* k, const Vec8& bdt,
                       double* out) {
-  IRK_DISPATCH_S(S, rk_update_kernel<SS><<<all_nodes_grid(nx), dim3(BX, BY), 0, st>>>(nx, u, k, bdt, out));
+  IRK_DISPATCH_S(S, launch_k(rk_update_kernel<SS>, all_nodes_grid(nx), dim3(BX, BY), 0, st, nx, u, k, bdt, out));
 }
 void launch_adjoint_lambda(int S, cudaStream_t st, int nx, const double* cf, const double* lam_np1, const double* mu,
                            double* lam_n) {
-  IRK_DISPATCH_S(S, adjoint_lambda_kernel<SS><<<all_nodes_grid(nx), dim3(BX, BY), 0, st>>>(nx, cf, lam_np1, mu, lam_n));
+  IRK_DISPATCH_S(S, launch_k(adjoint_lambda_kernel<SS>, all_nodes_grid(nx), dim3(BX, BY), 0, st, nx, cf, lam_np1, mu, lam_n));
 }
 void launch_block_apply(cudaStream_t st, int nx, const double* cf, double hm, double sigma, const double* x,
                         double* y) {
   dim3 g((nx - 2 + BX - 1) / BX, (nx - 2 + BY - 1) / BY);
-  block_apply_kernel<<<g, dim3(BX, BY), 0, st>>>(nx, cf, hm, sigma, x, y);
+  launch_k(block_apply_kernel, g, dim3(BX, BY), 0, st, nx, cf, hm, sigma, x, y);
 }
 void launch_mass_apply(cudaStream_t st, int nx, double hm, const double* x, double* y) {
-  mass_apply_kernel<<<all_nodes_grid(nx), dim3(BX, BY), 0, st>>>(nx, hm, x, y);
+  launch_k(mass_apply_kernel, all_nodes_grid(nx), dim3(BX, BY), 0, st, nx, hm, x, y);
 }
 void launch_cell_gradient(int S, cudaStream_t st, int N, const double* kappa, const double* u, const double* k,
                           const Mat4& dtA, const double* mu, double* grad) {
   dim3 g((N + BX - 1) / BX, (N + BY - 1) / BY);
-  IRK_DISPATCH_S(S, cell_gradient_kernel<SS><<<g, dim3(BX, BY), 0, st>>>(N, kappa, u, k, dtA, mu, grad));
+  IRK_DISPATCH_S(S, launch_k(cell_gradient_kernel<SS>, g, dim3(BX, BY), 0, st, N, kappa, u, k, dtA, mu, grad));
 }
 
 }  // namespace irk

@@ -41,6 +41,7 @@ __device__ __forceinline__ void class_sums3_masked(const double* __restrict__ u,
 template <int S>
 __global__ void __launch_bounds__(AX* AY* AZ) stage_apply3_kernel(int n, Cls4 mk, Mat4 mix,
                                                                   const double* __restrict__ x, double* __restrict__ y) {
+  IRK_PDL_ENTRY;
   IRK_3D_ALL_INDEX
   if (!interior3(ix, iy, iz, n)) {
 #pragma unroll
@@ -68,6 +69,7 @@ template <int S>
 __global__ void __launch_bounds__(AX* AY* AZ) rhs3_kernel(int n, Cls4 mk, const double* __restrict__ u,
                                                           const double* __restrict__ fsp, Vec8 fcoef,
                                                           const double* __restrict__ fst, double* __restrict__ r) {
+  IRK_PDL_ENTRY;
   IRK_3D_ALL_INDEX
   if (!interior3(ix, iy, iz, n)) {
 #pragma unroll
@@ -92,6 +94,7 @@ __global__ void __launch_bounds__(AX* AY* AZ) rhs3_kernel(int n, Cls4 mk, const 
 // y = (M + sigma K) x for one internal single-stage vector (boundary entries zero).
 __global__ void __launch_bounds__(AX* AY* AZ) block_apply3_kernel(int n, Cls4 mk, double sigma,
                                                                   const double* __restrict__ x, double* __restrict__ y) {
+  IRK_PDL_ENTRY;
   const int ix = 1 + blockIdx.x * AX + threadIdx.x;
   const int iy = 1 + blockIdx.y * AY + threadIdx.y;
   const int iz = 1 + blockIdx.z * AZ + threadIdx.z;
@@ -105,6 +108,7 @@ __global__ void __launch_bounds__(AX* AY* AZ) block_apply3_kernel(int n, Cls4 mk
 template <int S>
 __global__ void rk_update3_kernel(int n, const double* __restrict__ u, const double* __restrict__ k, Vec8 bdt,
                                   double* __restrict__ out) {
+  IRK_PDL_ENTRY;
   IRK_3D_ALL_INDEX
   double v = 0.0;
   if (interior3(ix, iy, iz, n)) {
@@ -125,19 +129,19 @@ __global__ void rk_update3_kernel(int n, const double* __restrict__ u, const dou
   }
 
 void launch_stage_apply3(int S, cudaStream_t st, int n, const Cls4& mk, const Mat4& mix, const double* x, double* y) {
-  IRK_DISPATCH_S(S, stage_apply3_kernel<SS><<<all_nodes_grid3(n), dim3(AX, AY, AZ), 0, st>>>(n, mk, mix, x, y));
+  IRK_DISPATCH_S(S, launch_k(stage_apply3_kernel<SS>, all_nodes_grid3(n), dim3(AX, AY, AZ), 0, st, n, mk, mix, x, y));
 }
 void launch_rhs3(int S, cudaStream_t st, int n, const Cls4& mk, const double* u, const double* fsp,
                  const Vec8& fcoef, const double* fst, double* r) {
-  IRK_DISPATCH_S(S, rhs3_kernel<SS><<<all_nodes_grid3(n), dim3(AX, AY, AZ), 0, st>>>(n, mk, u, fsp, fcoef, fst, r));
+  IRK_DISPATCH_S(S, launch_k(rhs3_kernel<SS>, all_nodes_grid3(n), dim3(AX, AY, AZ), 0, st, n, mk, u, fsp, fcoef, fst, r));
 }
 void launch_block_apply3(cudaStream_t st, int n, const Cls4& mk, double sigma, const double* x, double* y) {
   const int m = n - 2;
   dim3 g((m + AX - 1) / AX, (m + AY - 1) / AY, (m + AZ - 1) / AZ);
-  block_apply3_kernel<<<g, dim3(AX, AY, AZ), 0, st>>>(n, mk, sigma, x, y);
+  launch_k(block_apply3_kernel, g, dim3(AX, AY, AZ), 0, st, n, mk, sigma, x, y);
 }
 void launch_rk_update3(int S, cudaStream_t st, int n, const double* u, const double* k, const Vec8& bdt, double* out) {
-  IRK_DISPATCH_S(S, rk_update3_kernel<SS><<<all_nodes_grid3(n), dim3(AX, AY, AZ), 0, st>>>(n, u, k, bdt, out));
+  IRK_DISPATCH_S(S, launch_k(rk_update3_kernel<SS>, all_nodes_grid3(n), dim3(AX, AY, AZ), 0, st, n, u, k, bdt, out));
 }
 
 }  // namespace irk
