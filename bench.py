@@ -173,7 +173,7 @@ def aggregate(world: int, steps: int, ms_max: float) -> float:
 RESTART = 50
 
 
-def make_solver(wl, precond, vcycle, orth="cgs2", tableau=None):
+def make_solver(wl, precond, vcycle, orth="cgs2", tableau=None, splitting="ai"):
     from paper_2403_08084_gb300 import Solver
     from paper_2403_08084_gb300 import tableaux as PT
 
@@ -182,7 +182,7 @@ def make_solver(wl, precond, vcycle, orth="cgs2", tableau=None):
     kap = W.lognormal_kappa(wl.dim, wl.N, 0.5, wl.kappa_seed) if wl.kappa_seed is not None else None
     solver = "dirk_cg" if name.lower() == "alexander" else "fgmres"
     sv = Solver(wl.N, tab, wl.dt, dim=wl.dim, kappa=kap, levels=wl.levels, precond=precond, vcycle=vcycle,
-                rtol=wl.rtol, orth=orth, solver=solver, restart=RESTART)
+                rtol=wl.rtol, orth=orth, solver=solver, restart=RESTART, splitting=splitting)
     return sv, tab
 
 
@@ -365,15 +365,20 @@ def variants_leg(wl, u5_ref, args, vcycle0, precond0):
         runs = [("diag", "fp64", "cgs2", None), ("rana_ld", "fp64", "cgs2", None), ("lower", "fp64", "dgks", None),
                 ("lower", "fp32", "cgs2", None), ("lower", "bf16", "cgs2", None), ("diag", "fp32", "cgs2", None),
                 ("rana_ld", "fp32", "cgs2", None), ("lower", "fp64", "cgs2", ("Alexander", 3)),
-                ("lower", "fp32", "cgs2", ("Alexander", 3))]
+                ("lower", "fp32", "cgs2", ("Alexander", 3)), ("lower", "fp32", "cgs2", "ia"),
+                ("rana_ld", "fp32", "cgs2", "ia"), ("rana_ld", "fp64", "cgs2", "ia")]
     else:
         runs = [("lower", "fp64", "cgs2", None), ("lower", "fp32", "cgs2", None), ("lower", "bf16", "cgs2", None),
                 ("rana_ld", "fp32", "cgs2", None), ("lower", "fp32", "cgs2", ("GaussLegendre", 2)),
-                ("lower", "fp32", "cgs2", ("GaussLegendre", 4)), ("lower", "bf16", "cgs2", ("GaussLegendre", 4))]
+                ("lower", "fp32", "cgs2", ("GaussLegendre", 4)), ("lower", "bf16", "cgs2", ("GaussLegendre", 4)),
+                ("rana_ld", "fp32", "cgs2", "ia")]
     for precond, vcycle, orth, tabo in runs:
         if (precond, vcycle, orth, tabo) == (precond0, vcycle0, args.orth, None):
             continue
-        sv, tab = make_solver(wl, precond, vcycle, orth, tabo)
+        split = "ia" if tabo == "ia" else "ai"
+        if tabo == "ia":
+            tabo = None
+        sv, tab = make_solver(wl, precond, vcycle, orth, tabo, split)
         u0 = torch.from_numpy(W.sine_initial(wl.dim, wl.N)).cuda()
         f = torch.from_numpy(W.sine_load_space(wl.dim, wl.N)).cuda()
         u = u0.clone()
@@ -385,7 +390,7 @@ def variants_leg(wl, u5_ref, args, vcycle0, precond0):
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         un = u.cpu().numpy()
-        key = f"{precond}/{vcycle}/{orth}" + (f"/{tab.name}" if tabo else "")
+        key = f"{precond}/{vcycle}/{orth}" + (f"/{tab.name}" if tabo else "") + ("/IA" if split == "ia" else "")
         entry = {"steps_per_s": round(nsteps / dt, 4), "ms_per_step": round(dt * 1e3 / nsteps, 3),
                  "krylov_its_per_step": round(sum(s["fgmres_its"] for s in stats) / nsteps, 2)}
         if tabo is None:

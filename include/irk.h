@@ -65,6 +65,12 @@ extern "C" {
 #define IRK_SOLVER_DIRK_CG 1 /* lower-triangular A with a_ii > 0 (DIRK, Sec. 2.3): the stages one
                                 after another, each by CG preconditioned with one V-cycle         */
 
+/* stage formulation (Sec. 2.2, Sec. 3) */
+#define IRK_SPLIT_AI 0 /* stage derivatives k: (I (x) M + dt A (x) K) k = r            (eq. block_struct_AI) */
+#define IRK_SPLIT_IA 1 /* w = (A (x) I) k: (A^{-1} (x) M + dt I (x) K) w = r          (eq. block_struct_IA);
+                          the preconditioners are then (T^{-1} (x) M) + dt (I (x) K) with T = D, L + D, U + D
+                          or L D as printed in eq. pcbjac / pcbgs / pcranald                              */
+
 /* storage / arithmetic of the multigrid V-cycles inside the FP64 FGMRES */
 #define IRK_PREC_FP64 0 /* vectors and arithmetic in double                         */
 #define IRK_PREC_FP32 1 /* vectors and arithmetic in float                          */
@@ -99,6 +105,7 @@ typedef struct {
   int maxit;        /* total FGMRES iterations allowed per solve (default 500) */
   int orth;         /* IRK_ORTH_* (default IRK_ORTH_CGS2) */
   int solver;       /* IRK_SOLVER_* (default IRK_SOLVER_FGMRES) */
+  int splitting;    /* IRK_SPLIT_* (default IRK_SPLIT_AI); IA needs an invertible A and FGMRES */
 } irk_options;
 
 typedef struct {
@@ -140,10 +147,12 @@ int irk_set_kappa(irk_handle* h, const double* kappa_host);
 int irk_step(irk_handle* h, const double* u_n, const double* f_space, const double* f_coef,
              const double* f_stages, double* u_np1, double* stages_out, irk_stats* stats);
 
-/* Solve (I (x) M + dt A (x) K) k = r for a given stage vector r (no RK update). */
+/* Solve (I (x) M + dt A (x) K) k = r for a given stage vector r (no RK update); with IRK_SPLIT_IA
+ * the IA system is solved for w and k = (A^{-1} (x) I) w is returned. */
 int irk_solve(irk_handle* h, const double* r, double* k, irk_stats* stats);
 
-/* y = (I (x) M + dt A (x) K) x for stage vectors (transpose != 0: A^T instead of A). */
+/* y = (I (x) M + dt A (x) K) x for stage vectors (transpose != 0: A^T instead of A);
+ * with IRK_SPLIT_IA: y = (A^{-1} (x) M + dt I (x) K) x (A^{-T} for transpose). */
 int irk_apply_operator(irk_handle* h, const double* x, double* y, int transpose);
 
 /* y = M x for nodal vectors (the Q1 mass matrix; boundary entries of x read as 0,

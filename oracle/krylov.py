@@ -59,6 +59,44 @@ class BlockPreconditioner:
         return z.reshape(-1)
 
 
+class IABlockPreconditioner:
+    """Block preconditioners for the IA form (Sec. 3, eq. block_struct_IA), as the paper prints them
+    (Sec. 3.1, eq. pcbjac / pcbgs / pcranald):
+
+        P = (T^{-1} (x) M) + dt (I (x) K),   T = D (block Jacobi), L + D (block Gauss-Seidel) or L D (Rana),
+
+    i.e. block (i, j) = (T^{-1})_ij M for j < i and diagonal blocks (1/T_ii) M + dt K.  ``block_solves[i]``
+    approximates (M + dt T_ii K)^{-1}; the diagonal block inverse is T_ii times it.
+    """
+
+    def __init__(self, T: np.ndarray, M, dt: float, block_solves, diagonal_only: bool = False):
+        T = np.asarray(T, dtype=np.float64)
+        self.s = T.shape[0]
+        self.T = np.diag(np.diag(T)) if diagonal_only else np.tril(T)
+        self.Tinv = np.linalg.inv(self.T)
+        self.M, self.dt, self.solves = M, float(dt), block_solves
+
+    def __call__(self, v: np.ndarray) -> np.ndarray:
+        s = self.s
+        v = v.reshape(s, -1)
+        z = np.zeros_like(v)
+        for i in range(s):
+            rhs = v[i].copy()
+            for j in range(i):
+                if self.Tinv[i, j] != 0.0:
+                    rhs -= self.Tinv[i, j] * (self.M @ z[j])
+            z[i] = self.T[i, i] * self.solves[i](rhs)
+        return z.reshape(-1)
+
+
+def ia_operator(M, K, A: np.ndarray, dt: float):
+    """A^{-1} (x) M + dt I (x) K (Sec. 3, eq. block_struct_IA)."""
+    import scipy.sparse as sp
+
+    s = A.shape[0]
+    return (sp.kron(sp.csr_matrix(np.linalg.inv(A)), M) + dt * sp.kron(sp.identity(s), K)).tocsr()
+
+
 def ldu(A: np.ndarray):
     """A = L D U without pivoting (L unit lower, D diagonal, U unit upper), by Gaussian elimination."""
     A = np.asarray(A, dtype=np.float64)

@@ -21,6 +21,7 @@ PC = {"diag": 0, "lower": 1, "upper": 2, "rana_ld": 3}
 PREC = {"fp64": 0, "fp32": 1, "bf16": 2}
 ORTH = {"cgs2": 0, "dgks": 1}
 SOLVER = {"fgmres": 0, "dirk_cg": 1}
+SPLIT = {"ai": 0, "ia": 1}
 MAX_STAGES = 4
 _ERRNAMES = {-1: "IRK_EINVAL", -2: "IRK_ENOMEM", -3: "IRK_ECUDA", -4: "IRK_ENOCONV", -5: "IRK_ENONFINITE"}
 
@@ -43,7 +44,7 @@ class irk_tableau(C.Structure):
 class irk_options(C.Structure):
     _fields_ = [("precond", C.c_int), ("vcycle_prec", C.c_int), ("nu_pre", C.c_int), ("nu_post", C.c_int),
                 ("omega", C.c_double), ("rtol", C.c_double), ("restart", C.c_int), ("maxit", C.c_int),
-                ("orth", C.c_int), ("solver", C.c_int)]
+                ("orth", C.c_int), ("solver", C.c_int), ("splitting", C.c_int)]
 
 
 class irk_stats(C.Structure):

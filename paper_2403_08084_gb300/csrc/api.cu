@@ -90,6 +90,8 @@ struct irk_handle {
   cudaStream_t st = nullptr;
   std::vector<double> A, b, c, kappa;
   std::vector<double> Ap;  // the preconditioner's approximation of A: tril(A), or L D from A = L D U
+  // IA form: A^{-1}, the preconditioner matrix T (D, L + D, U + D or L D), T^{-1}, and A^{-T} b
+  std::vector<double> Ainv, Tm, Tinv, bIA;
   std::vector<Level> lev;
   // coarsest-level exact solve
   int nint = 0;
@@ -273,6 +275,30 @@ inline double n_int(int nx) { return (double)(nx - 2) * (double)(nx - 2); }
 // ----------------------------------------------------------------------------
 // setup
 // ----------------------------------------------------------------------------
+// Inverse of a small dense s x s matrix (Gauss-Jordan, partial pivoting); false if singular.
+bool small_inverse(const std::vector<double>& A, int s, std::vector<double>& inv) {
+  std::vector<double> B = A;
+  inv.assign(s * s, 0.0);
+  for (int i = 0; i < s; ++i) inv[i * s + i] = 1.0;
+  double scale = 0.0;
+  for (double v : A) scale = std::max(scale, std::fabs(v));
+  for (int k = 0; k < s; ++k) {
+    int piv = k;
+    for (int r = k + 1; r < s; ++r)
+      if (std::fabs(B[r * s + k]) > std::fabs(B[piv * s + k])) piv = r;
+    if (!(std::fabs(B[piv * s + k]) > 1e-13 * scale)) return false;
+    for (int c = 0; c < s; ++c) std::swap(B[k * s + c], B[piv * s + c]), std::swap(inv[k * s + c], inv[piv * s + c]);
+    const double d = 1.0 / B[k * s + k];
+    for (int c = 0; c < s; ++c) B[k * s + c] *= d, inv[k * s + c] *= d;
+    for (int r = 0; r < s; ++r) {
+      if (r == k) continue;
+      const double f = B[r * s + k];
+      for (int c = 0; c < s; ++c) B[r * s + c] -= f * B[k * s + c], inv[r * s + c] -= f * inv[k * s + c];
+    }
+  }
+  return true;
+}
+
 int validate(const irk_mesh* mesh, const irk_tableau* tab, double dt, const irk_options* opt) {
   if (!mesh || !tab || !opt) return fail(IRK_EINVAL, "null mesh, tableau or options");
   if (mesh->dim != 2 && mesh->dim != 3) return fail(IRK_EINVAL, "dim = %d: must be 2 or 3", mesh->dim);
@@ -323,6 +349,10 @@ int validate(const irk_mesh* mesh, const irk_tableau* tab, double dt, const irk_
   if (opt->orth != IRK_ORTH_CGS2 && opt->orth != IRK_ORTH_DGKS) return fail(IRK_EINVAL, "bad orth %d", opt->orth);
   if (opt->solver != IRK_SOLVER_FGMRES && opt->solver != IRK_SOLVER_DIRK_CG)
     return fail(IRK_EINVAL, "bad solver %d", opt->solver);
+  if (opt->splitting != IRK_SPLIT_AI && opt->splitting != IRK_SPLIT_IA)
+    return fail(IRK_EINVAL, "bad splitting %d", opt->splitting);
+  if (opt->splitting == IRK_SPLIT_IA && opt->solver != IRK_SOLVER_FGMRES)
+    return fail(IRK_EINVAL, "the IA splitting is implemented for the FGMRES solver");
   if (opt->solver == IRK_SOLVER_DIRK_CG) {
     for (int i = 0; i < s; ++i) {
       if (!(tab->A[i * s + i] > 0.0)) return fail(IRK_EINVAL, "DIRK solver needs a_ii > 0 (a_%d%d = %g)", i, i, tab->A[i * s + i]);
@@ -466,6 +496,28 @@ int create(irk_handle** out, const irk_mesh* mesh, const irk_tableau* tab, doubl
     }
     for (int i = 0; i < s; ++i)
       for (int j = 0; j < s; ++j) h->Ap[i * s + j] = (j <= i) ? Lm[i * s + j] * Um[j * s + j] : 0.0;
+  }
+  if (opt->splitting == IRK_SPLIT_IA) {
+    if (!small_inverse(h->A, s, h->Ainv)) {
+      destroy(h);
+      return fail(IRK_EINVAL, "the IA splitting needs an invertible Butcher matrix");
+    }
+    // T: the part of Ap the preconditioner keeps (D, L + D, U + D; Rana: L D is already lower triangular)
+    h->Tm.assign(s * s, 0.0);
+    for (int i = 0; i < s; ++i)
+      for (int j = 0; j < s; ++j) {
+        const bool keep = (i == j) || (opt->precond == IRK_PC_LOWER && j < i) ||
+                          (opt->precond == IRK_PC_UPPER && j > i) || (opt->precond == IRK_PC_RANA_LD && j < i);
+        if (keep && s > 1) h->Tm[i * s + j] = h->Ap[i * s + j];
+        if (s == 1) h->Tm[0] = h->Ap[0];
+      }
+    if (!small_inverse(h->Tm, s, h->Tinv)) {
+      destroy(h);
+      return fail(IRK_EINVAL, "the IA preconditioner matrix is singular (a zero diagonal entry?)");
+    }
+    h->bIA.assign(s, 0.0);
+    for (int j = 0; j < s; ++j)
+      for (int i = 0; i < s; ++i) h->bIA[j] += tab->b[i] * h->Ainv[i * s + j];
   }
   h->b.assign(tab->b, tab->b + s);
   h->c.assign(tab->c, tab->c + s);
@@ -773,6 +825,7 @@ int precond_apply(irk_handle* h, const double* v, double* z, bool transpose) {
   Level& L0 = h->lev[0];
   cudaStream_t st = h->st;
   const double p = sizeof(T), c = sizeof(C), ne = (double)h->ne;
+  const bool ia = (h->opt.splitting == IRK_SPLIT_IA);
   if (h->opt.precond == IRK_PC_DIAG || s == 1) {
     if constexpr (std::is_same<T, double>::value) {
       vcycle<T, C>(h, s, 0, v, z, nu1, nu2);
@@ -784,6 +837,12 @@ int precond_apply(irk_handle* h, const double* v, double* z, bool transpose) {
       T* x = vcycle<T, C>(h, s, 0, (const T*)L0.b, nullptr, nu1, nu2);
       KScope k(h, IRK_K_OTHER, ne * (8 + p), 0);
       MG::cast_from(st, x, z, h->ne);
+    }
+    if (ia) {  // IA diagonal blocks (1/a_ii) M + dt K = (1/a_ii)(M + dt a_ii K): scale the V-cycle output
+      Vec8 sc{};
+      for (int i = 0; i < s; ++i) sc.v[i] = h->Tm[i * s + i];
+      KScope k(h, IRK_K_OTHER, 16.0 * ne, ne);
+      launch_stage_scale(s, st, L0.nn, sc, z);
     }
     CK_LAUNCH();
     return IRK_OK;
@@ -802,13 +861,20 @@ int precond_apply(irk_handle* h, const double* v, double* z, bool transpose) {
     int done = 0;
     for (int j = 0; j < s; ++j) {
       const bool solved = lower ? (j < i) : (j > i);
-      const double a = transpose ? h->Ap[j * s + i] : h->Ap[i * s + j];
-      cj.v[j] = solved ? h->dt * a : 0.0;
+      // AI: dt (Ap)_ij couples through K; IA: (T^{-1})_ij couples through M
+      const double a = ia ? h->Tinv[i * s + j] : (transpose ? h->Ap[j * s + i] : h->Ap[i * s + j]);
+      cj.v[j] = solved ? (ia ? a : h->dt * a) : 0.0;
       done += (solved && a != 0.0) ? 1 : 0;
     }
     {  // single-stage right-hand side in level-0 b (precision T)
       KScope k(h, IRK_K_BLOCK_RHS, n * (8 + done * 8 + (d3 ? 0 : kCoef2 * c) + p), (d3 ? 32.0 : 19.0) * done * n);
-      if (d3) {
+      if (ia && d3) {
+        Cls4 mc{};
+        for (int q = 0; q < 4; ++q) mc.v[0][q] = L0.mcls[q];
+        MG3<T, C>::block_rhs(s, st, L0.nx, mc, v, z, i, cj, (T*)L0.b);
+      } else if (ia) {
+        MG::block_rhs_mass(s, st, L0.nx, L0.hm, v, z, i, cj, (T*)L0.b);
+      } else if (d3) {
         MG3<T, C>::block_rhs(s, st, L0.nx, kc, v, z, i, cj, (T*)L0.b);
       } else if constexpr (std::is_same<C, float>::value) {
         MG2K<T, C>::block_rhs(s, st, L0.nx, (const C*)h->kappa_f, v, z, i, cj, (T*)L0.b);
@@ -818,10 +884,11 @@ int precond_apply(irk_handle* h, const double* v, double* z, bool transpose) {
     }
     T* x = vcycle<T, C>(h, 1, i, (const T*)L0.b, nullptr, nu1, nu2);
     KScope k(h, IRK_K_OTHER, n * (p + 8), 0);
+    const double scale = ia ? h->Tm[i * s + i] : 1.0;
     if (d3)
-      MG3<T, C>::scatter_stage(s, st, L0.nx, x, i, z);
+      MG3<T, C>::scatter_stage(s, st, L0.nx, x, i, z, scale);
     else
-      MG::scatter_stage(s, st, L0.nx, x, i, z);
+      MG::scatter_stage(s, st, L0.nx, x, i, z, scale);
   }
   CK_LAUNCH();
   return IRK_OK;
@@ -849,9 +916,29 @@ Cls4 mass_stiff_classes(const Level& L0) {
   return mk;
 }
 
+Mat4 ia_mixing(const irk_handle* h, bool transpose) {
+  Mat4 m{};
+  const int s = h->s;
+  for (int i = 0; i < s; ++i)
+    for (int j = 0; j < s; ++j) m.v[i * s + j] = transpose ? h->Ainv[j * s + i] : h->Ainv[i * s + j];
+  return m;
+}
+
 int apply_operator(irk_handle* h, const double* x, double* y, bool transpose) {
   const Level& L0 = h->lev[0];
   const int s = h->s;
+  if (h->opt.splitting == IRK_SPLIT_IA) {
+    const double m = L0.nx - 2;
+    const double ni = (h->dim == 3) ? m * m * m : m * m;
+    KScope k(h, IRK_K_STAGE_APPLY, (double)L0.nn * (16.0 * s + (h->dim == 3 ? 0.0 : 8.0 * kCoef2)),
+             ni * s * (30.0 + 2.0 * s));
+    if (h->dim == 3)
+      launch_stage_apply3_ia(s, h->st, L0.nx, mass_stiff_classes(L0), ia_mixing(h, transpose), h->dt, x, y);
+    else
+      launch_stage_apply_ia(s, h->st, L0.nx, L0.cf_d, L0.hm, ia_mixing(h, transpose), h->dt, x, y);
+    CK_LAUNCH();
+    return IRK_OK;
+  }
   if (h->dim == 3) {
     const double m = L0.nx - 2;
     KScope k(h, IRK_K_STAGE_APPLY, (double)L0.nn * 16.0 * s, m * m * m * s * (38.0 + 2.0 * s));
@@ -1279,6 +1366,7 @@ void irk_default_options(irk_options* o) {
   o->maxit = 500;
   o->orth = IRK_ORTH_CGS2;
   o->solver = IRK_SOLVER_FGMRES;
+  o->splitting = IRK_SPLIT_AI;
 }
 
 const char* irk_last_error(void) { return g_err.c_str(); }
@@ -1370,6 +1458,8 @@ int irk_apply_mass(irk_handle* h, const double* x, double* y) {
 
 int irk_apply_preconditioner(irk_handle* h, const double* v, double* z, int transpose) {
   if (!h || !v || !z) return fail(IRK_EINVAL, "null argument");
+  if (transpose && h->opt.splitting != IRK_SPLIT_AI)
+    return fail(IRK_EINVAL, "the transposed preconditioner needs the AI splitting");
   const size_t bytes = h->ne * 8;
   const void* vd;
   void* zd;
@@ -1393,8 +1483,14 @@ int irk_solve(irk_handle* h, const double* r, double* k, irk_stats* stats) {
   bool khost;
   TRY(dev_in(h, r, bytes, 0, &rd));
   TRY(dev_out(h, k, bytes, 1, &kd, &khost));
-  const int rc = solve(h, (const double*)rd, (double*)kd, false, stats);
+  const bool ia = (h->opt.splitting == IRK_SPLIT_IA);
+  const int rc = solve(h, (const double*)rd, ia ? h->tmp : (double*)kd, false, stats);
   if (rc != IRK_OK && rc != IRK_ENOCONV) return rc;
+  if (ia) {  // k = (A^{-1} (x) I) w
+    KScope kk(h, IRK_K_OTHER, 16.0 * h->ne, 2.0 * h->s * h->ne);
+    launch_stage_mix(h->s, h->st, h->lev[0].nn, ia_mixing(h, false), h->tmp, (double*)kd);
+    CK_LAUNCH();
+  }
   if (khost) TRY(dev_out_finish(h, k, kd, bytes));
   CK(cudaStreamSynchronize(h->st));
   return rc;
@@ -1430,7 +1526,8 @@ int irk_step(irk_handle* h, const double* u_n, const double* f_space, const doub
   const int rc = solve(h, h->rhs, h->k, false, stats);
   if (rc != IRK_OK && rc != IRK_ENOCONV) return rc;
   Vec8 bdt{};
-  for (int i = 0; i < s; ++i) bdt.v[i] = h->dt * h->b[i];
+  const bool ia = (h->opt.splitting == IRK_SPLIT_IA);
+  for (int i = 0; i < s; ++i) bdt.v[i] = h->dt * (ia ? h->bIA[i] : h->b[i]);  // IA: dt (A^{-T} b) . w
   {
     KScope k(h, IRK_K_OTHER, (double)nn * (16.0 + 8.0 * s), 2.0 * s * n_int(h->lev[0].nx));
     if (h->dim == 3)
@@ -1439,7 +1536,13 @@ int irk_step(irk_handle* h, const double* u_n, const double* f_space, const doub
       launch_rk_update(s, h->st, h->lev[0].nx, (const double*)ud, h->k, bdt, (double*)outd);
   }
   CK_LAUNCH();
-  if (kd) CK(cudaMemcpyAsync(kd, h->k, sb, cudaMemcpyDeviceToDevice, h->st));
+  if (kd && ia) {  // stages k = (A^{-1} (x) I) w
+    KScope kk(h, IRK_K_OTHER, 16.0 * h->ne, 2.0 * s * h->ne);
+    launch_stage_mix(s, h->st, nn, ia_mixing(h, false), h->k, (double*)kd);
+    CK_LAUNCH();
+  } else if (kd) {
+    CK(cudaMemcpyAsync(kd, h->k, sb, cudaMemcpyDeviceToDevice, h->st));
+  }
   if (outhost) TRY(dev_out_finish(h, u_np1, outd, nb));
   if (khost) TRY(dev_out_finish(h, stages_out, kd, sb));
   CK(cudaStreamSynchronize(h->st));
@@ -1450,6 +1553,7 @@ int irk_step_adjoint(irk_handle* h, const double* u_n, const double* stages, con
                      double* grad_accum, irk_stats* stats) {
   if (!h || !u_n || !stages || !lam_np1 || !lam_n) return fail(IRK_EINVAL, "null argument");
   if (h->dim != 2) return fail(IRK_EINVAL, "irk_step_adjoint is implemented for dim = 2");
+  if (h->opt.splitting != IRK_SPLIT_AI) return fail(IRK_EINVAL, "irk_step_adjoint needs the AI splitting");
   const int s = h->s;
   const size_t nn = h->lev[0].nn, nb = nn * 8, sb = h->ne * 8, gb = (size_t)h->N * h->N * 8;
   const void *ud, *kd, *ld;

@@ -36,7 +36,10 @@ struct MG2 {
   static void prolong_add(int S, cudaStream_t st, int nxc, const T* ec, int nxf, T* xf);
   static void block_rhs(int SF, cudaStream_t st, int nx, const C* cf, const double* v, const double* z, int i,
                         const Vec8& cj, T* out);
-  static void scatter_stage(int SF, cudaStream_t st, int nx, const T* x, int i, double* z);
+  static void scatter_stage(int SF, cudaStream_t st, int nx, const T* x, int i, double* z, double scale = 1.0);
+  // IA form: out = v_i - sum_j cj[j] M z_j
+  static void block_rhs_mass(int SF, cudaStream_t st, int nx, double hm, const double* v, const double* z, int i,
+                             const Vec8& cj, T* out);
   static void cast_to(cudaStream_t st, const double* src, T* dst, size_t n);
   static void cast_from(cudaStream_t st, const T* src, double* dst, size_t n);
   static void coarse_solve(int S, cudaStream_t st, int nint, const C* binv, const int* map, const T* b, T* x);
@@ -65,7 +68,7 @@ struct MG3 {
   static void prolong_add(int S, cudaStream_t st, int nc, const T* ec, int nf, T* xf);
   static void block_rhs(int SF, cudaStream_t st, int n, const Cls4& kc, const double* v, const double* z, int i,
                         const Vec8& cj, T* out);
-  static void scatter_stage(int SF, cudaStream_t st, int n, const T* x, int i, double* z);
+  static void scatter_stage(int SF, cudaStream_t st, int n, const T* x, int i, double* z, double scale = 1.0);
   static void coarse_solve(int S, cudaStream_t st, int nint, const C* binv, const int* map, const T* b, T* x);
 };
 
@@ -74,11 +77,17 @@ void launch_stage_apply3(int S, cudaStream_t st, int n, const Cls4& mk, const Ma
 void launch_rhs3(int S, cudaStream_t st, int n, const Cls4& mk, const double* u, const double* fsp,
                  const Vec8& fcoef, const double* fst, double* r);
 void launch_block_apply3(cudaStream_t st, int n, const Cls4& mk, double sigma, const double* x, double* y);
+void launch_stage_apply3_ia(int S, cudaStream_t st, int n, const Cls4& mk, const Mat4& mixM, double dt,
+                            const double* x, double* y);
 void launch_rk_update3(int S, cudaStream_t st, int n, const double* u, const double* k, const Vec8& bdt, double* out);
 
 // FP64 stage-operator kernels (op2d.cu).
 void launch_stage_apply(int S, cudaStream_t st, int nx, const double* cf, double hm, const Mat4& mix, const double* x,
                         double* y);
+void launch_stage_apply_ia(int S, cudaStream_t st, int nx, const double* cf, double hm, const Mat4& mixM, double dt,
+                           const double* x, double* y);
+void launch_stage_mix(int S, cudaStream_t st, size_t nodes, const Mat4& mix, const double* in, double* out);
+void launch_stage_scale(int S, cudaStream_t st, size_t nodes, const Vec8& scale, double* z);
 void launch_rhs(int S, cudaStream_t st, int nx, const double* cf, const double* u, const double* fsp,
                 const Vec8& fcoef, const double* fst, double* r);
 void launch_rk_update(int S, cudaStream_t st, int nx, const double* u, const double* k, const Vec8& bdt,

@@ -189,16 +189,33 @@ __global__ void __launch_bounds__(kBX* kBY) block_rhs_kernel(int nx, const C* __
   st(out + p, acc);
 }
 
-// z[:, i] = x on interior nodes (single-stage x into an SF-interleaved double vector).
+// IA form: out = v_i - sum_j cj[j] M z_j (M: the level's Q1 mass stencil, scale hm).
 template <typename T, typename C, int SF>
-__global__ void __launch_bounds__(kBX* kBY) scatter_stage_kernel(int nx, const T* __restrict__ x, int i,
-                                                                 double* __restrict__ z) {
+__global__ void __launch_bounds__(kBX* kBY) block_rhs_mass_kernel(int nx, C hm, const double* __restrict__ v,
+                                                                  const double* __restrict__ z, int i, VecT<C> cj,
+                                                                  unsigned used, T* __restrict__ out) {
   IRK_PDL_ENTRY;
   const int ix = 1 + blockIdx.x * kBX + threadIdx.x;
   const int iy = 1 + blockIdx.y * kBY + threadIdx.y;
   if (ix > nx - 2 || iy > nx - 2) return;
   const int p = ix + nx * iy;
-  z[(size_t)p * SF + i] = static_cast<double>(ld<C>(x + p));
+  C acc = static_cast<C>(v[(size_t)p * SF + i]);
+#pragma unroll
+  for (int j = 0; j < SF; ++j)
+    if (used & (1u << j)) acc -= cj.v[j] * hm * m_apply_unscaled<SF, C>(z, p, nx, j);
+  st(out + p, acc);
+}
+
+// z[:, i] = scale * x on interior nodes (single-stage x into an SF-interleaved double vector).
+template <typename T, typename C, int SF>
+__global__ void __launch_bounds__(kBX* kBY) scatter_stage_kernel(int nx, const T* __restrict__ x, int i,
+                                                                 double* __restrict__ z, double scale) {
+  IRK_PDL_ENTRY;
+  const int ix = 1 + blockIdx.x * kBX + threadIdx.x;
+  const int iy = 1 + blockIdx.y * kBY + threadIdx.y;
+  if (ix > nx - 2 || iy > nx - 2) return;
+  const int p = ix + nx * iy;
+  z[(size_t)p * SF + i] = scale * static_cast<double>(ld<C>(x + p));
 }
 
 template <typename T, typename C>
@@ -312,9 +329,19 @@ void MG2<T, C>::block_rhs(int SF, cudaStream_t st, int nx, const C* cf, const do
   IRK_DISPATCH_S(SF, launch_k(block_rhs_kernel<T, C, SS>, g, blk, 0, st, nx, cf, v, z, i, c, used, out));
 }
 template <typename T, typename C>
-void MG2<T, C>::scatter_stage(int SF, cudaStream_t st, int nx, const T* x, int i, double* z) {
+void MG2<T, C>::scatter_stage(int SF, cudaStream_t st, int nx, const T* x, int i, double* z, double scale) {
   dim3 g = interior_grid(nx), blk(kBX, kBY);
-  IRK_DISPATCH_S(SF, launch_k(scatter_stage_kernel<T, C, SS>, g, blk, 0, st, nx, x, i, z));
+  IRK_DISPATCH_S(SF, launch_k(scatter_stage_kernel<T, C, SS>, g, blk, 0, st, nx, x, i, z, scale));
+}
+template <typename T, typename C>
+void MG2<T, C>::block_rhs_mass(int SF, cudaStream_t st, int nx, double hm, const double* v, const double* z, int i,
+                               const Vec8& cj, T* out) {
+  dim3 g = interior_grid(nx), blk(kBX, kBY);
+  unsigned used = 0;
+  for (int j = 0; j < SF; ++j)
+    if (cj.v[j] != 0.0) used |= 1u << j;
+  const VecT<C> c = to_vec<C>(cj);
+  IRK_DISPATCH_S(SF, launch_k(block_rhs_mass_kernel<T, C, SS>, g, blk, 0, st, nx, (C)hm, v, z, i, c, used, out));
 }
 template <typename T, typename C>
 void MG2<T, C>::cast_to(cudaStream_t st, const double* src, T* dst, size_t n) {

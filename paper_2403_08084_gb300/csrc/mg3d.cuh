@@ -179,10 +179,10 @@ __global__ void __launch_bounds__(k3X* k3Y* k3Z) block_rhs3_kernel(int n, ClsT<C
 
 template <typename T, typename C, int SF>
 __global__ void __launch_bounds__(k3X* k3Y* k3Z) scatter_stage3_kernel(int n, const T* __restrict__ x, int i,
-                                                                       double* __restrict__ z) {
+                                                                       double* __restrict__ z, double scale) {
   IRK_PDL_ENTRY;
   IRK_3D_INDEX
-  z[(size_t)p * SF + i] = static_cast<double>(ld<C>(x + p));
+  z[(size_t)p * SF + i] = scale * static_cast<double>(ld<C>(x + p));
 }
 
 template <typename T, typename C>
@@ -260,8 +260,8 @@ void MG3<T, C>::block_rhs(int SF, cudaStream_t st, int n, const Cls4& kc, const 
   IRK_DISPATCH_S3(SF, launch_k(block_rhs3_kernel<T, C, SS>, interior_grid3(n), dim3(k3X, k3Y, k3Z), 0, st, n, c, v, z, i, w, used, out));
 }
 template <typename T, typename C>
-void MG3<T, C>::scatter_stage(int SF, cudaStream_t st, int n, const T* x, int i, double* z) {
-  IRK_DISPATCH_S3(SF, launch_k(scatter_stage3_kernel<T, C, SS>, interior_grid3(n), dim3(k3X, k3Y, k3Z), 0, st, n, x, i, z));
+void MG3<T, C>::scatter_stage(int SF, cudaStream_t st, int n, const T* x, int i, double* z, double scale) {
+  IRK_DISPATCH_S3(SF, launch_k(scatter_stage3_kernel<T, C, SS>, interior_grid3(n), dim3(k3X, k3Y, k3Z), 0, st, n, x, i, z, scale));
 }
 template <typename T, typename C>
 void MG3<T, C>::coarse_solve(int S, cudaStream_t st, int nint, const C* binv, const int* map, const T* b, T* x) {

@@ -4,6 +4,8 @@
 #include "common.cuh"
 #include "kernels.h"
 
+#include <algorithm>
+
 namespace irk {
 
 namespace {
@@ -58,6 +60,61 @@ __global__ void __launch_bounds__(BX* BY) stage_apply_kernel(int nx, const doubl
 #pragma unroll
     for (int j = 0; j < S; ++j) acc += mix.v[i * S + j] * kx[j];
     y[(size_t)p * S + i] = acc;
+  }
+}
+
+// IA form (Sec. 3, eq. block_struct_IA): y_i = sum_j mixM_ij M x_j + dt K x_i (mixM = A^{-1} or A^{-T}).
+template <int S>
+__global__ void __launch_bounds__(BX* BY) stage_apply_ia_kernel(int nx, const double* __restrict__ cf, double hm,
+                                                                Mat4 mixM, double dt, const double* __restrict__ x,
+                                                                double* __restrict__ y) {
+  IRK_PDL_ENTRY;
+  const int ix = blockIdx.x * BX + threadIdx.x;
+  const int iy = blockIdx.y * BY + threadIdx.y;
+  if (ix >= nx || iy >= nx) return;
+  const int p = ix + nx * iy;
+  if (!interior2(ix, iy, nx)) {
+#pragma unroll
+    for (int i = 0; i < S; ++i) y[(size_t)p * S + i] = 0.0;
+    return;
+  }
+  double mx[S];
+#pragma unroll
+  for (int j = 0; j < S; ++j) mx[j] = hm * m_apply_unscaled<S, double>(x, p, nx, j);
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    double acc = dt * k_apply<S, double>(cf, x, p, nx, i);
+#pragma unroll
+    for (int j = 0; j < S; ++j) acc += mixM.v[i * S + j] * mx[j];
+    y[(size_t)p * S + i] = acc;
+  }
+}
+
+// out_i = sum_j mix_ij in_j for every node of a stage vector (the IA back-transform k = (A^{-1} (x) I) w).
+template <int S>
+__global__ void stage_mix_kernel(size_t nodes, Mat4 mix, const double* __restrict__ in, double* __restrict__ out) {
+  IRK_PDL_ENTRY;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < nodes; q += (size_t)gridDim.x * blockDim.x) {
+    double v[S];
+#pragma unroll
+    for (int j = 0; j < S; ++j) v[j] = in[q * S + j];
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      double acc = 0.0;
+#pragma unroll
+      for (int j = 0; j < S; ++j) acc += mix.v[i * S + j] * v[j];
+      out[q * S + i] = acc;
+    }
+  }
+}
+
+// z_i *= scale_i for every node of a stage vector.
+template <int S>
+__global__ void stage_scale_kernel(size_t nodes, Vec8 scale, double* __restrict__ z) {
+  IRK_PDL_ENTRY;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < nodes; q += (size_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int i = 0; i < S; ++i) z[q * S + i] *= scale.v[i];
   }
 }
 
@@ -208,6 +265,18 @@ __global__ void cell_gradient_kernel(int N, const double* __restrict__ kappa, co
 void launch_stage_apply(int S, cudaStream_t st, int nx, const double* cf, double hm, const Mat4& mix, const double* x,
                         double* y) {
   IRK_DISPATCH_S(S, launch_k(stage_apply_kernel<SS>, all_nodes_grid(nx), dim3(BX, BY), 0, st, nx, cf, hm, mix, x, y));
+}
+void launch_stage_apply_ia(int S, cudaStream_t st, int nx, const double* cf, double hm, const Mat4& mixM, double dt,
+                           const double* x, double* y) {
+  IRK_DISPATCH_S(S, launch_k(stage_apply_ia_kernel<SS>, all_nodes_grid(nx), dim3(BX, BY), 0, st, nx, cf, hm, mixM, dt, x, y));
+}
+void launch_stage_mix(int S, cudaStream_t st, size_t nodes, const Mat4& mix, const double* in, double* out) {
+  int blocks = (int)std::min<size_t>((nodes + 255) / 256, 152 * 8);
+  IRK_DISPATCH_S(S, launch_k(stage_mix_kernel<SS>, blocks, 256, 0, st, nodes, mix, in, out));
+}
+void launch_stage_scale(int S, cudaStream_t st, size_t nodes, const Vec8& scale, double* z) {
+  int blocks = (int)std::min<size_t>((nodes + 255) / 256, 152 * 8);
+  IRK_DISPATCH_S(S, launch_k(stage_scale_kernel<SS>, blocks, 256, 0, st, nodes, scale, z));
 }
 void launch_rhs(int S, cudaStream_t st, int nx, const double* cf, const double* u, const double* fsp,
                 const Vec8& fcoef, const double* fst, double* r) {

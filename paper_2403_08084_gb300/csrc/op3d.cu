@@ -66,6 +66,34 @@ __global__ void __launch_bounds__(AX* AY* AZ) stage_apply3_kernel(int n, Cls4 mk
 }
 
 template <int S>
+__global__ void __launch_bounds__(AX* AY* AZ) stage_apply3_ia_kernel(int n, Cls4 mk, Mat4 mixM, double dt,
+                                                                     const double* __restrict__ x,
+                                                                     double* __restrict__ y) {
+  IRK_PDL_ENTRY;
+  IRK_3D_ALL_INDEX
+  if (!interior3(ix, iy, iz, n)) {
+#pragma unroll
+    for (int i = 0; i < S; ++i) y[(size_t)p * S + i] = 0.0;
+    return;
+  }
+  double kx[S], mx[S];
+#pragma unroll
+  for (int j = 0; j < S; ++j) {
+    double cs[4];
+    class_sums3<S, double>(x, p, n, j, cs);
+    mx[j] = class_apply<double>(mk.v[0], cs);
+    kx[j] = class_apply<double>(mk.v[1], cs);
+  }
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    double acc = dt * kx[i];
+#pragma unroll
+    for (int j = 0; j < S; ++j) acc += mixM.v[i * S + j] * mx[j];
+    y[(size_t)p * S + i] = acc;
+  }
+}
+
+template <int S>
 __global__ void __launch_bounds__(AX* AY* AZ) rhs3_kernel(int n, Cls4 mk, const double* __restrict__ u,
                                                           const double* __restrict__ fsp, Vec8 fcoef,
                                                           const double* __restrict__ fst, double* __restrict__ r) {
@@ -130,6 +158,10 @@ __global__ void rk_update3_kernel(int n, const double* __restrict__ u, const dou
 
 void launch_stage_apply3(int S, cudaStream_t st, int n, const Cls4& mk, const Mat4& mix, const double* x, double* y) {
   IRK_DISPATCH_S(S, launch_k(stage_apply3_kernel<SS>, all_nodes_grid3(n), dim3(AX, AY, AZ), 0, st, n, mk, mix, x, y));
+}
+void launch_stage_apply3_ia(int S, cudaStream_t st, int n, const Cls4& mk, const Mat4& mixM, double dt,
+                            const double* x, double* y) {
+  IRK_DISPATCH_S(S, launch_k(stage_apply3_ia_kernel<SS>, all_nodes_grid3(n), dim3(AX, AY, AZ), 0, st, n, mk, mixM, dt, x, y));
 }
 void launch_rhs3(int S, cudaStream_t st, int n, const Cls4& mk, const double* u, const double* fsp,
                  const Vec8& fcoef, const double* fst, double* r) {

@@ -34,7 +34,7 @@ class Solver:
     def __init__(self, n_cells: int, tableau, dt: float, *, kappa=None, levels: int = 1, dim: int = 2,
                  precond: str = "lower", vcycle: str = "fp64", nu_pre: int = 2, nu_post: int = 2,
                  omega: float = 2.0 / 3.0, rtol: float = 1e-10, restart: int = 50, maxit: int = 500,
-                 orth: str = "cgs2", solver: str = "fgmres", stream=None):
+                 orth: str = "cgs2", solver: str = "fgmres", splitting: str = "ai", stream=None):
         A = np.ascontiguousarray(tableau.A, dtype=np.float64)
         self.s = int(A.shape[0])
         self.N, self.dim, self.dt = int(n_cells), int(dim), float(dt)
@@ -61,6 +61,7 @@ class Solver:
         opt.rtol, opt.restart, opt.maxit = float(rtol), int(restart), int(maxit)
         opt.orth = L.ORTH[orth]
         opt.solver = L.SOLVER[solver]
+        opt.splitting = L.SPLIT[splitting]
         self.options = opt
         self.stream = stream if stream is not None else _current_stream()
         h = C.c_void_p()

@@ -119,3 +119,85 @@ def test_rana_ld_solve_and_iterations():
     for s in (2, 3, 4):
         assert its[("rana_ld", s)] <= its[("lower", s)], its
     print("FGMRES iterations (preconditioner, s):", its)
+
+
+# ----------------------------------------------------------------------------
+# IA splitting (Sec. 2.2, Sec. 3 eq. block_struct_IA)
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("dim,N,s", [(2, 40, 3), (3, 10, 2)])
+@pytest.mark.parametrize("transpose", [False, True])
+def test_ia_operator(dim, N, s, transpose):
+    kap = W.lognormal_kappa(2, N, 0.5, seed=60) if dim == 2 else None
+    d = fem.Discretisation(dim, N, kap)
+    ot = OT.radau_iia(s)
+    dt = 0.02
+    x = W.random_nodal(dim, N, seed=61, s=s)
+    S = krylov.ia_operator(d.M, d.K, ot.A.T if transpose else ot.A, dt)
+    y_ref = d.to_full((S @ d.to_interior(x, s).reshape(-1)).reshape(s, -1), s)
+    with Solver(N, PT.radau_iia(s), dt, dim=dim, kappa=kap, levels=1, splitting="ia") as sv:
+        y = np.empty(sv.n_nodes * s)
+        sv.apply_operator(x, y, transpose=transpose)
+    assert rel(y, y_ref) < 1e-13
+
+
+@pytest.mark.parametrize("dim,N,levels", [(2, 64, 3), (3, 16, 2)])
+@pytest.mark.parametrize("kind", ["diag", "lower", "rana_ld"])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+def test_ia_preconditioner(dim, N, levels, kind, prec, tol):
+    s, dt = 3, 1 / 64
+    kap = W.lognormal_kappa(2, N, 0.5, seed=62) if dim == 2 else None
+    d = fem.Discretisation(dim, N, kap)
+    ot = OT.radau_iia(s)
+    Tm = krylov.rana_ld(ot.A) if kind == "rana_ld" else ot.A
+    h = mg.Hierarchy(d, levels)
+    solves = [mg.VCycle(h, dt * Tm[i, i]) for i in range(s)]
+    P = krylov.IABlockPreconditioner(Tm, d.M, dt, solves, diagonal_only=(kind == "diag"))
+    v = W.random_nodal(dim, N, seed=63, s=s)
+    z_ref = d.to_full(P(d.to_interior(v, s).reshape(-1)).reshape(s, -1), s)
+    with Solver(N, PT.radau_iia(s), dt, dim=dim, kappa=kap, levels=levels, precond=kind, vcycle=prec,
+                splitting="ia") as sv:
+        z = np.empty(sv.n_nodes * s)
+        sv.apply_preconditioner(v, z)
+    assert rel(z, z_ref) < tol
+
+
+@pytest.mark.parametrize("kind", ["lower", "rana_ld"])
+def test_ia_solve_and_iterations(kind):
+    N, levels, s, dt = 64, 3, 3, 1 / 64
+    kap = W.lognormal_kappa(2, N, 0.5, seed=64)
+    d = fem.Discretisation(2, N, kap)
+    ot = OT.radau_iia(s)
+    r = W.random_nodal(2, N, seed=65, s=s)
+    ri = d.to_interior(r, s)
+    k_ref = rk.KroneckerSolver(d.M, d.K, ot.A, dt).solve(ri)
+    with Solver(N, PT.radau_iia(s), dt, kappa=kap, levels=levels, precond=kind, rtol=1e-12, splitting="ia") as sv:
+        k = np.empty(sv.n_nodes * s)
+        st = sv.solve(r, k)
+    assert rel(d.to_interior(k, s), k_ref) < 1e-10
+    Tm = krylov.rana_ld(ot.A) if kind == "rana_ld" else ot.A
+    h = mg.Hierarchy(d, levels)
+    P = krylov.IABlockPreconditioner(Tm, d.M, dt, [mg.VCycle(h, dt * Tm[i, i]) for i in range(s)])
+    Sia = krylov.ia_operator(d.M, d.K, ot.A, dt)
+    _, its, _, _ = krylov.fgmres(lambda v: Sia @ v, ri.reshape(-1), P, rtol=1e-12)
+    assert abs(st["fgmres_its"] - its) <= 1, (st["fgmres_its"], its)
+
+
+@pytest.mark.parametrize("dim,N,levels,prec", [(2, 48, 2, "fp64"), (2, 48, 2, "bf16"), (3, 12, 2, "fp32")])
+def test_ia_steps(dim, N, levels, prec):
+    kap = W.lognormal_kappa(2, N, 0.5, seed=66) if dim == 2 else None
+    d = fem.Discretisation(dim, N, kap)
+    ot = OT.radau_iia(3)
+    dt, steps = 1 / 32, 3
+    u0 = d.to_interior(W.sine_initial(dim, N))
+    Fs = d.to_interior(W.sine_load_space(dim, N))
+    uN, ks = rk.run(d, ot, dt, steps, u0, lambda t: W.sine_load_time(dim, t) * Fs)
+    tab = PT.radau_iia(3)
+    with Solver(N, tab, dt, dim=dim, kappa=kap, levels=levels, precond="rana_ld", vcycle=prec, rtol=1e-12,
+                splitting="ia") as sv:
+        u = W.sine_initial(dim, N)
+        f = W.sine_load_space(dim, N)
+        k = np.empty(sv.n_nodes * 3)
+        for n in range(steps):
+            sv.step(u, u, f_space=f, f_coef=[W.sine_load_time(dim, (n + c) * dt) for c in tab.c], stages_out=k)
+    assert rel(d.to_interior(u), uN) < 1e-10
+    assert rel(d.to_interior(k, 3), ks[-1]) < 1e-9

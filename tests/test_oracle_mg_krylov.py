@@ -182,3 +182,49 @@ def test_rana_ld_iterations_vs_block_gauss_seidel():
     for s in (2, 3, 4):
         assert its[("rana", s)] < its[("lower", s)]
     assert its[("rana", 4)] - its[("rana", 2)] < its[("lower", 4)] - its[("lower", 2)]
+
+
+def test_ia_system_gives_the_same_stages():
+    """w = (A (x) I) k solves (A^{-1} (x) M + dt I (x) K) w = r (Sec. 2.2, eq. stageeqw, linear case)."""
+    tab = T.radau_iia(3)
+    dt = 0.07
+    d, S = kron_setup(tab, N=8, dt=dt)
+    r = np.random.default_rng(10).standard_normal(S.shape[0])
+    k = np.linalg.solve(S.toarray(), r)
+    Sia = krylov.ia_operator(d.M, d.K, tab.A, dt)
+    w = np.kron(tab.A, np.eye(d.n)) @ k
+    assert np.abs(Sia @ w - r).max() < 1e-12 * np.abs(r).max()
+
+
+@pytest.mark.parametrize("kind", ["diag", "lower"])
+def test_ia_preconditioner_exact_on_matching_structure(kind):
+    """IA P_L with exact blocks is the IA system itself for a lower-triangular A; P_D for a diagonal A."""
+    tab = T.alexander() if kind == "lower" else T.Tableau("diag", np.diag([0.3, 0.7, 1.1]), np.ones(3) / 3,
+                                                           np.array([0.3, 0.7, 1.1]), 1, 1)
+    dt = 0.1
+    d, _ = kron_setup(tab, dt=dt)
+    Sia = krylov.ia_operator(d.M, d.K, tab.A, dt)
+    solves = [mg.ExactBlock(d.M, d.K, dt * tab.A[i, i]) for i in range(tab.s)]
+    P = krylov.IABlockPreconditioner(tab.A, d.M, dt, solves, diagonal_only=(kind == "diag"))
+    b = np.random.default_rng(11).standard_normal(Sia.shape[0])
+    x, its, rel, _ = krylov.fgmres(lambda v: Sia @ v, b, P, rtol=1e-12)
+    assert its == 1 and np.abs(Sia @ x - b).max() < 1e-11 * np.abs(b).max()
+
+
+def test_ia_rana_ld_iterations_flat_in_s():
+    """Sec. 3.1 / 4.1 (IA form, exact blocks): P_LD iteration counts barely move with s, P_L's grow."""
+    its = {}
+    for s in (2, 3, 4):
+        tab = T.radau_iia(s)
+        dt = 0.05
+        d, _ = kron_setup(tab, N=16, dt=dt)
+        Sia = krylov.ia_operator(d.M, d.K, tab.A, dt)
+        b = np.random.default_rng(12).standard_normal(Sia.shape[0])
+        for name, Tm in (("lower", tab.A), ("rana", krylov.rana_ld(tab.A))):
+            solves = [mg.ExactBlock(d.M, d.K, dt * Tm[i, i]) for i in range(s)]
+            P = krylov.IABlockPreconditioner(Tm, d.M, dt, solves)
+            its[(name, s)] = krylov.fgmres(lambda v: Sia @ v, b, P, rtol=1e-10)[1]
+    print(its)
+    assert its[("rana", 4)] - its[("rana", 2)] < its[("lower", 4)] - its[("lower", 2)]
+    for s in (2, 3, 4):
+        assert its[("rana", s)] <= its[("lower", s)]
