@@ -16,7 +16,7 @@ followed by u_{n+1} = u_n + dt sum_i b_i k_i.  (The paper's eq. rkheat writes
 the update without dt; the RK definition in Sec. 2 has it, and that reading is
 used.)  Homogeneous Dirichlet conditions: the DAE-type conditions of Sec. 2.1
 give sum_j a_ij k_j = 0 on the boundary, hence k = 0 there for invertible A, so
-boundary unknowns are eliminated.
+boundary unknowns are eliminated.  ``step_dirichlet`` handles nonzero data g.
 
 Stage vectors are stage-major arrays of shape (s, n) over interior nodes.
 """
@@ -97,3 +97,28 @@ def run(disc, tab, dt: float, steps: int, u0_int: np.ndarray, load_fn, t0: float
         stages.append(k)
         t += dt
     return u, stages
+
+
+def step_dirichlet(M_full, K_full, interior, boundary, A, b, dt, u_full, F_full, g_full):
+    """One RK step with DAE-type Dirichlet conditions (Sec. 2.1) on the full node set.
+
+    On the boundary the stage values u_n + dt sum_j a_ij k_j must equal g(t_n + c_i dt), so
+    k_B = A^{-1} (g_B - u_n,B) / dt (node by node).  The interior rows of the stage equations
+    M k_i + K (u_n + dt sum_j a_ij k_j) = F_i then determine k_I with k_B known.
+    F_full, g_full: (s, nfull) loads and boundary data at the stage times.  Returns (u_{n+1}, k) full.
+    """
+    A = np.asarray(A, dtype=np.float64)
+    s = A.shape[0]
+    I, B = interior, boundary
+    kB = np.linalg.solve(A, (g_full[:, B] - u_full[None, B])) / dt  # (s, nB)
+    M_II, K_II = M_full[I][:, I].tocsr(), K_full[I][:, I].tocsr()
+    M_IB, K_IB = M_full[I][:, B].tocsr(), K_full[I][:, B].tocsr()
+    r = np.empty((s, len(I)))
+    for i in range(s):
+        coupling = M_IB @ kB[i] + dt * sum(A[i, j] * (K_IB @ kB[j]) for j in range(s))
+        r[i] = F_full[i, I] - (K_full[I] @ u_full) - coupling
+    kI = KroneckerSolver(M_II, K_II, A, dt).solve(r)
+    k = np.zeros((s, u_full.size))
+    k[:, I] = kI
+    k[:, B] = kB
+    return u_full + dt * (np.asarray(b) @ k), k

@@ -113,3 +113,71 @@ def test_convergence_order_eigenmode(tab, p):
     use = errs > 1e-13
     slope = np.polyfit(np.log(dts[use][-3:]), np.log(errs[use][-3:]), 1)[0]
     assert abs(slope - p) < 0.25, slope
+
+
+def _full_problem(dim, N, seed=0):
+    kap = W.lognormal_kappa(dim, N, 0.5, seed)
+    Mf, Kf = fem.assemble(dim, N, kap)
+    I = fem.interior_index(dim, N)
+    B = np.setdiff1d(np.arange(Mf.shape[0]), I)
+    return Mf, Kf, I, B
+
+
+@pytest.mark.parametrize("tab,q", [(T.radau_iia(2), 2), (T.radau_iia(3), 3), (T.gauss_legendre(2), 2),
+                                   (T.alexander(), 1)])
+def test_dae_dirichlet_keeps_stage_order(tab, q):
+    """Sec. 2.1: DAE-type boundary conditions retain the stage order.  u(t) = sum_k t^k U_k with
+    nonzero boundary values, g = u on the boundary, F = M u' + K u: exact for degree <= q, not q + 1."""
+    Mf, Kf, I, B = _full_problem(2, 5, seed=3)
+    rng = np.random.default_rng(6)
+    dt, steps = 0.1, 3
+    for deg, exact in ((q, True), (q + 1, False)):
+        U = rng.standard_normal((deg + 1, Mf.shape[0]))
+        u_of = lambda t: sum(t**k * U[k] for k in range(deg + 1))  # noqa: E731
+        du_of = lambda t: sum(k * t ** (k - 1) * U[k] for k in range(1, deg + 1))  # noqa: E731
+        u = u_of(0.0)
+        for n in range(steps):
+            ts = [(n + c) * dt for c in tab.c]
+            F = np.stack([Mf @ du_of(t) + Kf @ u_of(t) for t in ts])
+            g = np.stack([u_of(t) for t in ts])
+            u, _ = rk.step_dirichlet(Mf, Kf, I, B, tab.A, tab.b, dt, u, F, g)
+        err = np.abs(u - u_of(steps * dt)).max() / np.abs(u_of(steps * dt)).max()
+        assert (err < 1e-12) if exact else (err > 1e-9), (deg, err)
+
+
+def test_dae_dirichlet_stiffly_accurate_boundary_and_homogeneous_limit():
+    """RadauIIA is stiffly accurate: u_{n+1} = g(t_{n+1}) on the boundary (Sec. 2.1); with g = 0 the
+    step equals the homogeneous one."""
+    tab = T.radau_iia(3)
+    Mf, Kf, I, B = _full_problem(2, 6, seed=4)
+    rng = np.random.default_rng(7)
+    dt = 0.05
+    u = rng.standard_normal(Mf.shape[0])
+    F = rng.standard_normal((3, Mf.shape[0]))
+    g = rng.standard_normal((3, Mf.shape[0]))
+    u1, k = rk.step_dirichlet(Mf, Kf, I, B, tab.A, tab.b, dt, u, F, g)
+    assert np.abs(u1[B] - g[-1, B]).max() < 1e-13
+    u[B] = 0.0
+    u1, k = rk.step_dirichlet(Mf, Kf, I, B, tab.A, tab.b, dt, u, F, np.zeros_like(g))
+    M, K = Mf[I][:, I].tocsr(), Kf[I][:, I].tocsr()
+    u1h, kh = rk.step(rk.KroneckerSolver(M, K, tab.A, dt), K, tab.b, dt, u[I], F[:, I])
+    assert np.abs(u1[I] - u1h).max() < 1e-13 and np.abs(u1[B]).max() == 0.0
+
+
+def test_dae_dirichlet_incompatible_data_relaxes():
+    """The setting of Sec. 2.1's example in 2D: u0 = 0 inside, g = 1 on the boundary, f = 0.  With
+    DAE-type conditions the discrete solution relaxes to the constant 1 (which Q1 represents exactly)."""
+    tab = T.lobatto_iiic2()
+    N = 10
+    Mf, Kf = fem.assemble(2, N)
+    I = fem.interior_index(2, N)
+    B = np.setdiff1d(np.arange(Mf.shape[0]), I)
+    u = np.zeros(Mf.shape[0])
+    u[B] = 1.0
+    g = np.ones((2, Mf.shape[0]))
+    F = np.zeros((2, Mf.shape[0]))
+    errs = []
+    for n in range(40):
+        u, _ = rk.step_dirichlet(Mf, Kf, I, B, tab.A, tab.b, 0.05, u, F, g)
+        errs.append(np.abs(u - 1.0).max())
+    assert errs[-1] < 1e-3 and all(b <= a + 1e-15 for a, b in zip(errs, errs[1:]))
