@@ -147,6 +147,23 @@ int irk_set_kappa(irk_handle* h, const double* kappa_host);
 int irk_step(irk_handle* h, const double* u_n, const double* f_space, const double* f_coef,
              const double* f_stages, double* u_np1, double* stages_out, irk_stats* stats);
 
+/* One RK step with non-homogeneous Dirichlet data imposed the DAE way (Sec. 2.1): on every
+ * boundary node the stage values satisfy u_n + dt sum_j a_ij k_j = g(t_n + c_i dt), so there
+ * k = A^{-1} (g - u_n) / dt, and the interior rows of the stage equations take those boundary
+ * stages to the right-hand side.  u_np1 = u_n + dt sum_i b_i k_i on all nodes (for stiffly
+ * accurate tableaux u_np1 = g(t_{n+1}) on the boundary).
+ *   u_n        nodal, input; its boundary entries are the current boundary values.
+ *   g_stages   stage vector: g(t_n + c_i dt) at node p in g_stages[p * s + i] (boundary entries
+ *              are read, interior entries ignored).
+ *   f_space, f_coef, f_stages, u_np1, stages_out, stats: as in irk_step; F holds the loads of
+ *              the interior test functions (boundary entries ignored).  stages_out returns k on
+ *              all nodes.
+ * Needs an invertible Butcher matrix (IRK_EINVAL otherwise).  With IRK_SPLIT_IA the boundary
+ * values of w = (A (x) I) k are (g - u_n) / dt directly.  Returns IRK_ENOCONV as irk_step. */
+int irk_step_dirichlet(irk_handle* h, const double* u_n, const double* g_stages, const double* f_space,
+                       const double* f_coef, const double* f_stages, double* u_np1, double* stages_out,
+                       irk_stats* stats);
+
 /* Solve (I (x) M + dt A (x) K) k = r for a given stage vector r (no RK update); with IRK_SPLIT_IA
  * the IA system is solved for w and k = (A^{-1} (x) I) w is returned. */
 int irk_solve(irk_handle* h, const double* r, double* k, irk_stats* stats);

@@ -83,6 +83,7 @@ _SIGNATURES = {
     "irk_destroy": (C.c_int, [_P]),
     "irk_set_kappa": (C.c_int, [_P, _P]),
     "irk_step": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, C.POINTER(irk_stats)]),
+    "irk_step_dirichlet": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, C.POINTER(irk_stats)]),
     "irk_solve": (C.c_int, [_P, _P, _P, C.POINTER(irk_stats)]),
     "irk_apply_operator": (C.c_int, [_P, _P, _P, C.c_int]),
     "irk_apply_mass": (C.c_int, [_P, _P, _P]),

@@ -92,6 +92,7 @@ struct irk_handle {
   std::vector<double> Ap;  // the preconditioner's approximation of A: tril(A), or L D from A = L D U
   // IA form: A^{-1}, the preconditioner matrix T (D, L + D, U + D or L D), T^{-1}, and A^{-T} b
   std::vector<double> Ainv, Tm, Tinv, bIA;
+  bool ainv_ok = false;  // A is invertible and Ainv holds A^{-1}
   std::vector<Level> lev;
   // coarsest-level exact solve
   int nint = 0;
@@ -110,6 +111,7 @@ struct irk_handle {
   int* iflag = nullptr;  // device flags (re-orthogonalisation decision)
   double* pinned = nullptr;  // host-visible copies of the residual estimate
   double *rhs = nullptr, *k = nullptr, *tmp = nullptr;
+  double* bnd = nullptr;  // boundary unknowns of irk_step_dirichlet (allocated on first use)
   DevBuf stage_bufs[8];
   int vcycles = 0;
   // one CUDA graph per FGMRES iteration index j and direction (captured on first use)
@@ -443,7 +445,7 @@ void destroy(irk_handle* h) {
   dfree(h->cmap), dfree(h->binv_d), dfree(h->binv_f), dfree(h->kappa_d), dfree(h->kappa_f);
   dfree(h->V), dfree(h->Z), dfree(h->H), dfree(h->cs), dfree(h->sn), dfree(h->g), dfree(h->y);
   dfree(h->h1), dfree(h->h2), dfree(h->partial), dfree(h->scal), dfree(h->iflag);
-  dfree(h->rhs), dfree(h->k), dfree(h->tmp);
+  dfree(h->rhs), dfree(h->k), dfree(h->tmp), dfree(h->bnd);
   for (DevBuf& b : h->stage_bufs) dfree(b.p);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   for (auto& gv : h->graphs)
@@ -497,8 +499,9 @@ int create(irk_handle** out, const irk_mesh* mesh, const irk_tableau* tab, doubl
     for (int i = 0; i < s; ++i)
       for (int j = 0; j < s; ++j) h->Ap[i * s + j] = (j <= i) ? Lm[i * s + j] * Um[j * s + j] : 0.0;
   }
+  h->ainv_ok = small_inverse(h->A, s, h->Ainv);
   if (opt->splitting == IRK_SPLIT_IA) {
-    if (!small_inverse(h->A, s, h->Ainv)) {
+    if (!h->ainv_ok) {
       destroy(h);
       return fail(IRK_EINVAL, "the IA splitting needs an invertible Butcher matrix");
     }
@@ -1537,6 +1540,87 @@ int irk_step(irk_handle* h, const double* u_n, const double* f_space, const doub
   }
   CK_LAUNCH();
   if (kd && ia) {  // stages k = (A^{-1} (x) I) w
+    KScope kk(h, IRK_K_OTHER, 16.0 * h->ne, 2.0 * s * h->ne);
+    launch_stage_mix(s, h->st, nn, ia_mixing(h, false), h->k, (double*)kd);
+    CK_LAUNCH();
+  } else if (kd) {
+    CK(cudaMemcpyAsync(kd, h->k, sb, cudaMemcpyDeviceToDevice, h->st));
+  }
+  if (outhost) TRY(dev_out_finish(h, u_np1, outd, nb));
+  if (khost) TRY(dev_out_finish(h, stages_out, kd, sb));
+  CK(cudaStreamSynchronize(h->st));
+  return rc;
+}
+
+int irk_step_dirichlet(irk_handle* h, const double* u_n, const double* g_stages, const double* f_space,
+                       const double* f_coef, const double* f_stages, double* u_np1, double* stages_out,
+                       irk_stats* stats) {
+  if (!h || !u_n || !g_stages || !u_np1) return fail(IRK_EINVAL, "null argument");
+  if (!h->ainv_ok) return fail(IRK_EINVAL, "DAE-type boundary conditions need an invertible Butcher matrix");
+  const int s = h->s;
+  const Level& L0 = h->lev[0];
+  const size_t nn = L0.nn, nb = nn * 8, sb = h->ne * 8;
+  const bool ia = (h->opt.splitting == IRK_SPLIT_IA);
+  const void *ud, *gd, *fd, *fsd;
+  void *outd, *kd;
+  bool outhost, khost;
+  TRY(dev_in(h, u_n, nb, 2, &ud));
+  TRY(dev_in(h, g_stages, sb, 7, &gd));
+  TRY(dev_in(h, f_space, nb, 3, &fd));
+  TRY(dev_in(h, f_stages, sb, 4, &fsd));
+  TRY(dev_out(h, u_np1, nb, 5, &outd, &outhost));
+  TRY(dev_out(h, stages_out, sb, 6, &kd, &khost));
+  if (!h->bnd) TRY(dalloc(&h->bnd, sb));  // not h->bnd: FGMRES restarts use it
+  // boundary unknowns of the solved system: k_B = A^{-1} (g - u_n) / dt (AI), w_B = (g - u_n) / dt (IA)
+  Mat4 bmix{};
+  for (int i = 0; i < s; ++i)
+    for (int j = 0; j < s; ++j) bmix.v[i * s + j] = (ia ? double(i == j) : h->Ainv[i * s + j]) / h->dt;
+  {
+    KScope k(h, IRK_K_OTHER, (double)nn * 8.0 * (1 + 2 * s), 2.0 * s * s * nn);
+    if (h->dim == 3)
+      launch_bc_stages3(s, h->st, L0.nx, bmix, (const double*)ud, (const double*)gd, h->bnd);
+    else
+      launch_bc_stages(s, h->st, L0.nx, bmix, (const double*)ud, (const double*)gd, h->bnd);
+  }
+  CK_LAUNCH();
+  // r = F - K u_n (u_n with its boundary values) - S x_B on the interior rows
+  Vec8 fc{};
+  for (int i = 0; i < s; ++i) fc.v[i] = f_coef ? f_coef[i] : 1.0;
+  {
+    KScope k(h, IRK_K_OTHER, (double)nn * (8 + 8 + 8.0 * kCoef2 + 8.0 * s + (fsd ? 8.0 * s : 0.0)),
+             n_int(L0.nx) * (17.0 + 2.0 * s));
+    if (h->dim == 3)
+      launch_rhs3(s, h->st, L0.nx, mass_stiff_classes(L0), (const double*)ud, (const double*)fd, fc,
+                  (const double*)fsd, h->rhs, 1);
+    else
+      launch_rhs(s, h->st, L0.nx, L0.cf_d, (const double*)ud, (const double*)fd, fc, (const double*)fsd, h->rhs,
+                 1);
+  }
+  CK_LAUNCH();
+  TRY(apply_operator(h, h->bnd, h->k, false));
+  {
+    KScope k(h, IRK_K_OTHER, 24.0 * h->ne, (double)h->ne);
+    launch_sub(h->st, h->rhs, h->rhs, h->k, h->ne);
+  }
+  CK_LAUNCH();
+  const int rc = solve(h, h->rhs, h->k, false, stats);
+  if (rc != IRK_OK && rc != IRK_ENOCONV) return rc;
+  {
+    KScope k(h, IRK_K_OTHER, 24.0 * h->ne, (double)h->ne);
+    launch_add(h->st, h->k, h->k, h->bnd, h->ne);
+  }
+  CK_LAUNCH();
+  Vec8 bdt{};
+  for (int i = 0; i < s; ++i) bdt.v[i] = h->dt * (ia ? h->bIA[i] : h->b[i]);
+  {
+    KScope k(h, IRK_K_OTHER, (double)nn * (16.0 + 8.0 * s), 2.0 * s * nn);
+    if (h->dim == 3)
+      launch_rk_update3(s, h->st, L0.nx, (const double*)ud, h->k, bdt, (double*)outd, 1);
+    else
+      launch_rk_update(s, h->st, L0.nx, (const double*)ud, h->k, bdt, (double*)outd, 1);
+  }
+  CK_LAUNCH();
+  if (kd && ia) {
     KScope kk(h, IRK_K_OTHER, 16.0 * h->ne, 2.0 * s * h->ne);
     launch_stage_mix(s, h->st, nn, ia_mixing(h, false), h->k, (double*)kd);
     CK_LAUNCH();

@@ -75,11 +75,14 @@ struct MG3 {
 // FP64 3D stage-operator kernels (op3d.cu); mc / kc: mass / stiffness class values in v[0].
 void launch_stage_apply3(int S, cudaStream_t st, int n, const Cls4& mk, const Mat4& mix, const double* x, double* y);
 void launch_rhs3(int S, cudaStream_t st, int n, const Cls4& mk, const double* u, const double* fsp,
-                 const Vec8& fcoef, const double* fst, double* r);
+                 const Vec8& fcoef, const double* fst, double* r, int raw_u = 0);
 void launch_block_apply3(cudaStream_t st, int n, const Cls4& mk, double sigma, const double* x, double* y);
 void launch_stage_apply3_ia(int S, cudaStream_t st, int n, const Cls4& mk, const Mat4& mixM, double dt,
                             const double* x, double* y);
-void launch_rk_update3(int S, cudaStream_t st, int n, const double* u, const double* k, const Vec8& bdt, double* out);
+void launch_rk_update3(int S, cudaStream_t st, int n, const double* u, const double* k, const Vec8& bdt, double* out,
+                       int all_nodes = 0);
+void launch_bc_stages3(int S, cudaStream_t st, int n, const Mat4& ainv_dt, const double* u, const double* g,
+                       double* kb);
 
 // FP64 stage-operator kernels (op2d.cu).
 void launch_stage_apply(int S, cudaStream_t st, int nx, const double* cf, double hm, const Mat4& mix, const double* x,
@@ -89,9 +92,11 @@ void launch_stage_apply_ia(int S, cudaStream_t st, int nx, const double* cf, dou
 void launch_stage_mix(int S, cudaStream_t st, size_t nodes, const Mat4& mix, const double* in, double* out);
 void launch_stage_scale(int S, cudaStream_t st, size_t nodes, const Vec8& scale, double* z);
 void launch_rhs(int S, cudaStream_t st, int nx, const double* cf, const double* u, const double* fsp,
-                const Vec8& fcoef, const double* fst, double* r);
+                const Vec8& fcoef, const double* fst, double* r, int raw_u = 0);
 void launch_rk_update(int S, cudaStream_t st, int nx, const double* u, const double* k, const Vec8& bdt,
-                      double* out);
+                      double* out, int all_nodes = 0);
+void launch_bc_stages(int S, cudaStream_t st, int nx, const Mat4& ainv_dt, const double* u, const double* g,
+                      double* kb);
 void launch_adjoint_lambda(int S, cudaStream_t st, int nx, const double* cf, const double* lam_np1, const double* mu,
                            double* lam_n);
 void launch_block_apply(cudaStream_t st, int nx, const double* cf, double hm, double sigma, const double* x,
@@ -124,6 +129,7 @@ void launch_cg_update_xr(cudaStream_t st, double* x, double* r, const double* p,
                          size_t n);
 void launch_cg_update_p(cudaStream_t st, double* p, const double* z, const double* beta, size_t n);
 void launch_sub(cudaStream_t st, double* out, const double* a, const double* b, size_t n);
+void launch_add(cudaStream_t st, double* out, const double* a, const double* b, size_t n);
 void launch_init_g(cudaStream_t st, double* g, int m1, const double* beta);
 
 }  // namespace irk

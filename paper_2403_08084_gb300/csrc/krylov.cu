@@ -222,6 +222,13 @@ __global__ void __launch_bounds__(kThreads) sub_kernel(double* __restrict__ out,
     out[e] = a[e] - b[e];
 }
 
+__global__ void __launch_bounds__(kThreads) add_kernel(double* __restrict__ out, const double* __restrict__ a,
+                                                       const double* __restrict__ b, size_t n) {
+  IRK_PDL_ENTRY;
+  for (size_t e = blockIdx.x * (size_t)kThreads + threadIdx.x; e < n; e += (size_t)gridDim.x * kThreads)
+    out[e] = a[e] + b[e];
+}
+
 __global__ void sqrt_scalar_kernel(const double* __restrict__ in, double* __restrict__ out) {
   IRK_PDL_ENTRY;
   if (threadIdx.x == 0 && blockIdx.x == 0) {
@@ -321,6 +328,9 @@ void launch_cg_update_xr(cudaStream_t st, double* x, double* r, const double* p,
 }
 void launch_cg_update_p(cudaStream_t st, double* p, const double* z, const double* beta, size_t n) {
   launch_k(cg_update_p_kernel, grid_for(n), kThreads, 0, st, p, z, beta, n);
+}
+void launch_add(cudaStream_t st, double* out, const double* a, const double* b, size_t n) {
+  launch_k(add_kernel, grid_for(n), kThreads, 0, st, out, a, b, n);
 }
 void launch_sqrt_scalar(cudaStream_t st, const double* in, double* out) { launch_k(sqrt_scalar_kernel, 1, 32, 0, st, in, out); }
 void launch_init_g(cudaStream_t st, double* g, int m1, const double* beta) { launch_k(init_g_kernel, 1, 128, 0, st, g, m1, beta); }

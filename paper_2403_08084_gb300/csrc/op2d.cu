@@ -119,10 +119,12 @@ __global__ void stage_scale_kernel(size_t nodes, Vec8 scale, double* __restrict_
 }
 
 // r_i = fcoef_i F^ + F_i - K u_n (Sec. 2 eq. rkheat moved to the right-hand side).
+// raw_u != 0: u's boundary entries are Dirichlet data and enter K u_n (DAE-type conditions).
 template <int S>
 __global__ void __launch_bounds__(BX* BY) rhs_kernel(int nx, const double* __restrict__ cf, const double* __restrict__ u,
                                                      const double* __restrict__ fsp, Vec8 fcoef,
-                                                     const double* __restrict__ fst, double* __restrict__ r) {
+                                                     const double* __restrict__ fst, double* __restrict__ r,
+                                                     int raw_u) {
   IRK_PDL_ENTRY;
   const int ix = blockIdx.x * BX + threadIdx.x;
   const int iy = blockIdx.y * BY + threadIdx.y;
@@ -133,7 +135,7 @@ __global__ void __launch_bounds__(BX* BY) rhs_kernel(int nx, const double* __res
     for (int i = 0; i < S; ++i) r[(size_t)p * S + i] = 0.0;
     return;
   }
-  const double ku = (u != nullptr) ? k_apply_masked(cf, u, ix, iy, nx) : 0.0;
+  const double ku = (u == nullptr) ? 0.0 : (raw_u ? k_apply<1, double>(cf, u, p, nx, 0) : k_apply_masked(cf, u, ix, iy, nx));
   const double f = (fsp != nullptr) ? fsp[p] : 0.0;
 #pragma unroll
   for (int i = 0; i < S; ++i) {
@@ -143,22 +145,45 @@ __global__ void __launch_bounds__(BX* BY) rhs_kernel(int nx, const double* __res
   }
 }
 
-// u_{n+1} = u_n + sum_i (dt b_i) k_i on interior nodes, 0 on the boundary.
+// u_{n+1} = u_n + sum_i (dt b_i) k_i on interior nodes, 0 on the boundary (all_nodes: everywhere).
 template <int S>
 __global__ void rk_update_kernel(int nx, const double* __restrict__ u, const double* __restrict__ k, Vec8 bdt,
-                                 double* __restrict__ out) {
+                                 double* __restrict__ out, int all_nodes) {
   IRK_PDL_ENTRY;
   const int ix = blockIdx.x * BX + threadIdx.x;
   const int iy = blockIdx.y * BY + threadIdx.y;
   if (ix >= nx || iy >= nx) return;
   const int p = ix + nx * iy;
   double v = 0.0;
-  if (interior2(ix, iy, nx)) {
+  if (all_nodes || interior2(ix, iy, nx)) {
     v = u[p];
 #pragma unroll
     for (int i = 0; i < S; ++i) v += bdt.v[i] * k[(size_t)p * S + i];
   }
   out[p] = v;
+}
+
+// Boundary stage values of DAE-type Dirichlet conditions (Sec. 2.1): on the boundary
+// sum_j a_ij k_j = (g_i - u_n) / dt, so k = Ainv_dt (g - u_n) with Ainv_dt = A^{-1} / dt; 0 inside.
+template <int S>
+__global__ void bc_stages_kernel(int nx, Mat4 ainv_dt, const double* __restrict__ u, const double* __restrict__ g,
+                                 double* __restrict__ kb) {
+  IRK_PDL_ENTRY;
+  const int ix = blockIdx.x * BX + threadIdx.x;
+  const int iy = blockIdx.y * BY + threadIdx.y;
+  if (ix >= nx || iy >= nx) return;
+  const int p = ix + nx * iy;
+  const bool bnd = !interior2(ix, iy, nx);
+  double d[S];
+#pragma unroll
+  for (int j = 0; j < S; ++j) d[j] = bnd ? g[(size_t)p * S + j] - u[p] : 0.0;
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    double acc = 0.0;
+#pragma unroll
+    for (int j = 0; j < S; ++j) acc += ainv_dt.v[i * S + j] * d[j];
+    kb[(size_t)p * S + i] = acc;
+  }
 }
 
 // lam_n = lam_{n+1} - K sum_i mu_i (interior), 0 on the boundary.
@@ -279,12 +304,16 @@ void launch_stage_scale(int S, cudaStream_t st, size_t nodes, const Vec8& scale,
   IRK_DISPATCH_S(S, launch_k(stage_scale_kernel<SS>, blocks, 256, 0, st, nodes, scale, z));
 }
 void launch_rhs(int S, cudaStream_t st, int nx, const double* cf, const double* u, const double* fsp,
-                const Vec8& fcoef, const double* fst, double* r) {
-  IRK_DISPATCH_S(S, launch_k(rhs_kernel<SS>, all_nodes_grid(nx), dim3(BX, BY), 0, st, nx, cf, u, fsp, fcoef, fst, r));
+                const Vec8& fcoef, const double* fst, double* r, int raw_u) {
+  IRK_DISPATCH_S(S, launch_k(rhs_kernel<SS>, all_nodes_grid(nx), dim3(BX, BY), 0, st, nx, cf, u, fsp, fcoef, fst, r, raw_u));
 }
 void launch_rk_update(int S, cudaStream_t st, int nx, const double* u, const double* k, const Vec8& bdt,
-                      double* out) {
-  IRK_DISPATCH_S(S, launch_k(rk_update_kernel<SS>, all_nodes_grid(nx), dim3(BX, BY), 0, st, nx, u, k, bdt, out));
+                      double* out, int all_nodes) {
+  IRK_DISPATCH_S(S, launch_k(rk_update_kernel<SS>, all_nodes_grid(nx), dim3(BX, BY), 0, st, nx, u, k, bdt, out, all_nodes));
+}
+void launch_bc_stages(int S, cudaStream_t st, int nx, const Mat4& ainv_dt, const double* u, const double* g,
+                      double* kb) {
+  IRK_DISPATCH_S(S, launch_k(bc_stages_kernel<SS>, all_nodes_grid(nx), dim3(BX, BY), 0, st, nx, ainv_dt, u, g, kb));
 }
 void launch_adjoint_lambda(int S, cudaStream_t st, int nx, const double* cf, const double* lam_np1, const double* mu,
                            double* lam_n) {

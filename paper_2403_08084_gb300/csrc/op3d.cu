@@ -96,7 +96,8 @@ __global__ void __launch_bounds__(AX* AY* AZ) stage_apply3_ia_kernel(int n, Cls4
 template <int S>
 __global__ void __launch_bounds__(AX* AY* AZ) rhs3_kernel(int n, Cls4 mk, const double* __restrict__ u,
                                                           const double* __restrict__ fsp, Vec8 fcoef,
-                                                          const double* __restrict__ fst, double* __restrict__ r) {
+                                                          const double* __restrict__ fst, double* __restrict__ r,
+                                                          int raw_u) {
   IRK_PDL_ENTRY;
   IRK_3D_ALL_INDEX
   if (!interior3(ix, iy, iz, n)) {
@@ -107,7 +108,10 @@ __global__ void __launch_bounds__(AX* AY* AZ) rhs3_kernel(int n, Cls4 mk, const 
   double ku = 0.0;
   if (u != nullptr) {
     double cs[4];
-    class_sums3_masked(u, ix, iy, iz, n, cs);
+    if (raw_u)
+      class_sums3<1, double>(u, p, n, 0, cs);
+    else
+      class_sums3_masked(u, ix, iy, iz, n, cs);
     ku = class_apply<double>(mk.v[1], cs);
   }
   const double f = (fsp != nullptr) ? fsp[p] : 0.0;
@@ -135,16 +139,34 @@ __global__ void __launch_bounds__(AX* AY* AZ) block_apply3_kernel(int n, Cls4 mk
 
 template <int S>
 __global__ void rk_update3_kernel(int n, const double* __restrict__ u, const double* __restrict__ k, Vec8 bdt,
-                                  double* __restrict__ out) {
+                                  double* __restrict__ out, int all_nodes) {
   IRK_PDL_ENTRY;
   IRK_3D_ALL_INDEX
   double v = 0.0;
-  if (interior3(ix, iy, iz, n)) {
+  if (all_nodes || interior3(ix, iy, iz, n)) {
     v = u[p];
 #pragma unroll
     for (int i = 0; i < S; ++i) v += bdt.v[i] * k[(size_t)p * S + i];
   }
   out[p] = v;
+}
+
+template <int S>
+__global__ void bc_stages3_kernel(int n, Mat4 ainv_dt, const double* __restrict__ u, const double* __restrict__ g,
+                                  double* __restrict__ kb) {
+  IRK_PDL_ENTRY;
+  IRK_3D_ALL_INDEX
+  const bool bnd = !interior3(ix, iy, iz, n);
+  double d[S];
+#pragma unroll
+  for (int j = 0; j < S; ++j) d[j] = bnd ? g[(size_t)p * S + j] - u[p] : 0.0;
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    double acc = 0.0;
+#pragma unroll
+    for (int j = 0; j < S; ++j) acc += ainv_dt.v[i * S + j] * d[j];
+    kb[(size_t)p * S + i] = acc;
+  }
 }
 
 #define IRK_DISPATCH_S(S, ...)                                \
@@ -164,16 +186,23 @@ void launch_stage_apply3_ia(int S, cudaStream_t st, int n, const Cls4& mk, const
   IRK_DISPATCH_S(S, launch_k(stage_apply3_ia_kernel<SS>, all_nodes_grid3(n), dim3(AX, AY, AZ), 0, st, n, mk, mixM, dt, x, y));
 }
 void launch_rhs3(int S, cudaStream_t st, int n, const Cls4& mk, const double* u, const double* fsp,
-                 const Vec8& fcoef, const double* fst, double* r) {
-  IRK_DISPATCH_S(S, launch_k(rhs3_kernel<SS>, all_nodes_grid3(n), dim3(AX, AY, AZ), 0, st, n, mk, u, fsp, fcoef, fst, r));
+                 const Vec8& fcoef, const double* fst, double* r, int raw_u) {
+  IRK_DISPATCH_S(S, launch_k(rhs3_kernel<SS>, all_nodes_grid3(n), dim3(AX, AY, AZ), 0, st, n, mk, u, fsp, fcoef, fst, r,
+                             raw_u));
 }
 void launch_block_apply3(cudaStream_t st, int n, const Cls4& mk, double sigma, const double* x, double* y) {
   const int m = n - 2;
   dim3 g((m + AX - 1) / AX, (m + AY - 1) / AY, (m + AZ - 1) / AZ);
   launch_k(block_apply3_kernel, g, dim3(AX, AY, AZ), 0, st, n, mk, sigma, x, y);
 }
-void launch_rk_update3(int S, cudaStream_t st, int n, const double* u, const double* k, const Vec8& bdt, double* out) {
-  IRK_DISPATCH_S(S, launch_k(rk_update3_kernel<SS>, all_nodes_grid3(n), dim3(AX, AY, AZ), 0, st, n, u, k, bdt, out));
+void launch_rk_update3(int S, cudaStream_t st, int n, const double* u, const double* k, const Vec8& bdt, double* out,
+                       int all_nodes) {
+  IRK_DISPATCH_S(S, launch_k(rk_update3_kernel<SS>, all_nodes_grid3(n), dim3(AX, AY, AZ), 0, st, n, u, k, bdt, out,
+                             all_nodes));
+}
+void launch_bc_stages3(int S, cudaStream_t st, int n, const Mat4& ainv_dt, const double* u, const double* g,
+                       double* kb) {
+  IRK_DISPATCH_S(S, launch_k(bc_stages3_kernel<SS>, all_nodes_grid3(n), dim3(AX, AY, AZ), 0, st, n, ainv_dt, u, g, kb));
 }
 
 }  // namespace irk

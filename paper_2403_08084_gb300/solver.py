@@ -107,6 +107,22 @@ class Solver:
 
     step = irk_step
 
+    def irk_step_dirichlet(self, u_n, g_stages, u_np1, *, f_space=None, f_coef=None, f_stages=None,
+                           stages_out=None, allow_noconv: bool = False) -> dict:
+        """One step with DAE-type Dirichlet data (Sec. 2.1): g_stages[p * s + i] = g(t_n + c_i dt) at
+        boundary node p; u_n's boundary entries are the current boundary values."""
+        nn, ns = self.n_nodes, self.n_nodes * self.s
+        coef = L.dbl_array(f_coef) if f_coef is not None else None
+        st = L.irk_stats()
+        rc = L.lib.irk_step_dirichlet(self._h, L.ptr(u_n, count=nn), L.ptr(g_stages, count=ns),
+                                      L.ptr(f_space, count=nn),
+                                      C.cast(coef, C.c_void_p) if coef is not None else None,
+                                      L.ptr(f_stages, count=ns), L.ptr(u_np1, count=nn),
+                                      L.ptr(stages_out, count=ns), C.byref(st))
+        return self._stats(st, rc, allow_noconv)
+
+    step_dirichlet = irk_step_dirichlet
+
     def irk_solve(self, r, k, allow_noconv: bool = False) -> dict:
         ns = self.n_nodes * self.s
         st = L.irk_stats()
