@@ -36,6 +36,8 @@ METRIC = "time-steps/s and DOF·stage/s at fixed L2 error; stencil/V-cycle GB/s 
 # FP64 arithmetic peak: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz (matches the nominal 1.25 TFLOP/s)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP64_CLASSES = ("stage_apply", "multidot", "axpy")  # always FP64
+SPLIT_LABEL = {"ia": "IA: (A^-1 (x) M + dt I (x) K) w = r, k = (A^-1 (x) I) w",
+               "ai": "AI: (I (x) M + dt A (x) K) k = r"}
 
 
 def parse():
@@ -48,11 +50,16 @@ def parse():
     ap.add_argument("--precond", default="lower", choices=["diag", "lower", "upper", "rana_ld"])
     ap.add_argument("--vcycle", default=None, choices=["fp64", "fp32", "bf16"])
     ap.add_argument("--orth", default="cgs2", choices=["cgs2", "dgks"])
+    ap.add_argument("--splitting", default="ia", choices=["ia", "ai"],
+                    help="form of the stage system: IA (Sec. 3, eq. block_struct_IA, the paper's heat form) or AI")
     ap.add_argument("--tableau", default=None, help="override, e.g. GaussLegendre:4 or Alexander:3")
     ap.add_argument("--restart", type=int, default=50, help="FGMRES restart length (Krylov basis size)")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--study", default=None, choices=["long-horizon"],
+                    help="instead of the benchmark line: time-to-solution at equal final L2 error on the "
+                         "2048^2 long-horizon workload (SDIRK vs RadauIIA, FP64 vs FP32 V-cycles)")
     return ap.parse_args()
 
 
@@ -212,7 +219,7 @@ def gpu_arm(args, rank, world):
     if args.tableau:
         name, _, s_ = args.tableau.partition(":")
         tab_override = (name, int(s_ or 3))
-    sv, tab = make_solver(wl, precond, vcycle, args.orth, tab_override)
+    sv, tab = make_solver(wl, precond, vcycle, args.orth, tab_override, args.splitting)
     nn = (wl.N + 1) ** wl.dim
     u0 = torch.from_numpy(W.sine_initial(wl.dim, wl.N)).cuda()
     f = torch.from_numpy(W.sine_load_space(wl.dim, wl.N)).cuda()
@@ -303,7 +310,8 @@ def gpu_arm(args, rank, world):
         "data": "synthetic",
         "config": {"workload": wl.name, "mesh": "x".join([str(wl.N)] * wl.dim) + " Q1", "dofs": dof, "stages": s,
                    "tableau": tab_label(tab), "dt": wl.dt, "kappa": "lognormal sigma=0.5 seed %s" % wl.kappa_seed,
-                   "precond": precond, "vcycle": vcycle, "levels": wl.levels, "rtol": wl.rtol, "orth": args.orth,
+                   "precond": precond, "splitting": SPLIT_LABEL[args.splitting], "vcycle": vcycle,
+                   "levels": wl.levels, "rtol": wl.rtol, "orth": args.orth,
                    "restart": args.restart,
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                    "l2_policy": "working set > L2: Krylov basis of ~its x 25 MB stage vectors per step"},
@@ -322,7 +330,7 @@ def gpu_arm(args, rank, world):
     if rank == 0 and not args.no_variants:
         out["variants"] = variants_leg(wl, u5.cpu().numpy(), args, vcycle, precond)
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline_leg(wl)
+        out["cpu_baseline"] = cpu_baseline_leg(wl, precond, args.splitting if precond != "upper" else "ai")
     out["final_u_norm"] = float(torch.linalg.vector_norm(u_final).item())
     return out
 
@@ -356,28 +364,31 @@ def e2e_leg(sv, tab, wl, u0, args):
 
 
 def variants_leg(wl, u5_ref, args, vcycle0, precond0):
-    """Other preconditioners / V-cycle precisions / tableaux on the same workload (5 steps each)."""
+    """Other forms / preconditioners / V-cycle precisions / tableaux on the same workload (5 steps each)."""
     import torch
 
     res = {}
     nsteps = min(5, args.steps)
+    alex = ("Alexander", 3)
     if wl.dim == 2:
-        runs = [("diag", "fp64", "cgs2", None), ("rana_ld", "fp64", "cgs2", None), ("lower", "fp64", "dgks", None),
-                ("lower", "fp32", "cgs2", None), ("lower", "bf16", "cgs2", None), ("diag", "fp32", "cgs2", None),
-                ("rana_ld", "fp32", "cgs2", None), ("lower", "fp64", "cgs2", ("Alexander", 3)),
-                ("lower", "fp32", "cgs2", ("Alexander", 3)), ("lower", "fp32", "cgs2", "ia"),
-                ("rana_ld", "fp32", "cgs2", "ia"), ("rana_ld", "fp64", "cgs2", "ia")]
+        runs = [("lower", "fp64", "cgs2", None, "ia"), ("diag", "fp64", "cgs2", None, "ia"),
+                ("rana_ld", "fp64", "cgs2", None, "ia"), ("lower", "fp32", "cgs2", None, "ia"),
+                ("lower", "bf16", "cgs2", None, "ia"), ("rana_ld", "fp32", "cgs2", None, "ia"),
+                ("lower", "fp64", "dgks", None, "ia"),
+                ("lower", "fp64", "cgs2", None, "ai"), ("diag", "fp64", "cgs2", None, "ai"),
+                ("rana_ld", "fp64", "cgs2", None, "ai"), ("lower", "fp32", "cgs2", None, "ai"),
+                ("lower", "bf16", "cgs2", None, "ai"),
+                ("lower", "fp64", "cgs2", alex, "ai"), ("lower", "fp32", "cgs2", alex, "ai")]
     else:
-        runs = [("lower", "fp64", "cgs2", None), ("lower", "fp32", "cgs2", None), ("lower", "bf16", "cgs2", None),
-                ("rana_ld", "fp32", "cgs2", None), ("lower", "fp32", "cgs2", ("GaussLegendre", 2)),
-                ("lower", "fp32", "cgs2", ("GaussLegendre", 4)), ("lower", "bf16", "cgs2", ("GaussLegendre", 4)),
-                ("rana_ld", "fp32", "cgs2", "ia")]
-    for precond, vcycle, orth, tabo in runs:
-        if (precond, vcycle, orth, tabo) == (precond0, vcycle0, args.orth, None):
+        runs = [("lower", "fp64", "cgs2", None, "ia"), ("lower", "fp32", "cgs2", None, "ia"),
+                ("lower", "bf16", "cgs2", None, "ia"), ("rana_ld", "fp32", "cgs2", None, "ia"),
+                ("lower", "fp32", "cgs2", None, "ai"), ("lower", "fp64", "cgs2", None, "ai"),
+                ("lower", "fp32", "cgs2", ("GaussLegendre", 2), "ia"),
+                ("lower", "fp32", "cgs2", ("GaussLegendre", 4), "ia"),
+                ("lower", "bf16", "cgs2", ("GaussLegendre", 4), "ia")]
+    for precond, vcycle, orth, tabo, split in runs:
+        if (precond, vcycle, orth, tabo, split) == (precond0, vcycle0, args.orth, None, args.splitting):
             continue
-        split = "ia" if tabo == "ia" else "ai"
-        if tabo == "ia":
-            tabo = None
         sv, tab = make_solver(wl, precond, vcycle, orth, tabo, split)
         u0 = torch.from_numpy(W.sine_initial(wl.dim, wl.N)).cuda()
         f = torch.from_numpy(W.sine_load_space(wl.dim, wl.N)).cuda()
@@ -390,7 +401,7 @@ def variants_leg(wl, u5_ref, args, vcycle0, precond0):
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         un = u.cpu().numpy()
-        key = f"{precond}/{vcycle}/{orth}" + (f"/{tab.name}" if tabo else "") + ("/IA" if split == "ia" else "")
+        key = f"{split.upper()}/{precond}/{vcycle}/{orth}" + (f"/{tab.name}" if tabo else "")
         entry = {"steps_per_s": round(nsteps / dt, 4), "ms_per_step": round(dt * 1e3 / nsteps, 3),
                  "krylov_its_per_step": round(sum(s["fgmres_its"] for s in stats) / nsteps, 2)}
         if tabo is None:
@@ -402,64 +413,67 @@ def variants_leg(wl, u5_ref, args, vcycle0, precond0):
     return res
 
 
-def cpu_baseline_leg(wl):
-    """One time step of the same workload through the oracle's FGMRES + V-cycle restatement
-    (3D: on a 64^3 sample, scaled to the full DOF count)."""
+def oracle_stepper(wl, N, levels, kind, split):
+    """The oracle's FGMRES + sparse V-cycle restatement of one RK step (AI or IA form) on an N^dim mesh.
+    Returns (one(u, n) -> (u_next, its), u0)."""
     from oracle import fem, krylov, mg, rk
     from oracle import tableaux as OT
 
-    N = wl.N if wl.dim == 2 else min(wl.N, 64)
-    levels = wl.levels - int(round(np.log2(wl.N // N)))
     kap = W.lognormal_kappa(wl.dim, N, 0.5, wl.kappa_seed) if wl.kappa_seed is not None else None
     d = fem.Discretisation(wl.dim, N, kap)
     h = mg.Hierarchy(d, levels)
     ot = OT.by_name(wl.tableau, wl.s)
-    solves = [mg.VCycle(h, wl.dt * ot.A[i, i]) for i in range(wl.s)]
-    S = rk.kronecker_operator(d.M, d.K, ot.A, wl.dt)
-    P = krylov.BlockPreconditioner("lower", ot.A, d.K, wl.dt, solves)
-    u0 = d.to_interior(W.sine_initial(wl.dim, N))
+    Ap = krylov.rana_ld(ot.A) if kind == "rana_ld" else ot.A
+    if split == "ia":
+        T = np.diag(np.diag(Ap)) if kind == "diag" else np.tril(Ap)
+        solves = [mg.VCycle(h, wl.dt * T[i, i]) for i in range(wl.s)]
+        S = krylov.ia_operator(d.M, d.K, ot.A, wl.dt)
+        P = krylov.IABlockPreconditioner(T, d.M, wl.dt, solves, diagonal_only=(kind == "diag"))
+        Ainv = np.linalg.inv(ot.A)
+    else:
+        solves = [mg.VCycle(h, wl.dt * Ap[i, i]) for i in range(wl.s)]
+        S = rk.kronecker_operator(d.M, d.K, ot.A, wl.dt)
+        P = krylov.BlockPreconditioner("lower" if kind == "rana_ld" else kind, Ap, d.K, wl.dt, solves)
+        Ainv = np.eye(wl.s)
     Fs = d.to_interior(W.sine_load_space(wl.dim, N))
+
+    def one(u, n):
+        r = np.stack([W.sine_load_time(wl.dim, (n + c) * wl.dt) * Fs for c in ot.c]) - (d.K @ u)[None, :]
+        w, its, _, _ = krylov.fgmres(lambda v: S @ v, r.reshape(-1), P, rtol=wl.rtol)
+        k = Ainv @ w.reshape(wl.s, -1)
+        return u + wl.dt * (ot.b @ k), its
+
+    return one, d.to_interior(W.sine_initial(wl.dim, N))
+
+
+def cpu_baseline_leg(wl, precond, split):
+    """One time step of the same workload through the oracle's FGMRES + V-cycle restatement
+    (3D: on a 64^3 sample, scaled to the full DOF count)."""
+    N = wl.N if wl.dim == 2 else min(wl.N, 64)
+    levels = wl.levels - int(round(np.log2(wl.N // N)))
+    one, u0 = oracle_stepper(wl, N, levels, precond, split)
     t0 = time.perf_counter()
-    r = np.stack([W.sine_load_time(wl.dim, c * wl.dt) * Fs for c in ot.c]) - (d.K @ u0)[None, :]
-    k, its, _, _ = krylov.fgmres(lambda v: S @ v, r.reshape(-1), P, rtol=wl.rtol)
-    u1 = u0 + wl.dt * (ot.b @ k.reshape(wl.s, -1))
+    u1, its = one(u0, 0)
     dt = time.perf_counter() - t0
     scale = ((N + 1) / (wl.N + 1)) ** wl.dim
     where = "at full size" if N == wl.N else f"on a {N}^{wl.dim} sample, steps/s scaled by the DOF ratio {scale:.4f}"
     return {"value": round(scale / dt, 6), "unit": "time-steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"1 time step of {wl.name} {where} (oracle FGMRES + sparse V-cycle, P_L, FP64; "
-                      f"{its} its; setup excluded)", "seconds": round(dt, 2), "u_norm": float(np.linalg.norm(u1))}
+            "sample": f"1 time step of {wl.name} {where} (oracle FGMRES + sparse V-cycle, {split.upper()} form, "
+                      f"{precond}, FP64; {its} its; setup excluded)", "seconds": round(dt, 2),
+            "u_norm": float(np.linalg.norm(u1))}
 
 
 # ----------------------------------------------------------------------------
 # reference arm: the FP64 CPU oracle
 # ----------------------------------------------------------------------------
 def reference_arm(args):
-    from oracle import fem, krylov, mg, rk
-    from oracle import tableaux as OT
-
     wl = W.WORKLOADS[args.workload]
     # bounded sample: the same workload on a mesh with 1/4 of the nodes (one fewer level), so that
     # every step is a few seconds of CPU work; throughput is scaled to the full DOF count
     Ns = max(wl.N // 2, 32) if wl.dim == 2 else min(wl.N, 64)
     lv = max(1, wl.levels - int(round(np.log2(wl.N // Ns))))
-    kap = W.lognormal_kappa(wl.dim, Ns, 0.5, wl.kappa_seed) if wl.kappa_seed is not None else None
-    d = fem.Discretisation(wl.dim, Ns, kap)
-    h = mg.Hierarchy(d, lv)
-    ot = OT.by_name(wl.tableau, wl.s)
-    kind, Ap = args.precond, ot.A
-    if kind == "rana_ld":
-        kind, Ap = "lower", krylov.rana_ld(ot.A)
-    solves = [mg.VCycle(h, wl.dt * Ap[i, i]) for i in range(wl.s)]
-    S = rk.kronecker_operator(d.M, d.K, ot.A, wl.dt)
-    P = krylov.BlockPreconditioner(kind, Ap, d.K, wl.dt, solves)
-    u0 = d.to_interior(W.sine_initial(wl.dim, Ns))
-    Fs = d.to_interior(W.sine_load_space(wl.dim, Ns))
-
-    def one(u, n):
-        r = np.stack([W.sine_load_time(wl.dim, (n + c) * wl.dt) * Fs for c in ot.c]) - (d.K @ u)[None, :]
-        k, its, _, _ = krylov.fgmres(lambda v: S @ v, r.reshape(-1), P, rtol=wl.rtol)
-        return u + wl.dt * (ot.b @ k.reshape(wl.s, -1)), its
+    split = args.splitting if args.precond != "upper" else "ai"
+    one, u0 = oracle_stepper(wl, Ns, lv, args.precond, split)
 
     u = u0.copy()
     for n in range(args.warmup):
@@ -474,7 +488,7 @@ def reference_arm(args):
     scale = ((Ns + 1) ** wl.dim) / ((wl.N + 1) ** wl.dim)
     value = args.steps / dt * scale
     sample = (f"each step: one RK step of {wl.name} on a {Ns}^{wl.dim} mesh ({lv} levels), oracle FGMRES + sparse "
-              f"V-cycle, P_{args.precond[0].upper()}, FP64; steps/s scaled by the DOF ratio {scale:.4f}")
+              f"V-cycle, {split.upper()} form, {args.precond}, FP64; steps/s scaled by the DOF ratio {scale:.4f}")
     return {
         "impl": "reference",
         "metric": METRIC,
@@ -490,12 +504,103 @@ def reference_arm(args):
         "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": wl.name, "mesh": "x".join([str(wl.N)] * wl.dim) + " Q1", "precond": args.precond,
-                   "sample_mesh": Ns},
+                   "splitting": SPLIT_LABEL[split], "sample_mesh": Ns},
         "fgmres_its_per_step": round(sum(its) / len(its), 2),
         "cpu_baseline": {"value": round(value, 6), "unit": "time-steps/s", "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": round(value, 6), "unit": "time-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
+
+
+# ----------------------------------------------------------------------------
+# long-horizon study: time-to-solution at equal final L2 error
+# ----------------------------------------------------------------------------
+def study_long_horizon(args):
+    """2048^2 Q1, lognormal kappa (seed 0), integrated to T = 1 with Alexander's 3-stage SDIRK (sequential
+    per-stage V-cycle-preconditioned CG) and RadauIIA(3) (FGMRES, P_L, IA and AI forms), each with FP64 and
+    FP32 V-cycles,
+    over a sweep of step sizes.  The error is ||u_N - u_ref||_M / ||u_ref||_M against RadauIIA(4) at
+    dt = 1/200 (order 7; its own error is estimated from the same scheme at dt = 1/100).  Time is the
+    wall time of the step loop (setup reported apart); at a target error, each form's time is
+    interpolated log-log between the two sweep points that bracket it."""
+    import torch
+
+    from paper_2403_08084_gb300 import Solver
+    from paper_2403_08084_gb300 import tableaux as PT
+
+    wl = W.WORKLOADS["heat2d-2048-long"]
+    N, T = wl.N, 1.0
+    kap = W.lognormal_kappa(2, N, 0.5, wl.kappa_seed)
+    u0 = torch.from_numpy(W.sine_initial(2, N)).cuda()
+    f = torch.from_numpy(W.sine_load_space(2, N)).cuda()
+
+    def integrate(tab, nsteps, vcycle, solver, rtol, split="ai", precond="lower"):
+        dt = T / nsteps
+        t0 = time.perf_counter()
+        sv = Solver(N, tab, dt, kappa=kap, levels=wl.levels, precond=precond, vcycle=vcycle, rtol=rtol,
+                    solver=solver, restart=RESTART, maxit=2000, splitting=split)
+        torch.cuda.synchronize()
+        setup = time.perf_counter() - t0
+        u = u0.clone()
+        for n in range(min(2, nsteps)):  # warm-up: CUDA-graph capture of the first iterations
+            sv.step(u, u, f_space=f, f_coef=[W.sine_load_time(2, (n + c) * dt) for c in tab.c])
+        u.copy_(u0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        its = 0
+        for n in range(nsteps):
+            its += sv.step(u, u, f_space=f, f_coef=[W.sine_load_time(2, (n + c) * dt) for c in tab.c])["fgmres_its"]
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        sv.close()
+        return u, wall, setup, its / nsteps
+
+    mass = Solver(N, PT.radau_iia(1), 1.0, levels=wl.levels)
+
+    def mnorm(x):
+        y = torch.empty_like(x)
+        mass.apply_mass(x, y)
+        return math.sqrt(float(torch.dot(x, y).item()))
+
+    ref, ref_wall, _, ref_its = integrate(PT.radau_iia(4), 200, "fp64", "fgmres", 1e-13, "ia")
+    ref2, _, _, _ = integrate(PT.radau_iia(4), 100, "fp64", "fgmres", 1e-13, "ia")
+    ref_norm = mnorm(ref)
+    ref_err_est = mnorm(ref2 - ref) / ref_norm / (2**7 - 1)
+
+    forms = [("RadauIIA(3) IA", PT.radau_iia(3), "fgmres", (2, 4, 8, 16, 32, 64), "ia"),
+             ("RadauIIA(3) AI", PT.radau_iia(3), "fgmres", (2, 4, 8, 16, 32, 64), "ai"),
+             ("Alexander SDIRK", PT.alexander(), "dirk_cg", (10, 25, 50, 100, 200, 400), "ai")]
+    rows = []
+    for label, tab, solver, sweep, split in forms:
+        for vcycle in ("fp64", "fp32"):
+            for nsteps in sweep:
+                u, wall, setup, its = integrate(tab, nsteps, vcycle, solver, wl.rtol, split)
+                rows.append({"scheme": label, "vcycle": vcycle, "dt": 1 / nsteps, "steps": nsteps,
+                             "loop_s": round(wall, 4), "setup_s": round(setup, 3), "its_per_step": round(its, 2),
+                             "rel_l2_err": mnorm(u - ref) / ref_norm})
+    mass.close()
+
+    def time_at(label, vcycle, target):
+        pts = sorted((r["rel_l2_err"], r["loop_s"]) for r in rows if r["scheme"] == label and r["vcycle"] == vcycle)
+        for (e_lo, t_lo), (e_hi, t_hi) in zip(pts, pts[1:]):
+            if e_lo <= target <= e_hi:
+                w = (math.log(target) - math.log(e_lo)) / (math.log(e_hi) - math.log(e_lo))
+                return round(math.exp((1 - w) * math.log(t_lo) + w * math.log(t_hi)), 4)
+        return None
+
+    matched = []
+    for target in (1e-4, 1e-5, 1e-6, 1e-7, 1e-8, 1e-9):
+        entry = {"target_rel_l2_err": target}
+        for label, _, _, _, _ in forms:
+            for vcycle in ("fp64", "fp32"):
+                entry[f"{label} {vcycle}"] = time_at(label, vcycle, target)
+        matched.append(entry)
+    return {"study": "long-horizon time-to-solution at equal final L2 error",
+            "workload": wl.name, "mesh": f"{N}x{N} Q1", "dofs": (N + 1) ** 2, "T": T, "rtol": wl.rtol,
+            "levels": wl.levels, "precond": "P_L (RadauIIA, IA and AI forms); per-stage V(2,2)-PCG (SDIRK)",
+            "reference": {"scheme": "RadauIIA(4), IA form", "dt": 1 / 200, "rtol": 1e-13, "loop_s": round(ref_wall, 2),
+                          "its_per_step": round(ref_its, 2), "est_rel_err": ref_err_est},
+            "runs": rows, "loop_seconds_at_matched_error": matched}
 
 
 def main():
@@ -513,6 +618,10 @@ def main():
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    if args.study:
+        if rank == 0:
+            print(json.dumps(study_long_horizon(args)))
+        return 0
     if world > 1:
         import torch.distributed as td
 
