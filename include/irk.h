@@ -59,6 +59,10 @@ extern "C" {
 #define IRK_ORTH_CGS2 0 /* classical Gram-Schmidt, always two passes                       */
 #define IRK_ORTH_DGKS 1 /* classical Gram-Schmidt, second pass only when ||w'|| < ||w||/sqrt(2)
                            (Daniel-Gragg-Kaufman-Stewart test), norm by Pythagoras otherwise   */
+#define IRK_ORTH_CGS 2  /* classical Gram-Schmidt, one pass (the GMRES default of the PETSc
+                           stack the paper used); the norm of the new vector is reduced
+                           directly, and at convergence the true residual ||r - S x|| is
+                           recomputed and iteration continues if it misses rtol              */
 
 /* outer solver */
 #define IRK_SOLVER_FGMRES 0  /* FGMRES on the whole stage system (any tableau)                    */

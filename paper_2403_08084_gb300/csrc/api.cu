@@ -348,7 +348,8 @@ int validate(const irk_mesh* mesh, const irk_tableau* tab, double dt, const irk_
   if (!(opt->rtol > 0.0 && opt->rtol < 1.0)) return fail(IRK_EINVAL, "rtol = %g not in (0, 1)", opt->rtol);
   if (opt->restart < 1 || opt->restart > 100) return fail(IRK_EINVAL, "restart = %d not in [1, 100]", opt->restart);
   if (opt->maxit < 1) return fail(IRK_EINVAL, "maxit = %d < 1", opt->maxit);
-  if (opt->orth != IRK_ORTH_CGS2 && opt->orth != IRK_ORTH_DGKS) return fail(IRK_EINVAL, "bad orth %d", opt->orth);
+  if (opt->orth != IRK_ORTH_CGS2 && opt->orth != IRK_ORTH_DGKS && opt->orth != IRK_ORTH_CGS)
+    return fail(IRK_EINVAL, "bad orth %d", opt->orth);
   if (opt->solver != IRK_SOLVER_FGMRES && opt->solver != IRK_SOLVER_DIRK_CG)
     return fail(IRK_EINVAL, "bad solver %d", opt->solver);
   if (opt->splitting != IRK_SPLIT_AI && opt->splitting != IRK_SPLIT_IA)
@@ -571,11 +572,12 @@ int create(irk_handle** out, const irk_mesh* mesh, const irk_tableau* tab, doubl
       (r = dalloc(&h->H, (m + 1) * m * 8)) || (r = dalloc(&h->cs, m * 8)) || (r = dalloc(&h->sn, m * 8)) ||
       (r = dalloc(&h->g, (m + 1) * 8)) || (r = dalloc(&h->y, m * 8)) || (r = dalloc(&h->h1, (m + 1) * 8)) ||
       (r = dalloc(&h->h2, (m + 1) * 8)) ||
-      (r = dalloc(&h->partial, (m + 1) * (size_t)krylov_partial_blocks() * 8)) || (r = dalloc(&h->scal, 16 * 8)) || (r = dalloc(&h->iflag, 16 * sizeof(int))) ||
+      (r = dalloc(&h->partial, (m + 1) * (size_t)krylov_partial_blocks() * 8)) || (r = dalloc(&h->scal, 16 * 8)) ||
+      (r = dalloc(&h->iflag, 16 * sizeof(int))) ||
       (r = dalloc(&h->rhs, ne * 8)) || (r = dalloc(&h->k, ne * 8)) || (r = dalloc(&h->tmp, ne * 8)))
     return bail(r);
   if (cudaMemsetAsync(h->V, 0, (m + 1) * ne * 8, h->st) || cudaMemsetAsync(h->Z, 0, m * ne * 8, h->st) ||
-      cudaMemsetAsync(h->H, 0, (m + 1) * m * 8, h->st))
+      cudaMemsetAsync(h->H, 0, (m + 1) * m * 8, h->st) || cudaMemsetAsync(h->h2, 0, (m + 1) * 8, h->st))
     return bail(fail(IRK_ECUDA, "cudaMemsetAsync failed"));
   if (cudaMallocHost((void**)&h->pinned, 8 * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
@@ -694,11 +696,28 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2) {
       MG::jacobi(S, st, Lv.nx, cf, Lv.hm, sig, dinv, s, xin, b, xout);
     }
   };
+  // 2D coarse levels under V(2, 2): one fused kernel per leg (mg2d_legs.cuh) instead of six launches
+  auto fused_leg = [&](int l) { return !d3 && l >= 1 && nu1 == 2 && nu2 == 2; };
+  auto rec_of = [&](const Level& Lv) {
+    const C* rec = P::rec(Lv);
+    return rec ? rec + (size_t)st0 * Lv.nn * kCoef2 : nullptr;
+  };
   for (int l = 0; l < L - 1; ++l) {
     Level& Lv = h->lev[l];
     Level& Lc = h->lev[l + 1];
     const C* cf = d3 ? nullptr : P::cf(Lv);
     const C* dinv = d3 ? nullptr : P::dinv(Lv) + st0;
+    if (fused_leg(l)) {
+      const double n = interior(Lv), nc = interior(Lc);
+      const bool rec = P::rec(Lv) != nullptr;
+      KScope k(h, IRK_K_MG_COARSE, n * S * (2 * p + c) + n * kCoef2 * c * (rec ? S : 1) + nc * S * p,
+               n * S * (rec ? 42.0 : 66.0));
+      MG::down_leg(S, st, Lv.nx, cf, Lv.hm, sig, rec_of(Lv), Lv.nn * kCoef2, dinv, s, bl, (T*)Lv.xa, Lc.nx,
+                   (T*)Lc.b);
+      cur[l] = (T*)Lv.xa;
+      bl = (const T*)Lc.b;
+      continue;
+    }
     // choose the two buffers so that the last of the nu1 + nu2 sweeps lands in `last`
     T* last = (l == 0 && x0) ? x0 : (T*)Lv.xa;
     T* other = (l == 0 && x0) ? (T*)Lv.xa : (T*)Lv.xb;
@@ -785,7 +804,7 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2) {
     if (d3)
       MG3T::coarse_solve(S, st, h->nint, binv, h->cmap, bl, xc);
     else
-      MG::coarse_solve(S, st, h->nint, binv, h->cmap, bl, xc);
+      MG::coarse_solve(S, st, Lc.nx, binv, bl, xc);
     cur[L - 1] = xc;
   }
   for (int l = L - 2; l >= 0; --l) {
@@ -795,6 +814,16 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2) {
     const C* dinv = d3 ? nullptr : P::dinv(Lv) + st0;
     const T* bfine = (l == 0) ? b0 : (const T*)Lv.b;
     const double nf = interior(Lv), nc = interior(Lc);
+    if (fused_leg(l)) {
+      T* xo = (cur[l] == (T*)Lv.xa) ? (T*)Lv.xb : (T*)Lv.xa;
+      const bool rec = P::rec(Lv) != nullptr;
+      KScope k(h, IRK_K_MG_COARSE, nf * S * (4 * p + c) + nf * kCoef2 * c * (rec ? S : 1) + nc * S * p,
+               nf * S * (rec ? 45.0 : 69.0));
+      MG::up_leg(S, st, Lv.nx, cf, Lv.hm, sig, rec_of(Lv), Lv.nn * kCoef2, dinv, s, cur[l], bfine, Lc.nx,
+                 cur[l + 1], xo);
+      cur[l] = xo;
+      continue;
+    }
     {
       KScope k(h, cls(Lv, IRK_K_PROLONG), (nc + 2 * nf) * S * p, (d3 ? 9.0 : 5.0) * nf * S);
       if (d3)
@@ -1008,8 +1037,19 @@ int arnoldi_step(irk_handle* h, int j, bool transpose) {
     // slot of V_{j+1}), so it returns ||w'||^2; the Givens kernel takes ||w''|| by
     // Pythagoras and the second update normalises in the same sweep.
     multidot(h, h->V, ne, j + 1, w, h->h1);
-    multi_axpy(h, w, h->V, ne, j + 1, h->h1, -1.0);
-    multidot(h, h->V, ne, j + 2, w, h->h2);
+    if (j + 1 <= krylov_axpy_dot_max()) {
+      {  // w' = w - V h1 and the second pass's dot products (with ||w'||^2 last) from one read of V
+        const double n = (double)ne;
+        KScope k(h, IRK_K_MULTIDOT, (j + 3.0) * n * 8, 4.0 * (j + 1) * n + 2.0 * n);
+        launch_axpy_dot(st, w, h->V, ne, j + 1, h->h1, ne, h->partial);
+      }
+      const double nb = krylov_partial_blocks();
+      KScope k(h, IRK_K_OTHER, (j + 2) * nb * 8, (j + 2) * nb);
+      launch_reduce_partials(st, h->partial, j + 2, h->h2);
+    } else {
+      multi_axpy(h, w, h->V, ne, j + 1, h->h1, -1.0);
+      multidot(h, h->V, ne, j + 2, w, h->h2);
+    }
     {
       KScope k(h, IRK_K_OTHER, 0, 0);
       launch_givens(st, j, ldh, h->H, h->cs, h->sn, h->g, h->h1, h->h2, nullptr, h->scal + 4, r0p, h->scal + 5, 1,
@@ -1020,6 +1060,25 @@ int arnoldi_step(irk_handle* h, int j, bool transpose) {
       KScope k(h, IRK_K_AXPY, (j + 3.0) * n * 8, 2.0 * (j + 1) * n + n);
       launch_multi_axpy(st, w, h->V, ne, j + 1, h->h2, -1.0, ne, h->scal + 8);
     }
+  } else if (h->opt.orth == IRK_ORTH_CGS) {
+    // one pass: h1 = V^T w, w' = w - V h1 with ||w'||^2 reduced in the same sweep, normalise
+    multidot(h, h->V, ne, j + 1, w, h->h1);
+    const double n = (double)ne;
+    {
+      KScope k(h, IRK_K_AXPY, (j + 3.0) * n * 8, 2.0 * (j + 1) * n + 2.0 * n);
+      launch_axpy_norm(st, w, h->V, ne, j + 1, h->h1, ne, h->partial);
+    }
+    {
+      const double nb = krylov_partial_blocks();
+      KScope k(h, IRK_K_OTHER, nb * 8, nb);
+      launch_reduce_partials(st, h->partial, 1, h->scal + 3);
+    }
+    {
+      KScope k(h, IRK_K_OTHER, 0, 0);  // h2 holds zeros in this mode (set at create)
+      launch_givens(st, j, ldh, h->H, h->cs, h->sn, h->g, h->h1, h->h2, h->scal + 3, h->scal + 4, r0p, h->scal + 5);
+    }
+    KScope k(h, IRK_K_OTHER, 16.0 * n, n);
+    launch_scale(st, w, w, h->scal + 4, ne);
   } else {
     // one pass with ||w||^2 (V_{j+1} is w itself), DGKS test, normalisation fused
     multidot(h, h->V, ne, j + 2, w, h->h1);
@@ -1161,14 +1220,25 @@ int fgmres(irk_handle* h, const double* rhs, double* x, bool transpose, irk_stat
     }
     multi_axpy(h, x, h->Z, ne, J, h->y, 1.0);
     CK_LAUNCH();
-    if (conv || its >= h->opt.maxit) break;
-    // restart: r = rhs - S x in tmp, beta = ||r||
+    // one-pass Gram-Schmidt: the estimate |g_{J}| assumes an orthonormal basis, so confirm it
+    const bool verify = conv && h->opt.orth == IRK_ORTH_CGS;
+    if ((conv && !verify) || (!conv && its >= h->opt.maxit)) break;
+    // restart (or verification): r = rhs - S x in tmp, beta = ||r||
     TRY(apply_operator(h, x, h->tmp, transpose));
     {
       KScope k(h, IRK_K_OTHER, 24.0 * ne, (double)ne);
       launch_sub(st, h->tmp, rhs, h->tmp, ne);
     }
     TRY(norm2(h, h->tmp, 0));
+    if (verify) {
+      CK(cudaMemcpyAsync(h->pinned, h->scal, 8, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      rel = h->pinned[0] / r0;
+      if (!std::isfinite(rel)) return fail(IRK_ENONFINITE, "FGMRES true residual is %g", rel);
+      if (rel <= h->opt.rtol) break;
+      conv = false;
+      if (its >= h->opt.maxit) break;
+    }
     r = h->tmp;
   }
   if (stats) {
@@ -1487,11 +1557,12 @@ int irk_solve(irk_handle* h, const double* r, double* k, irk_stats* stats) {
   TRY(dev_in(h, r, bytes, 0, &rd));
   TRY(dev_out(h, k, bytes, 1, &kd, &khost));
   const bool ia = (h->opt.splitting == IRK_SPLIT_IA);
-  const int rc = solve(h, (const double*)rd, ia ? h->tmp : (double*)kd, false, stats);
+  // IA: w in h->k (not h->tmp, which FGMRES uses for restart residuals)
+  const int rc = solve(h, (const double*)rd, ia ? h->k : (double*)kd, false, stats);
   if (rc != IRK_OK && rc != IRK_ENOCONV) return rc;
   if (ia) {  // k = (A^{-1} (x) I) w
     KScope kk(h, IRK_K_OTHER, 16.0 * h->ne, 2.0 * h->s * h->ne);
-    launch_stage_mix(h->s, h->st, h->lev[0].nn, ia_mixing(h, false), h->tmp, (double*)kd);
+    launch_stage_mix(h->s, h->st, h->lev[0].nn, ia_mixing(h, false), h->k, (double*)kd);
     CK_LAUNCH();
   }
   if (khost) TRY(dev_out_finish(h, k, kd, bytes));

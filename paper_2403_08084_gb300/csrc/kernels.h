@@ -42,7 +42,15 @@ struct MG2 {
                              const Vec8& cj, T* out);
   static void cast_to(cudaStream_t st, const double* src, T* dst, size_t n);
   static void cast_from(cudaStream_t st, const T* src, double* dst, size_t n);
-  static void coarse_solve(int S, cudaStream_t st, int nint, const C* binv, const int* map, const T* b, T* x);
+  // coarsest level (nxc nodes per axis, (nxc - 2)^2 unknowns in row-major interior order)
+  static void coarse_solve(int S, cudaStream_t st, int nxc, const C* binv, const T* b, T* x);
+  // fused V(2, 2) legs of a coarse level (mg2d_legs.cuh): x = J(J(0; b)), b_c = P^T (b - B x); and
+  // xout = J(J(xin + P e_c; b)) (xout != xin).  rec != nullptr: B_i records, else hm M + sigma K.
+  static void down_leg(int S, cudaStream_t st, int nxf, const C* cf, double hm, const Vec8& sigma, const C* rec,
+                       size_t rstride, const C* dinv, int dstride, const T* b, T* xout, int nxc, T* bc);
+  static void up_leg(int S, cudaStream_t st, int nxf, const C* cf, double hm, const Vec8& sigma, const C* rec,
+                     size_t rstride, const C* dinv, int dstride, const T* xin, const T* b, int nxc, const T* ec,
+                     T* xout);
 };
 
 // Finest-level 2D kernels forming the stencil from per-cell kappa (mg2d_kappa.cuh);
@@ -112,6 +120,14 @@ void launch_multidot(cudaStream_t st, const double* V, size_t ld, int count, con
                      double* partial, const int* run_if = nullptr);
 void launch_reduce_partials(cudaStream_t st, const double* partial, int count, double* out,
                             const int* run_if = nullptr);
+// w -= sum_k coef[k] V_k and partial sums of V_k . w (k < count) and w . w (entry count) in one pass,
+// for count <= krylov_axpy_dot_max() (else nothing is launched and false returned).
+int krylov_axpy_dot_max();
+bool launch_axpy_dot(cudaStream_t st, double* w, const double* V, size_t ld, int count, const double* coef, size_t n,
+                     double* partial);
+// w -= sum_k coef[k] V_k (count <= 128) with the partial sums of the updated w . w (count 1 for reduce_partials)
+void launch_axpy_norm(cudaStream_t st, double* w, const double* V, size_t ld, int count, const double* coef,
+                      size_t n, double* partial);
 void launch_multi_axpy(cudaStream_t st, double* w, const double* V, size_t ld, int count, const double* coef,
                        double sign, size_t n, const double* scale = nullptr, const int* run_if = nullptr);
 void launch_scale(cudaStream_t st, double* dst, const double* src, const double* denom, size_t n,

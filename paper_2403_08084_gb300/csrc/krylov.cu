@@ -118,6 +118,81 @@ __global__ void __launch_bounds__(kThreads) multi_axpy_kernel(double* __restrict
   }
 }
 
+// The middle of classical Gram-Schmidt applied twice, in one pass over V:
+//   w' = w - sum_k coef[k] V_k   (written back to w), and
+//   partial sums of V_k . w' for k < K and of w' . w' (as entry K),
+// each thread keeping its K entries of V in registers between the update and the dot
+// products (one read of V instead of two).  Layout of partial as in multidot_kernel.
+constexpr int kAxpyDotMax = 16;  // largest K handled; the caller falls back to two kernels above
+
+template <int K>
+__global__ void __launch_bounds__(kThreads) axpy_dot_kernel(double* __restrict__ w, const double* __restrict__ V,
+                                                            size_t ld, const double* __restrict__ coef, size_t n,
+                                                            double* __restrict__ partial) {
+  IRK_PDL_ENTRY;
+  __shared__ double c[K];
+  __shared__ double red[kThreads / 32][K + 1];
+  if (threadIdx.x < K) c[threadIdx.x] = coef[threadIdx.x];
+  __syncthreads();
+  double d[K + 1];
+#pragma unroll
+  for (int k = 0; k <= K; ++k) d[k] = 0.0;
+  for (size_t e = blockIdx.x * (size_t)kThreads + threadIdx.x; e < n; e += (size_t)gridDim.x * kThreads) {
+    double v[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = V[(size_t)k * ld + e];
+    double acc = w[e];
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc = fma(-c[k], v[k], acc);
+    w[e] = acc;
+#pragma unroll
+    for (int k = 0; k < K; ++k) d[k] = fma(v[k], acc, d[k]);
+    d[K] = fma(acc, acc, d[K]);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k <= K; ++k) {
+    const double t = warp_sum(d[k]);
+    if (lane == 0) red[warp][k] = t;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k <= K; ++k) {
+      double t = (lane < kThreads / 32) ? red[lane][k] : 0.0;
+      t = warp_sum(t);
+      if (lane == 0) partial[(size_t)k * gridDim.x + blockIdx.x] = t;
+    }
+  }
+}
+
+// w -= sum_k coef[k] V_k, with the partial sums of the updated w . w (layout of multidot_kernel, one product).
+__global__ void __launch_bounds__(kThreads) axpy_norm_kernel(double* __restrict__ w, const double* __restrict__ V,
+                                                             size_t ld, int count, const double* __restrict__ coef,
+                                                             size_t n, double* __restrict__ partial) {
+  IRK_PDL_ENTRY;
+  __shared__ double c[128];
+  __shared__ double red[kThreads / 32];
+  for (int k = threadIdx.x; k < count; k += kThreads) c[k] = coef[k];
+  __syncthreads();
+  double d = 0.0;
+  for (size_t e = blockIdx.x * (size_t)kThreads + threadIdx.x; e < n; e += (size_t)gridDim.x * kThreads) {
+    double acc = w[e];
+    for (int k = 0; k < count; ++k) acc = fma(-c[k], V[(size_t)k * ld + e], acc);
+    w[e] = acc;
+    d = fma(acc, acc, d);
+  }
+  d = warp_sum(d);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = d;
+  __syncthreads();
+  if (warp == 0) {
+    d = (lane < kThreads / 32) ? red[lane] : 0.0;
+    d = warp_sum(d);
+    if (lane == 0) partial[blockIdx.x] = d;
+  }
+}
+
 __global__ void __launch_bounds__(kThreads) scale_kernel(double* __restrict__ dst, const double* __restrict__ src,
                                                          const double* __restrict__ denom, size_t n,
                                                          const int* __restrict__ run_if) {
@@ -285,6 +360,7 @@ int grid_for(size_t n) {
 }  // namespace
 
 int krylov_partial_blocks() { return kPartialBlocks; }
+int krylov_axpy_dot_max() { return kAxpyDotMax; }
 
 void launch_multidot(cudaStream_t st, const double* V, size_t ld, int count, const double* w, size_t n,
                      double* partial, const int* run_if) {
@@ -297,6 +373,22 @@ void launch_reduce_partials(cudaStream_t st, const double* partial, int count, d
 void launch_multi_axpy(cudaStream_t st, double* w, const double* V, size_t ld, int count, const double* coef,
                        double sign, size_t n, const double* scale, const int* run_if) {
   launch_k(multi_axpy_kernel, grid_for(n), kThreads, 0, st, w, V, ld, count, coef, sign, n, scale, run_if);
+}
+void launch_axpy_norm(cudaStream_t st, double* w, const double* V, size_t ld, int count, const double* coef,
+                      size_t n, double* partial) {
+  launch_k(axpy_norm_kernel, kPartialBlocks, kThreads, 0, st, w, V, ld, count, coef, n, partial);
+}
+bool launch_axpy_dot(cudaStream_t st, double* w, const double* V, size_t ld, int count, const double* coef, size_t n,
+                     double* partial) {
+#define IRK_AXPY_DOT(K) \
+  case K: launch_k(axpy_dot_kernel<K>, kPartialBlocks, kThreads, 0, st, w, V, ld, coef, n, partial); return true;
+  switch (count) {
+    IRK_AXPY_DOT(1) IRK_AXPY_DOT(2) IRK_AXPY_DOT(3) IRK_AXPY_DOT(4) IRK_AXPY_DOT(5) IRK_AXPY_DOT(6)
+    IRK_AXPY_DOT(7) IRK_AXPY_DOT(8) IRK_AXPY_DOT(9) IRK_AXPY_DOT(10) IRK_AXPY_DOT(11) IRK_AXPY_DOT(12)
+    IRK_AXPY_DOT(13) IRK_AXPY_DOT(14) IRK_AXPY_DOT(15) IRK_AXPY_DOT(16)
+    default: return false;
+  }
+#undef IRK_AXPY_DOT
 }
 void launch_scale(cudaStream_t st, double* dst, const double* src, const double* denom, size_t n, const int* run_if) {
   launch_k(scale_kernel, grid_for(n), kThreads, 0, st, dst, src, denom, n, run_if);

@@ -233,34 +233,58 @@ __global__ void cast_from_kernel(const T* __restrict__ src, double* __restrict__
 
 // Exact coarsest-level solve x = B_c^{-1} b with a precomputed dense inverse per
 // stage (the paper's multigrid uses a direct coarse solve).  blockIdx.y = stage;
-// one warp per row; the stage's interior right-hand side is staged in shared memory.
+// one warp per row.  The solve is a dense matrix-vector product whose matrix
+// (7.4 MB in FP64 for a 32 x 32 coarsest mesh) is mostly evicted from L2 between
+// V-cycles, so it is latency-bound unless many loads are in flight: each lane first
+// issues the loads of its kCoarseChunk row entries (the whole row for up to 1024
+// columns) into registers, and only then stages the right-hand side in shared
+// memory (independent loads: interior unknown c is node (c % m + 1) + nxc (c / m + 1),
+// m = nxc - 2), so the row fetch overlaps the staging.
+constexpr int kCoarseChunk = 32;  // row entries per lane held in registers (32 x 32 = 1024 columns)
+constexpr int kCoarseThreads = 128;
+
+__device__ __forceinline__ int coarse_node(int c, int nxc) {
+  const int m = nxc - 2;
+  return (c % m + 1) + nxc * (c / m + 1);
+}
+
 template <typename T, typename C, int S>
-__global__ void coarse_solve_kernel(int nint, const C* __restrict__ binv, const int* __restrict__ map,
-                                    const T* __restrict__ b, T* __restrict__ x) {
+__global__ void __launch_bounds__(kCoarseThreads) coarse_solve_kernel(int nint, int nxc, const C* __restrict__ binv,
+                                                                      const T* __restrict__ b, T* __restrict__ x) {
   IRK_PDL_ENTRY;
   extern __shared__ unsigned char smem_raw[];
   C* bs = reinterpret_cast<C*>(smem_raw);
   const int i = blockIdx.y;
-  for (int c = threadIdx.x; c < nint; c += blockDim.x) bs[c] = ld<C>(b + (size_t)map[c] * S + i);
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const C* Bi = binv + (size_t)i * nint * nint;
-  for (int r = blockIdx.x * nw + warp; r < nint; r += gridDim.x * nw) {
-    C a0 = 0, a1 = 0, a2 = 0, a3 = 0;  // independent chains keep several loads in flight
-    const C* row = Bi + (size_t)r * nint;
-    int c = lane;
-    for (; c + 96 < nint; c += 128) {
-      a0 += row[c] * bs[c];
-      a1 += row[c + 32] * bs[c + 32];
-      a2 += row[c + 64] * bs[c + 64];
-      a3 += row[c + 96] * bs[c + 96];
-    }
-    for (; c < nint; c += 32) a0 += row[c] * bs[c];
-    C acc = (a0 + a1) + (a2 + a3);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int r = blockIdx.x * (kCoarseThreads / 32) + warp;  // one row per warp; the grid covers every row
+  const C* row = binv + (size_t)i * nint * nint + (size_t)(r < nint ? r : 0) * nint;
+  C acc = 0;
+  for (int c0 = 0; c0 < nint; c0 += 32 * kCoarseChunk) {
+    C a[kCoarseChunk];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) st(x + (size_t)map[r] * S + i, acc);
+    for (int k = 0; k < kCoarseChunk; ++k) {
+      const int c = c0 + lane + 32 * k;
+      a[k] = (r < nint && c < nint) ? row[c] : C(0);
+    }
+    if (c0 == 0) {
+#pragma unroll 8
+      for (int c = threadIdx.x; c < nint; c += kCoarseThreads) bs[c] = ld<C>(b + (size_t)coarse_node(c, nxc) * S + i);
+      __syncthreads();
+    }
+    C p0 = 0, p1 = 0, p2 = 0, p3 = 0;
+#pragma unroll
+    for (int k = 0; k < kCoarseChunk; k += 4) {
+      const int c = c0 + lane + 32 * k;
+      if (c < nint) p0 += a[k] * bs[c];
+      if (c + 32 < nint) p1 += a[k + 1] * bs[c + 32];
+      if (c + 64 < nint) p2 += a[k + 2] * bs[c + 64];
+      if (c + 96 < nint) p3 += a[k + 3] * bs[c + 96];
+    }
+    acc += (p0 + p1) + (p2 + p3);
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0 && r < nint) st(x + (size_t)coarse_node(r, nxc) * S + i, acc);
 }
 
 // ----------------------------------------------------------------------------
@@ -358,13 +382,14 @@ void MG2<T, C>::cast_from(cudaStream_t st, const T* src, double* dst, size_t n) 
   launch_k(cast_from_kernel<T, C>, blocks, 256, 0, st, src, dst, n);
 }
 template <typename T, typename C>
-void MG2<T, C>::coarse_solve(int S, cudaStream_t st, int nint, const C* binv, const int* map, const T* b, T* x) {
-  const int threads = 256, rows_per_block = threads / 32;
-  int gx = (nint + rows_per_block - 1) / rows_per_block;
-  if (gx > 152 * 4) gx = 152 * 4;
+void MG2<T, C>::coarse_solve(int S, cudaStream_t st, int nxc, const C* binv, const T* b, T* x) {
+  const int nint = (nxc - 2) * (nxc - 2);
+  const int gx = (nint + kCoarseThreads / 32 - 1) / (kCoarseThreads / 32);  // one warp per row
   dim3 g(gx, S);
   size_t shm = sizeof(C) * (size_t)nint;
-  IRK_DISPATCH_S(S, launch_k(coarse_solve_kernel<T, C, SS>, g, threads, shm, st, nint, binv, map, b, x));
+  IRK_DISPATCH_S(S, launch_k(coarse_solve_kernel<T, C, SS>, g, kCoarseThreads, shm, st, nint, nxc, binv, b, x));
 }
 
 }  // namespace irk
+
+#include "mg2d_legs.cuh"

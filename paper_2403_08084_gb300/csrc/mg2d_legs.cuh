@@ -1,0 +1,335 @@
+// Fused legs of the 2D V-cycle on the coarse levels (Sec. 3.1's multigrid
+// approximation of a diagonal block B = M + sigma K), V(2, 2).
+//
+// On the coarse levels the six kernels of a level (two pre-sweeps, residual,
+// restriction, prolongation, two post-sweeps) each process so few nodes that a
+// launch costs more than its work.  Two kernels replace them:
+//
+//   down leg   x2 = J(J(0; b)), r = b - B x2, b_c = P^T r
+//   up leg     y0 = x + P e_c, y2 = J(J(y0; b))
+//
+// Each block owns a rectangle of fine nodes and recomputes the values its
+// stencils need on a halo in shared memory (x1 on a halo of 2 and x2 on a halo
+// of 1 for the down leg, y0 on 2 and y1 on 1 for the up leg).  The arithmetic at
+// every node is that of the separate kernels (same stencil records, same order of
+// operations); only the intermediate vectors stay in shared memory in the
+// arithmetic type C instead of being stored in T.
+//
+// Stencil records: FP64 V-cycles (REC) store B_i per stage (stage-major, stride
+// rstride); FP32 / BF16 ones form hm M + sigma_i K from the stiffness records cf.
+#pragma once
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace irk {
+
+// The level's 9-point record stencil at node p, the neighbour values given by X(dx, dy).
+// Same products and order as k_apply.
+template <typename C, typename F>
+__device__ __forceinline__ C rec_apply_xy(const C* __restrict__ cf, int p, int nx, F X) {
+  const C* c0 = cf + (size_t)p * kCoef2;
+  const C* cw = cf + (size_t)(p - 1) * kCoef2;
+  const C* cs = cf + (size_t)(p - nx) * kCoef2;
+  const C* csw = cf + (size_t)(p - nx - 1) * kCoef2;
+  const C* cse = cf + (size_t)(p - nx + 1) * kCoef2;
+  C y = c0[0] * X(0, 0);
+  y += c0[1] * X(1, 0);
+  y += cw[1] * X(-1, 0);
+  y += c0[2] * X(0, 1);
+  y += cs[2] * X(0, -1);
+  y += c0[3] * X(1, 1);
+  y += csw[3] * X(-1, -1);
+  y += c0[4] * X(-1, 1);
+  y += cse[4] * X(1, -1);
+  return y;
+}
+
+// 36/h^2 (M x) at a node, neighbour values from X(dx, dy); same order as m_apply_unscaled.
+template <typename C, typename F>
+__device__ __forceinline__ C mass_unscaled_xy(F X) {
+  C edge = X(-1, 0) + X(1, 0) + X(0, -1) + X(0, 1);
+  C corner = X(-1, -1) + X(1, -1) + X(-1, 1) + X(1, 1);
+  return C(16) * X(0, 0) + C(4) * edge + corner;
+}
+
+// B_i x at node p: the stage's B record (REC) or hm M + sigma_i K.
+template <typename C, bool REC>
+struct BlockOp {
+  const C* rec;    // REC: records of B_0 .. B_{S-1} of this V-cycle, stage-major
+  size_t rstride;  // REC: distance between the stages' records
+  const C* cf;     // !REC: stiffness records
+  C hm;
+  VecT<C> sigma;
+  template <typename F>
+  __device__ __forceinline__ C apply(int i, int p, int nx, F X) const {
+    if constexpr (REC) {
+      return rec_apply_xy<C>(rec + (size_t)i * rstride, p, nx, X);
+    } else {
+      return hm * mass_unscaled_xy<C>(X) + sigma.v[i] * rec_apply_xy<C>(cf, p, nx, X);
+    }
+  }
+};
+
+__device__ __forceinline__ bool interior_node(int ix, int iy, int nx) {
+  return ix >= 1 && iy >= 1 && ix <= nx - 2 && iy <= nx - 2;
+}
+
+// Down leg.  The block owns fine nodes [FX0, FX0 + 2CX) x [FY0, FY0 + 2CY), FX0 = 1 + 2 CX bx, and the
+// coarse nodes I in [1 + CX bx, 1 + CX (bx + 1)) (fine node 2I), likewise in y.  Regions (fine, inclusive):
+//   x1 on [FX0 - 2, FX0 + 2CX + 2], x2 on [FX0 - 1, FX0 + 2CX + 1], r on [FX0, FX0 + 2CX].
+//
+// NT threads; every phase loop has a compile-time trip count and is unrolled, so that all the
+// global loads of a phase are in flight together (the small levels are latency-bound).
+template <typename T, typename C, int S, int CX, int CY, int NT, bool REC>
+__global__ void __launch_bounds__(NT) down_leg_kernel(int nxf, BlockOp<C, REC> op, const C* __restrict__ dinv,
+                                                       int dstride, const T* __restrict__ b, T* __restrict__ xout,
+                                                       int nxc, T* __restrict__ bc) {
+  IRK_PDL_ENTRY;
+  constexpr int W1 = 2 * CX + 5, H1 = 2 * CY + 5;
+  constexpr int W2 = 2 * CX + 3, H2 = 2 * CY + 3;
+  constexpr int W3 = 2 * CX + 1, H3 = 2 * CY + 1;
+  extern __shared__ unsigned char leg_smem[];
+  C* X1 = reinterpret_cast<C*>(leg_smem);
+  C* X2 = X1 + W1 * H1 * S;
+  C* R = X2 + W2 * H2 * S;
+  const int FX0 = 1 + 2 * CX * blockIdx.x, FY0 = 1 + 2 * CY * blockIdx.y;
+
+  // x1 = omega D^{-1} b (zero initial guess), 0 off the interior
+#pragma unroll
+  for (int t = threadIdx.x; t < W1 * H1; t += NT) {
+    const int ix = FX0 - 2 + t % W1, iy = FY0 - 2 + t / W1;
+    const bool in = interior_node(ix, iy, nxf);
+    const int p = ix + nxf * iy;
+#pragma unroll
+    for (int i = 0; i < S; ++i)
+      X1[t * S + i] = in ? dinv[(size_t)p * dstride + i] * ld<C>(b + (size_t)p * S + i) : C(0);
+  }
+  __syncthreads();
+  // x2 = x1 + omega D^{-1} (b - B x1); the owned part is the leg's smoothed iterate
+#pragma unroll
+  for (int t = threadIdx.x; t < W2 * H2; t += NT) {
+    const int lx = t % W2, ly = t / W2;
+    const int ix = FX0 - 1 + lx, iy = FY0 - 1 + ly;
+    const bool in = interior_node(ix, iy, nxf);
+    const bool own = in && ix >= FX0 && ix < FX0 + 2 * CX && iy >= FY0 && iy < FY0 + 2 * CY;
+    const int p = ix + nxf * iy;
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      C v = C(0);
+      if (in) {
+        auto X = [&](int dx, int dy) { return X1[((ly + 1 + dy) * W1 + (lx + 1 + dx)) * S + i]; };
+        const C bx = op.apply(i, p, nxf, X);
+        v = X(0, 0) + dinv[(size_t)p * dstride + i] * (ld<C>(b + (size_t)p * S + i) - bx);
+      }
+      X2[t * S + i] = v;
+      if (own) st(xout + (size_t)p * S + i, v);
+    }
+  }
+  __syncthreads();
+  // r = b - B x2
+#pragma unroll
+  for (int t = threadIdx.x; t < W3 * H3; t += NT) {
+    const int lx = t % W3, ly = t / W3;
+    const int ix = FX0 + lx, iy = FY0 + ly;
+    const bool in = interior_node(ix, iy, nxf);
+    const int p = ix + nxf * iy;
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      C v = C(0);
+      if (in) {
+        auto X = [&](int dx, int dy) { return X2[((ly + 1 + dy) * W2 + (lx + 1 + dx)) * S + i]; };
+        v = ld<C>(b + (size_t)p * S + i) - op.apply(i, p, nxf, X);
+      }
+      R[t * S + i] = v;
+    }
+  }
+  __syncthreads();
+  // b_c = P^T r (full weighting), same order as restrict_kernel
+#pragma unroll
+  for (int t = threadIdx.x; t < CX * CY; t += NT) {
+    const int I = 1 + CX * blockIdx.x + t % CX, J = 1 + CY * blockIdx.y + t / CX;
+    if (I > nxc - 2 || J > nxc - 2) continue;
+    const int lx = 2 * I - FX0, ly = 2 * J - FY0;  // in [1, 2CX - 1]
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      auto Rv = [&](int dx, int dy) { return R[((ly + dy) * W3 + (lx + dx)) * S + i]; };
+      C v = Rv(0, 0) + C(0.5) * (Rv(-1, 0) + Rv(1, 0) + Rv(0, -1) + Rv(0, 1)) +
+            C(0.25) * (Rv(-1, -1) + Rv(1, -1) + Rv(-1, 1) + Rv(1, 1));
+      st(bc + (size_t)(I + nxc * J) * S + i, v);
+    }
+  }
+}
+
+// Up leg.  The block owns fine nodes [FX0, FX0 + TX) x [FY0, FY0 + TY), FX0 = 1 + TX bx.  Regions:
+//   y0 = x + P e_c on [FX0 - 2, FX0 + TX + 1], y1 = J(y0) on [FX0 - 1, FX0 + TX], y2 = J(y1) owned.
+// xout must not alias xin (other blocks read xin on their halos).
+template <typename T, typename C, int S, int TX, int TY, int NT, bool REC>
+__global__ void __launch_bounds__(NT) up_leg_kernel(int nxf, BlockOp<C, REC> op, const C* __restrict__ dinv,
+                                                     int dstride, const T* __restrict__ xin, const T* __restrict__ b,
+                                                     int nxc, const T* __restrict__ ec, T* __restrict__ xout) {
+  IRK_PDL_ENTRY;
+  constexpr int W0 = TX + 4, H0 = TY + 4;
+  constexpr int W1 = TX + 2, H1 = TY + 2;
+  extern __shared__ unsigned char leg_smem[];
+  C* Y0 = reinterpret_cast<C*>(leg_smem);
+  C* Y1 = Y0 + W0 * H0 * S;
+  const int FX0 = 1 + TX * blockIdx.x, FY0 = 1 + TY * blockIdx.y;
+
+  // y0 = x + P e_c (bilinear interpolation as in prolong_add_kernel), 0 off the interior
+#pragma unroll
+  for (int t = threadIdx.x; t < W0 * H0; t += NT) {
+    const int ix = FX0 - 2 + t % W0, iy = FY0 - 2 + t / W0;
+    const bool in = interior_node(ix, iy, nxf);
+    const int p = ix + nxf * iy;
+    const int I0 = ix >> 1, I1 = (ix + 1) >> 1, J0 = iy >> 1, J1 = (iy + 1) >> 1;
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      C v = C(0);
+      if (in) {
+        auto E = [&](int I, int J) { return ld<C>(ec + (size_t)(I + nxc * J) * S + i); };
+        const C pe = C(0.25) * ((E(I0, J0) + E(I1, J0)) + (E(I0, J1) + E(I1, J1)));
+        v = ld<C>(xin + (size_t)p * S + i) + pe;
+      }
+      Y0[t * S + i] = v;
+    }
+  }
+  __syncthreads();
+  // y1 = y0 + omega D^{-1} (b - B y0)
+#pragma unroll
+  for (int t = threadIdx.x; t < W1 * H1; t += NT) {
+    const int lx = t % W1, ly = t / W1;
+    const int ix = FX0 - 1 + lx, iy = FY0 - 1 + ly;
+    const bool in = interior_node(ix, iy, nxf);
+    const int p = ix + nxf * iy;
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      C v = C(0);
+      if (in) {
+        auto X = [&](int dx, int dy) { return Y0[((ly + 1 + dy) * W0 + (lx + 1 + dx)) * S + i]; };
+        v = X(0, 0) + dinv[(size_t)p * dstride + i] * (ld<C>(b + (size_t)p * S + i) - op.apply(i, p, nxf, X));
+      }
+      Y1[t * S + i] = v;
+    }
+  }
+  __syncthreads();
+  // y2 = y1 + omega D^{-1} (b - B y1) on the owned nodes
+#pragma unroll
+  for (int t = threadIdx.x; t < TX * TY; t += NT) {
+    const int lx = t % TX, ly = t / TX;
+    const int ix = FX0 + lx, iy = FY0 + ly;
+    if (!interior_node(ix, iy, nxf)) continue;
+    const int p = ix + nxf * iy;
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      auto X = [&](int dx, int dy) { return Y1[((ly + 1 + dy) * W1 + (lx + 1 + dx)) * S + i]; };
+      const C v = X(0, 0) + dinv[(size_t)p * dstride + i] * (ld<C>(b + (size_t)p * S + i) - op.apply(i, p, nxf, X));
+      st(xout + (size_t)p * S + i, v);
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// launchers: tile sizes by level size (large levels: fewer halo nodes per owned
+// node; small ones: more blocks in flight)
+// ----------------------------------------------------------------------------
+template <typename K>
+inline void leg_smem_attr(K kernel, size_t smem) {
+  if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <typename T, typename C, int S, int CX, int CY, int NT, bool REC>
+void launch_down_leg(cudaStream_t st, int nxf, const BlockOp<C, REC>& op, const C* dinv, int dstride, const T* b,
+                     T* xout, int nxc, T* bc) {
+  constexpr int W1 = 2 * CX + 5, H1 = 2 * CY + 5, W2 = 2 * CX + 3, H2 = 2 * CY + 3, W3 = 2 * CX + 1, H3 = 2 * CY + 1;
+  const size_t smem = sizeof(C) * S * (size_t)(W1 * H1 + W2 * H2 + W3 * H3);
+  auto kern = down_leg_kernel<T, C, S, CX, CY, NT, REC>;
+  leg_smem_attr(kern, smem);
+  const int m = nxf - 2;
+  dim3 g((m + 2 * CX - 1) / (2 * CX), (m + 2 * CY - 1) / (2 * CY));
+  launch_k(kern, g, dim3(NT), smem, st, nxf, op, dinv, dstride, b, xout, nxc, bc);
+}
+
+template <typename T, typename C, int S, int TX, int TY, int NT, bool REC>
+void launch_up_leg(cudaStream_t st, int nxf, const BlockOp<C, REC>& op, const C* dinv, int dstride, const T* xin,
+                   const T* b, int nxc, const T* ec, T* xout) {
+  const size_t smem = sizeof(C) * S * (size_t)((TX + 4) * (TY + 4) + (TX + 2) * (TY + 2));
+  auto kern = up_leg_kernel<T, C, S, TX, TY, NT, REC>;
+  leg_smem_attr(kern, smem);
+  const int m = nxf - 2;
+  dim3 g((m + TX - 1) / TX, (m + TY - 1) / TY);
+  launch_k(kern, g, dim3(NT), smem, st, nxf, op, dinv, dstride, xin, b, nxc, ec, xout);
+}
+
+// Levels whose fine grid has at least this many nodes per axis use the large tiles (fewer halo
+// nodes per owned node, for the arithmetic-bound FP64 legs); smaller levels use 8 x 8 owned nodes
+// per block so that each phase is one round of loads and there are many blocks in flight.
+constexpr int kLegLargeNx = 513;
+
+template <typename T, typename C, int S, bool REC>
+void down_leg_s(cudaStream_t st, int nxf, const BlockOp<C, REC>& op, const C* dinv, int dstride, const T* b, T* xout,
+                int nxc, T* bc) {
+  if (nxf >= kLegLargeNx)
+    launch_down_leg<T, C, S, 16, 8, 256, REC>(st, nxf, op, dinv, dstride, b, xout, nxc, bc);
+  else  // regions 13 x 13, 11 x 11, 9 x 9
+    launch_down_leg<T, C, S, 4, 4, 192, REC>(st, nxf, op, dinv, dstride, b, xout, nxc, bc);
+}
+
+template <typename T, typename C, int S, bool REC>
+void up_leg_s(cudaStream_t st, int nxf, const BlockOp<C, REC>& op, const C* dinv, int dstride, const T* xin,
+              const T* b, int nxc, const T* ec, T* xout) {
+  if (nxf >= kLegLargeNx)
+    launch_up_leg<T, C, S, 32, 16, 256, REC>(st, nxf, op, dinv, dstride, xin, b, nxc, ec, xout);
+  else  // regions 12 x 12, 10 x 10, 8 x 8
+    launch_up_leg<T, C, S, 8, 8, 160, REC>(st, nxf, op, dinv, dstride, xin, b, nxc, ec, xout);
+}
+
+#define IRK_LEG_DISPATCH(S, FN, ...)                                  \
+  switch (S) {                                                        \
+    case 1: FN<T, C, 1>(__VA_ARGS__); break;                          \
+    case 2: FN<T, C, 2>(__VA_ARGS__); break;                          \
+    case 3: FN<T, C, 3>(__VA_ARGS__); break;                          \
+    case 4: FN<T, C, 4>(__VA_ARGS__); break;                          \
+    default: break;                                                   \
+  }
+
+template <typename T, typename C, int S>
+void down_leg_any(cudaStream_t st, int nxf, const C* cf, double hm, const Vec8& sigma, const C* rec, size_t rstride,
+                  const C* dinv, int dstride, const T* b, T* xout, int nxc, T* bc) {
+  if (rec != nullptr) {
+    BlockOp<C, true> op{rec, rstride, nullptr, C(0), {}};
+    down_leg_s<T, C, S, true>(st, nxf, op, dinv, dstride, b, xout, nxc, bc);
+  } else {
+    BlockOp<C, false> op{nullptr, 0, cf, (C)hm, to_vec<C>(sigma)};
+    down_leg_s<T, C, S, false>(st, nxf, op, dinv, dstride, b, xout, nxc, bc);
+  }
+}
+
+template <typename T, typename C, int S>
+void up_leg_any(cudaStream_t st, int nxf, const C* cf, double hm, const Vec8& sigma, const C* rec, size_t rstride,
+                const C* dinv, int dstride, const T* xin, const T* b, int nxc, const T* ec, T* xout) {
+  if (rec != nullptr) {
+    BlockOp<C, true> op{rec, rstride, nullptr, C(0), {}};
+    up_leg_s<T, C, S, true>(st, nxf, op, dinv, dstride, xin, b, nxc, ec, xout);
+  } else {
+    BlockOp<C, false> op{nullptr, 0, cf, (C)hm, to_vec<C>(sigma)};
+    up_leg_s<T, C, S, false>(st, nxf, op, dinv, dstride, xin, b, nxc, ec, xout);
+  }
+}
+
+template <typename T, typename C>
+void MG2<T, C>::down_leg(int S, cudaStream_t st, int nxf, const C* cf, double hm, const Vec8& sigma, const C* rec,
+                         size_t rstride, const C* dinv, int dstride, const T* b, T* xout, int nxc, T* bc) {
+  IRK_LEG_DISPATCH(S, down_leg_any, st, nxf, cf, hm, sigma, rec, rstride, dinv, dstride, b, xout, nxc, bc)
+}
+
+template <typename T, typename C>
+void MG2<T, C>::up_leg(int S, cudaStream_t st, int nxf, const C* cf, double hm, const Vec8& sigma, const C* rec,
+                       size_t rstride, const C* dinv, int dstride, const T* xin, const T* b, int nxc, const T* ec,
+                       T* xout) {
+  IRK_LEG_DISPATCH(S, up_leg_any, st, nxf, cf, hm, sigma, rec, rstride, dinv, dstride, xin, b, nxc, ec, xout)
+}
+
+#undef IRK_LEG_DISPATCH
+
+}  // namespace irk

@@ -118,7 +118,7 @@ def test_vcycle_levels_single_stage(levels):
 # ----------------------------------------------------------------------------
 @pytest.mark.parametrize("kind", ["diag", "lower", "upper"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
-@pytest.mark.parametrize("orth", ["cgs2", "dgks"])
+@pytest.mark.parametrize("orth", ["cgs2", "dgks", "cgs"])
 def test_solve_matches_direct_and_iteration_count(kind, prec, orth):
     N, levels, s, dt = 64, 3, 3, 1 / 64
     kap = W.lognormal_kappa(2, N, 0.5, seed=9)
@@ -138,7 +138,8 @@ def test_solve_matches_direct_and_iteration_count(kind, prec, orth):
         S = rk.kronecker_operator(d.M, d.K, ot.A, dt)
         P = oracle_preconditioner(d, ot, dt, levels, kind, False)
         _, its, _, _ = krylov.fgmres(lambda v: S @ v, r_int.reshape(-1), P, rtol=1e-12)
-        assert abs(st["fgmres_its"] - its) <= 1, (st["fgmres_its"], its)
+        # one-pass Gram-Schmidt may need a few more iterations at this tight tolerance
+        assert abs(st["fgmres_its"] - its) <= (1 if orth != "cgs" else 3), (st["fgmres_its"], its)
 
 
 def manufactured_run(N, name, s, dt, steps, levels, kind, prec, kappa=None, rtol=1e-12):
@@ -197,8 +198,9 @@ def test_other_tableaux(name, s):
     assert rel(d.to_interior(u), uN) < 1e-10
 
 
-@pytest.mark.parametrize("orth", ["cgs2", "dgks"])
-def test_restarted_fgmres(orth):
+@pytest.mark.parametrize("splitting", ["ai", "ia"])
+@pytest.mark.parametrize("orth", ["cgs2", "dgks", "cgs"])
+def test_restarted_fgmres(orth, splitting):
     """A short restart length forces several restart cycles; the result still matches the direct solve."""
     N, levels, s, dt = 48, 2, 3, 1 / 32
     kap = W.lognormal_kappa(2, N, 0.5, seed=30)
@@ -207,11 +209,38 @@ def test_restarted_fgmres(orth):
     r_full = W.random_nodal(2, N, seed=31, s=s)
     k_ref = rk.KroneckerSolver(d.M, d.K, ot.A, dt).solve(d.to_interior(r_full, s))
     with Solver(N, product_tableau("RadauIIA", s), dt, kappa=kap, levels=levels, precond="diag", restart=4,
-                rtol=1e-12, orth=orth) as sv:
+                rtol=1e-12, orth=orth, splitting=splitting) as sv:
         k = np.empty(sv.n_nodes * s)
         st = sv.solve(r_full, k)
     assert st["converged"] and st["fgmres_its"] > 4
     assert rel(d.to_interior(k, s), k_ref) < 1e-10
+
+
+@pytest.mark.parametrize("splitting", ["ai", "ia"])
+@pytest.mark.parametrize("rtol", [1e-8, 1e-10, 1e-12])
+def test_one_pass_gram_schmidt_reports_the_true_residual(splitting, rtol):
+    """With one-pass classical Gram-Schmidt the reported residual is recomputed as ||r - S k|| / ||r||
+    at convergence; it must meet rtol, and the solution must match the two-pass solve to that level."""
+    N, levels, s, dt = 128, 4, 3, 1 / 64
+    kap = W.lognormal_kappa(2, N, 0.5, seed=33)
+    tab = product_tableau("RadauIIA", s)
+    r = dev(W.random_nodal(2, N, seed=34, s=s))
+    ks = {}
+    for orth in ("cgs", "cgs2"):
+        with Solver(N, tab, dt, kappa=kap, levels=levels, precond="lower", rtol=rtol, orth=orth,
+                    splitting=splitting) as sv:
+            k = torch.empty(sv.n_nodes * s, dtype=torch.float64, device="cuda")
+            st = sv.solve(r, k)
+            assert st["converged"] and st["rel_resid"] <= rtol
+            if orth == "cgs":
+                # the AI operator applied to k reproduces r (the IA solve returns k too)
+                with Solver(N, tab, dt, kappa=kap, levels=levels, precond="lower") as ai:
+                    y = torch.empty_like(k)
+                    ai.apply_operator(k, y)
+                true = float(torch.linalg.vector_norm(y - r) / torch.linalg.vector_norm(r))
+                assert true <= 1.5 * rtol, (true, st["rel_resid"])
+            ks[orth] = host(k)
+    assert rel(ks["cgs"], ks["cgs2"]) < 1e3 * rtol
 
 
 @pytest.mark.parametrize("prec", ["fp64", "bf16"])
