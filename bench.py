@@ -231,12 +231,26 @@ def gpu_arm(args, rank, world):
     # warm-up, then one instrumented step to find the kernel class that dominates device time
     run_steps(sv, tab, wl, u, f, 0, args.warmup)
     sv.perf_select([c for c in ("stage_apply", "jacobi", "residual", "restrict", "prolong", "coarse", "multidot",
-                                "axpy", "block_rhs", "mg_coarse")])
+                                "axpy", "block_rhs", "mg_coarse", "mg_tail")])
     u.copy_(u0)
     run_steps(sv, tab, wl, u, f, 0, 1)
     prof = sv.perf_read()["classes"]
     dominant = max(prof, key=lambda k: prof[k]["timed_ms"] if k != "other" else -1)
     shares = {k: round(v["timed_ms"], 4) for k, v in prof.items() if v["timed_ms"] > 0}
+    # every class's algorithmic rate in the instrumented step (events around each launch inflate
+    # the shortest kernels' times)
+    class_rates = {}
+    for k, v in prof.items():
+        if v["timed_ms"] > 0 and v["timed_launches"] > 0:
+            sec = v["timed_ms"] / 1e3
+            fp64 = k in FP64_CLASSES or vcycle == "fp64" or k == "other"
+            tfl = v["timed_flops"] / sec / 1e12
+            class_rates[k] = {"ms": round(v["timed_ms"], 4), "launches": v["timed_launches"],
+                              "gbs": round(v["timed_bytes"] / sec / 1e9, 1),
+                              "tflops": round(tfl, 4),
+                              "frac": round(tfl / FP64_PEAK_TFLOPS, 4) if fp64 else
+                              round(v["timed_bytes"] / sec / 1e9 / peaks()[0], 4),
+                              "bound": "alu" if fp64 else "hbm"}
 
     # timed region: the workload's first K steps from t = 0 (launch counters only, no per-kernel events)
     u.copy_(u0)
@@ -324,6 +338,7 @@ def gpu_arm(args, rank, world):
         "gpu_launches": launches,
         "roofline": roof,
         "kernel_ms_one_step": shares,
+        "class_rooflines": class_rates,
         "clocks": clk,
     }
     if rank == 0 and not args.no_e2e:

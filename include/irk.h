@@ -223,8 +223,10 @@ int irk_apply_preconditioner_noalloc(irk_handle* h, const double* v, double* z, 
 #define IRK_K_AXPY 7        /* Arnoldi / solution multi-axpy                 */
 #define IRK_K_BLOCK_RHS 8   /* triangular-preconditioner block right side    */
 #define IRK_K_OTHER 9       /* reductions, scaling, Givens, casts, RHS, update */
-#define IRK_K_MG_COARSE 10  /* smoothing, residual and transfers on the coarser levels */
-#define IRK_K_COUNT 11
+#define IRK_K_MG_COARSE 10  /* V-cycle work on coarse levels whose finer grid has >= 513 nodes
+                               per axis (large-tile fused legs)                          */
+#define IRK_K_MG_TAIL 11    /* V-cycle work on the smaller coarse levels (small-tile legs)   */
+#define IRK_K_COUNT 12
 
 typedef struct {
   long long launches;                   /* kernels launched since the last irk_perf_select */

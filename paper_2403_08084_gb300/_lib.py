@@ -56,7 +56,7 @@ class irk_stats(C.Structure):
 
 
 K_CLASSES = ["stage_apply", "jacobi", "residual", "restrict", "prolong", "coarse", "multidot", "axpy",
-             "block_rhs", "other", "mg_coarse"]
+             "block_rhs", "other", "mg_coarse", "mg_tail"]
 _NK = len(K_CLASSES)
 
 

@@ -661,8 +661,10 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2) {
       dv.v[i] = h->opt.omega / bc.v[i][0];
     }
   };
-  // finest-level launches keep their class; every launch on a coarser level is IRK_K_MG_COARSE
-  auto cls = [&](const Level& Lv, int fine_class) { return (&Lv == &h->lev[0]) ? fine_class : IRK_K_MG_COARSE; };
+  // finest-level launches keep their class; launches on a coarser level are IRK_K_MG_COARSE (large
+  // levels) or IRK_K_MG_TAIL
+  auto coarse_cls = [&](const Level& Lv) { return Lv.nx >= kMgLargeNx ? IRK_K_MG_COARSE : IRK_K_MG_TAIL; };
+  auto cls = [&](const Level& Lv, int fine_class) { return (&Lv == &h->lev[0]) ? fine_class : coarse_cls(Lv); };
   // FP32 / BF16, 2D: the finest level forms its stencil from per-cell kappa
   constexpr bool f32c = std::is_same<C, float>::value;
   auto use_kappa = [&](const Level& Lv) { return f32c && !d3 && &Lv == &h->lev[0]; };
@@ -710,7 +712,7 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2) {
     if (fused_leg(l)) {
       const double n = interior(Lv), nc = interior(Lc);
       const bool rec = P::rec(Lv) != nullptr;
-      KScope k(h, IRK_K_MG_COARSE, n * S * (2 * p + c) + n * kCoef2 * c * (rec ? S : 1) + nc * S * p,
+      KScope k(h, coarse_cls(Lv), n * S * (2 * p + c) + n * kCoef2 * c * (rec ? S : 1) + nc * S * p,
                n * S * (rec ? 42.0 : 66.0));
       MG::down_leg(S, st, Lv.nx, cf, Lv.hm, sig, rec_of(Lv), Lv.nn * kCoef2, dinv, s, bl, (T*)Lv.xa, Lc.nx,
                    (T*)Lc.b);
@@ -817,7 +819,7 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2) {
     if (fused_leg(l)) {
       T* xo = (cur[l] == (T*)Lv.xa) ? (T*)Lv.xb : (T*)Lv.xa;
       const bool rec = P::rec(Lv) != nullptr;
-      KScope k(h, IRK_K_MG_COARSE, nf * S * (4 * p + c) + nf * kCoef2 * c * (rec ? S : 1) + nc * S * p,
+      KScope k(h, coarse_cls(Lv), nf * S * (4 * p + c) + nf * kCoef2 * c * (rec ? S : 1) + nc * S * p,
                nf * S * (rec ? 45.0 : 69.0));
       MG::up_leg(S, st, Lv.nx, cf, Lv.hm, sig, rec_of(Lv), Lv.nn * kCoef2, dinv, s, cur[l], bfine, Lc.nx,
                  cur[l + 1], xo);

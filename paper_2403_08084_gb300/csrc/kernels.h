@@ -53,6 +53,10 @@ struct MG2 {
                      T* xout);
 };
 
+// Coarse levels whose finer grid has at least this many nodes per axis run the fused V-cycle legs
+// on large tiles (and count as IRK_K_MG_COARSE); smaller ones use small tiles (IRK_K_MG_TAIL).
+constexpr int kMgLargeNx = 513;
+
 // Finest-level 2D kernels forming the stencil from per-cell kappa (mg2d_kappa.cuh);
 // instantiated for the FP32 and BF16 V-cycles.
 template <typename T, typename C>

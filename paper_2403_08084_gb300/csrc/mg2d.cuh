@@ -150,22 +150,35 @@ __global__ void __launch_bounds__(kBX* kBY) restrict_kernel(int nxf, const T* __
   }
 }
 
-// x_f += P e_c: bilinear interpolation.  With I0 = ix >> 1, I1 = (ix + 1) >> 1 (equal
-// for even ix) the average of the four corner values is the interpolant.
+// x_f += P e_c: bilinear interpolation.  Each thread takes the fine nodes ix (odd) and ix + 1 (even)
+// of one row, between coarse columns I0 = ix >> 1 and I1 = I0 + 1.  Per parity the interpolant is
+// E (even, even), the mean of two coarse values (one odd index) or of four (both odd); written that
+// way it is bit-for-bit the four-corner average with repeated corners, in under half the operations.
 template <typename T, typename C, int S>
 __global__ void __launch_bounds__(kBX* kBY) prolong_add_kernel(int nxc, const T* __restrict__ ec, int nxf,
                                                                T* __restrict__ xf) {
   IRK_PDL_ENTRY;
-  const int ix = 1 + blockIdx.x * kBX + threadIdx.x;
+  const int ix = 1 + 2 * (blockIdx.x * kBX + threadIdx.x);  // odd
   const int iy = 1 + blockIdx.y * kBY + threadIdx.y;
   if (ix > nxf - 2 || iy > nxf - 2) return;
-  const int I0 = ix >> 1, I1 = (ix + 1) >> 1, J0 = iy >> 1, J1 = (iy + 1) >> 1;
+  const bool two = ix + 1 <= nxf - 2;
+  const int I0 = ix >> 1, I1 = I0 + 1, J0 = iy >> 1, J1 = (iy + 1) >> 1;
   const int p = ix + nxf * iy;
 #pragma unroll
   for (int i = 0; i < S; ++i) {
     auto E = [&](int I, int J) { return ld<C>(ec + (size_t)(I + nxc * J) * S + i); };
-    C v = C(0.25) * ((E(I0, J0) + E(I1, J0)) + (E(I0, J1) + E(I1, J1)));
-    st(xf + (size_t)p * S + i, ld<C>(xf + (size_t)p * S + i) + v);
+    C v_odd, v_even;
+    if (J0 == J1) {
+      const C a = E(I0, J0), b = E(I1, J0);
+      v_odd = C(0.5) * (a + b);
+      v_even = b;
+    } else {
+      const C b0 = E(I1, J0), b1 = E(I1, J1);
+      v_odd = C(0.25) * ((E(I0, J0) + b0) + (E(I0, J1) + b1));
+      v_even = C(0.5) * (b0 + b1);
+    }
+    st(xf + (size_t)p * S + i, ld<C>(xf + (size_t)p * S + i) + v_odd);
+    if (two) st(xf + (size_t)(p + 1) * S + i, ld<C>(xf + (size_t)(p + 1) * S + i) + v_even);
   }
 }
 
@@ -189,21 +202,35 @@ __global__ void __launch_bounds__(kBX* kBY) block_rhs_kernel(int nx, const C* __
   st(out + p, acc);
 }
 
-// IA form: out = v_i - sum_j cj[j] M z_j (M: the level's Q1 mass stencil, scale hm).
+// IA form: out = v_i - sum_j cj[j] M z_j (M: the level's Q1 mass stencil; cjh = cj h^2 / 36).
+// The mass stencil is separable, [1 4 1] (x) [1 4 1]: each thread takes two vertically adjacent
+// interior nodes and shares the row sums of rows iy - 1 .. iy + 2 between them.
 template <typename T, typename C, int SF>
-__global__ void __launch_bounds__(kBX* kBY) block_rhs_mass_kernel(int nx, C hm, const double* __restrict__ v,
-                                                                  const double* __restrict__ z, int i, VecT<C> cj,
+__global__ void __launch_bounds__(kBX* kBY) block_rhs_mass_kernel(int nx, const double* __restrict__ v,
+                                                                  const double* __restrict__ z, int i, VecT<C> cjh,
                                                                   unsigned used, T* __restrict__ out) {
   IRK_PDL_ENTRY;
   const int ix = 1 + blockIdx.x * kBX + threadIdx.x;
-  const int iy = 1 + blockIdx.y * kBY + threadIdx.y;
-  if (ix > nx - 2 || iy > nx - 2) return;
-  const int p = ix + nx * iy;
-  C acc = static_cast<C>(v[(size_t)p * SF + i]);
+  const int iy0 = 1 + 2 * (blockIdx.y * kBY + threadIdx.y);
+  if (ix > nx - 2 || iy0 > nx - 2) return;
+  const bool two = iy0 + 1 <= nx - 2;
+  const int p0 = ix + nx * iy0;
+  C acc0 = static_cast<C>(v[(size_t)p0 * SF + i]);
+  C acc1 = two ? static_cast<C>(v[(size_t)(p0 + nx) * SF + i]) : C(0);
 #pragma unroll
-  for (int j = 0; j < SF; ++j)
-    if (used & (1u << j)) acc -= cj.v[j] * hm * m_apply_unscaled<SF, C>(z, p, nx, j);
-  st(out + p, acc);
+  for (int j = 0; j < SF; ++j) {
+    if (!(used & (1u << j))) continue;
+    auto row = [&](int q) {
+      return fma(C(4), ld<C>(z + (size_t)q * SF + j), ld<C>(z + (size_t)(q - 1) * SF + j)) +
+             ld<C>(z + (size_t)(q + 1) * SF + j);
+    };
+    const C r_m = row(p0 - nx), r_0 = row(p0), r_1 = row(p0 + nx);
+    const C r_2 = (iy0 + 2 <= nx - 1) ? row(p0 + 2 * nx) : C(0);
+    acc0 -= cjh.v[j] * (fma(C(4), r_0, r_m) + r_1);
+    acc1 -= cjh.v[j] * (fma(C(4), r_1, r_0) + r_2);
+  }
+  st(out + p0, acc0);
+  if (two) st(out + p0 + nx, acc1);
 }
 
 // z[:, i] = scale * x on interior nodes (single-stage x into an SF-interleaved double vector).
@@ -339,7 +366,8 @@ void MG2<T, C>::restrict_(int S, cudaStream_t st, int nxf, const T* rf, int nxc,
 }
 template <typename T, typename C>
 void MG2<T, C>::prolong_add(int S, cudaStream_t st, int nxc, const T* ec, int nxf, T* xf) {
-  dim3 g = interior_grid(nxf), blk(kBX, kBY);
+  const int m = nxf - 2;
+  dim3 g(((m + 1) / 2 + kBX - 1) / kBX, (m + kBY - 1) / kBY), blk(kBX, kBY);  // two nodes per thread in x
   IRK_DISPATCH_S(S, launch_k(prolong_add_kernel<T, C, SS>, g, blk, 0, st, nxc, ec, nxf, xf));
 }
 template <typename T, typename C>
@@ -360,12 +388,16 @@ void MG2<T, C>::scatter_stage(int SF, cudaStream_t st, int nx, const T* x, int i
 template <typename T, typename C>
 void MG2<T, C>::block_rhs_mass(int SF, cudaStream_t st, int nx, double hm, const double* v, const double* z, int i,
                                const Vec8& cj, T* out) {
-  dim3 g = interior_grid(nx), blk(kBX, kBY);
+  const int m = nx - 2;
+  dim3 g((m + kBX - 1) / kBX, ((m + 1) / 2 + kBY - 1) / kBY), blk(kBX, kBY);  // two rows per thread
   unsigned used = 0;
-  for (int j = 0; j < SF; ++j)
+  Vec8 cjh{};
+  for (int j = 0; j < SF; ++j) {
     if (cj.v[j] != 0.0) used |= 1u << j;
-  const VecT<C> c = to_vec<C>(cj);
-  IRK_DISPATCH_S(SF, launch_k(block_rhs_mass_kernel<T, C, SS>, g, blk, 0, st, nx, (C)hm, v, z, i, c, used, out));
+    cjh.v[j] = cj.v[j] * hm;
+  }
+  const VecT<C> c = to_vec<C>(cjh);
+  IRK_DISPATCH_S(SF, launch_k(block_rhs_mass_kernel<T, C, SS>, g, blk, 0, st, nx, v, z, i, c, used, out));
 }
 template <typename T, typename C>
 void MG2<T, C>::cast_to(cudaStream_t st, const double* src, T* dst, size_t n) {

@@ -261,10 +261,10 @@ void launch_up_leg(cudaStream_t st, int nxf, const BlockOp<C, REC>& op, const C*
   launch_k(kern, g, dim3(NT), smem, st, nxf, op, dinv, dstride, xin, b, nxc, ec, xout);
 }
 
-// Levels whose fine grid has at least this many nodes per axis use the large tiles (fewer halo
+// Levels whose fine grid has at least kMgLargeNx nodes per axis use the large tiles (fewer halo
 // nodes per owned node, for the arithmetic-bound FP64 legs); smaller levels use 8 x 8 owned nodes
 // per block so that each phase is one round of loads and there are many blocks in flight.
-constexpr int kLegLargeNx = 513;
+constexpr int kLegLargeNx = kMgLargeNx;
 
 template <typename T, typename C, int S, bool REC>
 void down_leg_s(cudaStream_t st, int nxf, const BlockOp<C, REC>& op, const C* dinv, int dstride, const T* b, T* xout,

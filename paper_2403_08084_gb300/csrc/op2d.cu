@@ -35,6 +35,45 @@ __device__ __forceinline__ double k_apply_masked(const double* __restrict__ cf, 
 }
 }  // namespace
 
+// The Q1 mass stencil is separable: 36/h^2 M = [1 4 1] (x) [1 4 1].  The stage-operator kernels
+// give each thread two vertically adjacent nodes, so the four row sums x_w + 4 x_c + x_e of rows
+// iy - 1 .. iy + 2 serve both: 6 FP64 operations per node and stage instead of 10 (on GB300 the
+// FP64 pipe, not memory, bounds these kernels).
+template <int S>
+__device__ __forceinline__ double row_sum(const double* __restrict__ x, int q, int j) {
+  return fma(4.0, x[(size_t)q * S + j], x[(size_t)(q - 1) * S + j]) + x[(size_t)(q + 1) * S + j];
+}
+
+// Node pair (ix, iy0), (ix, iy0 + 1) of a thread; both rows exist unless iy0 = nx - 1.
+struct NodePair {
+  int ix, iy0, p0;
+  bool two, in0, in1;
+  __device__ NodePair(int nx) {
+    ix = blockIdx.x * BX + threadIdx.x;
+    iy0 = 2 * (blockIdx.y * BY + threadIdx.y);
+    p0 = ix + nx * iy0;
+    two = iy0 + 1 < nx;
+    const bool col = ix >= 1 && ix <= nx - 2;
+    in0 = col && iy0 >= 1 && iy0 <= nx - 2;
+    in1 = two && col && iy0 + 1 <= nx - 2;
+  }
+};
+
+// Unscaled mass stencil of stage j at both nodes of the pair (only called when a node is interior,
+// so column ix is interior and rows iy0 - 1 .. iy0 + 2 that exist are in range).
+template <int S>
+__device__ __forceinline__ void mass_pair(const double* __restrict__ x, const NodePair& q, int nx, int j, double& m0,
+                                          double& m1) {
+  const double r_m = (q.iy0 >= 1) ? row_sum<S>(x, q.p0 - nx, j) : 0.0;
+  const double r_0 = row_sum<S>(x, q.p0, j);
+  const double r_1 = q.two ? row_sum<S>(x, q.p0 + nx, j) : 0.0;
+  const double r_2 = (q.iy0 + 2 < nx) ? row_sum<S>(x, q.p0 + 2 * nx, j) : 0.0;
+  m0 = fma(4.0, r_0, r_m) + r_1;
+  m1 = fma(4.0, r_1, r_0) + r_2;
+}
+
+inline dim3 pair_grid(int nx) { return dim3((nx + BX - 1) / BX, ((nx + 1) / 2 + BY - 1) / BY); }
+
 // y_i = M x_i + sum_j mix_ij K x_j (mix = dt A or dt A^T) on interior nodes, 0 on the boundary.
 // One load of the S interleaved values per stencil point serves every stage; the
 // S x S mixing stays in registers.
@@ -42,51 +81,67 @@ template <int S>
 __global__ void __launch_bounds__(BX* BY) stage_apply_kernel(int nx, const double* __restrict__ cf, double hm, Mat4 mix,
                                                              const double* __restrict__ x, double* __restrict__ y) {
   IRK_PDL_ENTRY;
-  const int ix = blockIdx.x * BX + threadIdx.x;
-  const int iy = blockIdx.y * BY + threadIdx.y;
-  if (ix >= nx || iy >= nx) return;
-  const int p = ix + nx * iy;
-  if (!interior2(ix, iy, nx)) {
+  const NodePair q(nx);
+  if (q.ix >= nx || q.iy0 >= nx) return;
+  const bool in[2] = {q.in0, q.in1};
+  double mx[2][S];
+  if (q.in0 || q.in1) {
 #pragma unroll
-    for (int i = 0; i < S; ++i) y[(size_t)p * S + i] = 0.0;
-    return;
+    for (int j = 0; j < S; ++j) mass_pair<S>(x, q, nx, j, mx[0][j], mx[1][j]);
   }
-  double kx[S];
 #pragma unroll
-  for (int j = 0; j < S; ++j) kx[j] = k_apply<S, double>(cf, x, p, nx, j);
+  for (int r = 0; r < 2; ++r) {
+    if (r == 1 && !q.two) break;
+    const int p = q.p0 + r * nx;
+    if (!in[r]) {
 #pragma unroll
-  for (int i = 0; i < S; ++i) {
-    double acc = hm * m_apply_unscaled<S, double>(x, p, nx, i);
+      for (int i = 0; i < S; ++i) y[(size_t)p * S + i] = 0.0;
+      continue;
+    }
+    double kx[S];
 #pragma unroll
-    for (int j = 0; j < S; ++j) acc += mix.v[i * S + j] * kx[j];
-    y[(size_t)p * S + i] = acc;
+    for (int j = 0; j < S; ++j) kx[j] = k_apply<S, double>(cf, x, p, nx, j);
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      double acc = hm * mx[r][i];
+#pragma unroll
+      for (int j = 0; j < S; ++j) acc += mix.v[i * S + j] * kx[j];
+      y[(size_t)p * S + i] = acc;
+    }
   }
 }
 
-// IA form (Sec. 3, eq. block_struct_IA): y_i = sum_j mixM_ij M x_j + dt K x_i (mixM = A^{-1} or A^{-T}).
+// IA form (Sec. 3, eq. block_struct_IA): y_i = sum_j mixM_ij M x_j + dt K x_i (mixM = A^{-1} or A^{-T},
+// passed already multiplied by the mass scale h^2 / 36).
 template <int S>
-__global__ void __launch_bounds__(BX* BY) stage_apply_ia_kernel(int nx, const double* __restrict__ cf, double hm,
-                                                                Mat4 mixM, double dt, const double* __restrict__ x,
+__global__ void __launch_bounds__(BX* BY) stage_apply_ia_kernel(int nx, const double* __restrict__ cf, Mat4 mixMh,
+                                                                double dt, const double* __restrict__ x,
                                                                 double* __restrict__ y) {
   IRK_PDL_ENTRY;
-  const int ix = blockIdx.x * BX + threadIdx.x;
-  const int iy = blockIdx.y * BY + threadIdx.y;
-  if (ix >= nx || iy >= nx) return;
-  const int p = ix + nx * iy;
-  if (!interior2(ix, iy, nx)) {
+  const NodePair q(nx);
+  if (q.ix >= nx || q.iy0 >= nx) return;
+  const bool in[2] = {q.in0, q.in1};
+  double mx[2][S];
+  if (q.in0 || q.in1) {
 #pragma unroll
-    for (int i = 0; i < S; ++i) y[(size_t)p * S + i] = 0.0;
-    return;
+    for (int j = 0; j < S; ++j) mass_pair<S>(x, q, nx, j, mx[0][j], mx[1][j]);
   }
-  double mx[S];
 #pragma unroll
-  for (int j = 0; j < S; ++j) mx[j] = hm * m_apply_unscaled<S, double>(x, p, nx, j);
+  for (int r = 0; r < 2; ++r) {
+    if (r == 1 && !q.two) break;
+    const int p = q.p0 + r * nx;
+    if (!in[r]) {
 #pragma unroll
-  for (int i = 0; i < S; ++i) {
-    double acc = dt * k_apply<S, double>(cf, x, p, nx, i);
+      for (int i = 0; i < S; ++i) y[(size_t)p * S + i] = 0.0;
+      continue;
+    }
 #pragma unroll
-    for (int j = 0; j < S; ++j) acc += mixM.v[i * S + j] * mx[j];
-    y[(size_t)p * S + i] = acc;
+    for (int i = 0; i < S; ++i) {
+      double acc = dt * k_apply<S, double>(cf, x, p, nx, i);
+#pragma unroll
+      for (int j = 0; j < S; ++j) acc += mixMh.v[i * S + j] * mx[r][j];
+      y[(size_t)p * S + i] = acc;
+    }
   }
 }
 
@@ -289,11 +344,13 @@ __global__ void cell_gradient_kernel(int N, const double* __restrict__ kappa, co
 
 void launch_stage_apply(int S, cudaStream_t st, int nx, const double* cf, double hm, const Mat4& mix, const double* x,
                         double* y) {
-  IRK_DISPATCH_S(S, launch_k(stage_apply_kernel<SS>, all_nodes_grid(nx), dim3(BX, BY), 0, st, nx, cf, hm, mix, x, y));
+  IRK_DISPATCH_S(S, launch_k(stage_apply_kernel<SS>, pair_grid(nx), dim3(BX, BY), 0, st, nx, cf, hm, mix, x, y));
 }
 void launch_stage_apply_ia(int S, cudaStream_t st, int nx, const double* cf, double hm, const Mat4& mixM, double dt,
                            const double* x, double* y) {
-  IRK_DISPATCH_S(S, launch_k(stage_apply_ia_kernel<SS>, all_nodes_grid(nx), dim3(BX, BY), 0, st, nx, cf, hm, mixM, dt, x, y));
+  Mat4 mixMh = mixM;
+  for (int e = 0; e < S * S; ++e) mixMh.v[e] *= hm;
+  IRK_DISPATCH_S(S, launch_k(stage_apply_ia_kernel<SS>, pair_grid(nx), dim3(BX, BY), 0, st, nx, cf, mixMh, dt, x, y));
 }
 void launch_stage_mix(int S, cudaStream_t st, size_t nodes, const Mat4& mix, const double* in, double* out) {
   int blocks = (int)std::min<size_t>((nodes + 255) / 256, 152 * 8);
