@@ -68,7 +68,8 @@ struct Level {
   double* cf_d = nullptr;     // stencil records, double
   float* cf_f = nullptr;      // stencil records, float
   double* brec_d = nullptr;   // FP64 V-cycles: records of M + dt a_ii K, stage-major
-  double* dinv_d = nullptr;   // omega / diag, s per node
+  float* brec_f = nullptr;    // FP32 / BF16 V-cycles: the same records in FP32
+  double* dinv_d = nullptr;   // omega / diag(B_i): node-major (s per node), then stage-major (nn per stage)
   float* dinv_f = nullptr;
   void* xa = nullptr;         // V-cycle vectors (s per node, V-cycle precision)
   void* xb = nullptr;
@@ -100,7 +101,6 @@ struct irk_handle {
   double* binv_d = nullptr;
   float* binv_f = nullptr;
   double* kappa_d = nullptr;
-  float* kappa_f = nullptr;  // 2D: per-cell kappa for the FP32 / BF16 finest-level kernels
   // Krylov space
   size_t ne = 0;  // entries of a stage vector
   int m = 0;
@@ -401,15 +401,22 @@ int build_operators(irk_handle* h) {
       galerkin_coarsen_2d(h->lev[l - 1].N, h->lev[l - 1].cf_host, Lv.cf_host);
     std::vector<double> dinv;
     jacobi_inverse_diag_2d(Lv.N, Lv.cf_host, Lv.hm, sigma.data(), s, h->opt.omega, dinv);
+    // the same values stage-major, for the one-block-at-a-time V-cycles of the triangular sweeps
+    dinv.resize(2 * Lv.nn * s);
+    for (size_t q = 0; q < Lv.nn; ++q)
+      for (int i = 0; i < s; ++i) dinv[Lv.nn * s + (size_t)i * Lv.nn + q] = dinv[q * s + i];
     std::vector<float> cff(Lv.cf_host.begin(), Lv.cf_host.end()), dinvf(dinv.begin(), dinv.end());
     CK(cudaMemcpyAsync(Lv.cf_d, Lv.cf_host.data(), Lv.cf_host.size() * 8, cudaMemcpyHostToDevice, h->st));
     CK(cudaMemcpyAsync(Lv.dinv_d, dinv.data(), dinv.size() * 8, cudaMemcpyHostToDevice, h->st));
     CK(cudaMemcpyAsync(Lv.cf_f, cff.data(), cff.size() * 4, cudaMemcpyHostToDevice, h->st));
     CK(cudaMemcpyAsync(Lv.dinv_f, dinvf.data(), dinvf.size() * 4, cudaMemcpyHostToDevice, h->st));
     std::vector<double> brec;
-    if (Lv.brec_d) {
-      block_records_2d(Lv.N, Lv.cf_host, Lv.hm, sigma.data(), s, brec);
-      CK(cudaMemcpyAsync(Lv.brec_d, brec.data(), brec.size() * 8, cudaMemcpyHostToDevice, h->st));
+    std::vector<float> brecf;
+    if (Lv.brec_d || Lv.brec_f) block_records_2d(Lv.N, Lv.cf_host, Lv.hm, sigma.data(), s, brec);
+    if (Lv.brec_d) CK(cudaMemcpyAsync(Lv.brec_d, brec.data(), brec.size() * 8, cudaMemcpyHostToDevice, h->st));
+    if (Lv.brec_f) {
+      brecf.assign(brec.begin(), brec.end());
+      CK(cudaMemcpyAsync(Lv.brec_f, brecf.data(), brecf.size() * 4, cudaMemcpyHostToDevice, h->st));
     }
     CK(cudaStreamSynchronize(h->st));  // host vectors above go out of scope
   }
@@ -430,9 +437,6 @@ int build_operators(irk_handle* h) {
   CK(cudaMemcpyAsync(h->binv_f, allf.data(), allf.size() * 4, cudaMemcpyHostToDevice, h->st));
   if (!h->kappa.empty())
     CK(cudaMemcpyAsync(h->kappa_d, h->kappa.data(), h->kappa.size() * 8, cudaMemcpyHostToDevice, h->st));
-  std::vector<float> kf((size_t)h->N * h->N, 1.0f);
-  if (!h->kappa.empty()) std::copy(h->kappa.begin(), h->kappa.end(), kf.begin());
-  CK(cudaMemcpyAsync(h->kappa_f, kf.data(), kf.size() * 4, cudaMemcpyHostToDevice, h->st));
   CK(cudaStreamSynchronize(h->st));
   return IRK_OK;
 }
@@ -440,10 +444,10 @@ int build_operators(irk_handle* h) {
 void destroy(irk_handle* h) {
   if (!h) return;
   for (Level& Lv : h->lev) {
-    dfree(Lv.cf_d), dfree(Lv.cf_f), dfree(Lv.brec_d), dfree(Lv.dinv_d), dfree(Lv.dinv_f);
+    dfree(Lv.cf_d), dfree(Lv.cf_f), dfree(Lv.brec_d), dfree(Lv.brec_f), dfree(Lv.dinv_d), dfree(Lv.dinv_f);
     dfree(Lv.xa), dfree(Lv.xb), dfree(Lv.b), dfree(Lv.r);
   }
-  dfree(h->cmap), dfree(h->binv_d), dfree(h->binv_f), dfree(h->kappa_d), dfree(h->kappa_f);
+  dfree(h->cmap), dfree(h->binv_d), dfree(h->binv_f), dfree(h->kappa_d);
   dfree(h->V), dfree(h->Z), dfree(h->H), dfree(h->cs), dfree(h->sn), dfree(h->g), dfree(h->y);
   dfree(h->h1), dfree(h->h2), dfree(h->partial), dfree(h->scal), dfree(h->iflag);
   dfree(h->rhs), dfree(h->k), dfree(h->tmp), dfree(h->bnd);
@@ -543,9 +547,11 @@ int create(irk_handle** out, const irk_mesh* mesh, const irk_tableau* tab, doubl
     Lv.hm = hh * hh / 36.0;
     int r = IRK_OK;
     if (dim == 2) {  // stencil records (3D uses constant class values instead)
+      // records of each diagonal block B_i = M + dt a_ii K, in the V-cycle's arithmetic precision
       if (opt->vcycle_prec == IRK_PREC_FP64 && (r = dalloc(&Lv.brec_d, Lv.nn * kCoef2 * s * 8))) return bail(r);
+      if (opt->vcycle_prec != IRK_PREC_FP64 && (r = dalloc(&Lv.brec_f, Lv.nn * kCoef2 * s * 4))) return bail(r);
       if ((r = dalloc(&Lv.cf_d, Lv.nn * kCoef2 * 8)) || (r = dalloc(&Lv.cf_f, Lv.nn * kCoef2 * 4)) ||
-          (r = dalloc(&Lv.dinv_d, Lv.nn * s * 8)) || (r = dalloc(&Lv.dinv_f, Lv.nn * s * 4)))
+          (r = dalloc(&Lv.dinv_d, Lv.nn * s * 2 * 8)) || (r = dalloc(&Lv.dinv_f, Lv.nn * s * 2 * 4)))
         return bail(r);
     }
     if ((r = dalloc(&Lv.xa, Lv.nn * s * vb)) || (r = dalloc(&Lv.xb, Lv.nn * s * vb)) ||
@@ -562,8 +568,7 @@ int create(irk_handle** out, const irk_mesh* mesh, const irk_tableau* tab, doubl
   if ((r = dalloc(&h->cmap, (size_t)h->nint * sizeof(int))) ||
       (r = dalloc(&h->binv_d, (size_t)s * h->nint * h->nint * 8)) ||
       (r = dalloc(&h->binv_f, (size_t)s * h->nint * h->nint * 4)) ||
-      (r = dalloc(&h->kappa_d, dim == 2 ? (size_t)h->N * h->N * 8 : 16)) ||
-      (dim == 2 && (r = dalloc(&h->kappa_f, (size_t)h->N * h->N * 4))))
+      (r = dalloc(&h->kappa_d, dim == 2 ? (size_t)h->N * h->N * 8 : 16)))
     return bail(r);
   h->ne = h->lev[0].nn * s;
   h->m = opt->restart;
@@ -621,14 +626,14 @@ struct Prec<double, double> {
 };
 template <>
 struct Prec<float, float> {
-  static const float* rec(const Level&) { return nullptr; }
+  static const float* rec(const Level& L) { return L.brec_f; }
   static const float* cf(const Level& L) { return L.cf_f; }
   static const float* dinv(const Level& L) { return L.dinv_f; }
   static const float* binv(const irk_handle* h) { return h->binv_f; }
 };
 template <>
 struct Prec<__nv_bfloat16, float> {
-  static const float* rec(const Level&) { return nullptr; }
+  static const float* rec(const Level& L) { return L.brec_f; }
   static const float* cf(const Level& L) { return L.cf_f; }
   static const float* dinv(const Level& L) { return L.dinv_f; }
   static const float* binv(const irk_handle* h) { return h->binv_f; }
@@ -665,19 +670,14 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2) {
   // levels) or IRK_K_MG_TAIL
   auto coarse_cls = [&](const Level& Lv) { return Lv.nx >= kMgLargeNx ? IRK_K_MG_COARSE : IRK_K_MG_TAIL; };
   auto cls = [&](const Level& Lv, int fine_class) { return (&Lv == &h->lev[0]) ? fine_class : coarse_cls(Lv); };
-  // FP32 / BF16, 2D: the finest level forms its stencil from per-cell kappa
-  constexpr bool f32c = std::is_same<C, float>::value;
-  auto use_kappa = [&](const Level& Lv) { return f32c && !d3 && &Lv == &h->lev[0]; };
+  // Jacobi diagonal: one block (S == 1) reads the stage-major copy, batched blocks the node-major one
+  const int s_d = (S == 1) ? 1 : s;
+  auto dinv_of = [&](const Level& Lv) {
+    return S == 1 ? P::dinv(Lv) + (size_t)Lv.nn * s + (size_t)st0 * Lv.nn : P::dinv(Lv) + st0;
+  };
   auto sweep = [&](Level& Lv, const C* cf, const C* dinv, const T* xin, const T* b, T* xout) {
     const double n = interior(Lv);
     const int kj = cls(Lv, IRK_K_JACOBI);
-    if constexpr (f32c) {
-      if (use_kappa(Lv)) {
-        KScope k(h, kj, n * S * (xin ? 3 : 2) * p + n * 4.0, (xin ? 40.0 : 4.0) * n * S);
-        MG2K<T, C>::jacobi(S, st, Lv.nx, (const C*)h->kappa_f, Lv.hm, sig, h->opt.omega, xin, b, xout, 0);
-        return;
-      }
-    }
     if (d3) {
       Cls4 bc{};
       Vec8 dv{};
@@ -689,13 +689,13 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2) {
     const C* rec = P::rec(Lv);
     if (xin == nullptr) {
       KScope k(h, kj, n * S * (2 * p + c), n * S);
-      MG::jacobi(S, st, Lv.nx, cf, Lv.hm, sig, dinv, s, xin, b, xout);
+      MG::jacobi(S, st, Lv.nx, cf, Lv.hm, sig, dinv, s_d, xin, b, xout);
     } else if (rec != nullptr) {  // B_i records: 9 products + 2 per node and stage
       KScope k(h, kj, n * S * (3 * p + c + kCoef2 * c), 20.0 * n * S);
-      MG::jacobi_rec(S, st, Lv.nx, rec + (size_t)st0 * Lv.nn * kCoef2, Lv.nn * kCoef2, dinv, s, xin, b, xout);
+      MG::jacobi_rec(S, st, Lv.nx, rec + (size_t)st0 * Lv.nn * kCoef2, Lv.nn * kCoef2, dinv, s_d, xin, b, xout);
     } else {
       KScope k(h, kj, n * (S * (3 * p + c) + kCoef2 * c), 33.0 * n * S);
-      MG::jacobi(S, st, Lv.nx, cf, Lv.hm, sig, dinv, s, xin, b, xout);
+      MG::jacobi(S, st, Lv.nx, cf, Lv.hm, sig, dinv, s_d, xin, b, xout);
     }
   };
   // 2D coarse levels under V(2, 2): one fused kernel per leg (mg2d_legs.cuh) instead of six launches
@@ -708,13 +708,13 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2) {
     Level& Lv = h->lev[l];
     Level& Lc = h->lev[l + 1];
     const C* cf = d3 ? nullptr : P::cf(Lv);
-    const C* dinv = d3 ? nullptr : P::dinv(Lv) + st0;
+    const C* dinv = d3 ? nullptr : dinv_of(Lv);
     if (fused_leg(l)) {
       const double n = interior(Lv), nc = interior(Lc);
       const bool rec = P::rec(Lv) != nullptr;
       KScope k(h, coarse_cls(Lv), n * S * (2 * p + c) + n * kCoef2 * c * (rec ? S : 1) + nc * S * p,
                n * S * (rec ? 42.0 : 66.0));
-      MG::down_leg(S, st, Lv.nx, cf, Lv.hm, sig, rec_of(Lv), Lv.nn * kCoef2, dinv, s, bl, (T*)Lv.xa, Lc.nx,
+      MG::down_leg(S, st, Lv.nx, cf, Lv.hm, sig, rec_of(Lv), Lv.nn * kCoef2, dinv, s_d, bl, (T*)Lv.xa, Lc.nx,
                    (T*)Lc.b);
       cur[l] = (T*)Lv.xa;
       bl = (const T*)Lc.b;
@@ -736,15 +736,7 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2) {
     int k0 = 1;
     if (fuse2) {
       const double n = interior(Lv);
-      if constexpr (f32c) {
-        if (use_kappa(Lv)) {
-          KScope kk(h, cls(Lv, IRK_K_JACOBI), n * S * 2 * p + n * 4.0, 60.0 * n * S);
-          MG2K<T, C>::jacobi(S, st, Lv.nx, (const C*)h->kappa_f, Lv.hm, sig, h->opt.omega, nullptr, bl, bufs[1], 1);
-        }
-      }
-      if (use_kappa(Lv)) {
-        // done above
-      } else if (d3) {
+      if (d3) {
         Cls4 bc{};
         Vec8 dv{};
         classes(Lv, bc, dv);
@@ -755,7 +747,7 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2) {
         KScope kk(h, cls(Lv, IRK_K_JACOBI), n * S * (2 * p + c + kCoef2 * c) + (rec ? 0.0 : n * kCoef2 * c),
                   (rec ? 30.0 : 42.0) * n * S);
         MG::jacobi2z(S, st, Lv.nx, cf, Lv.hm, sig, rec ? rec + (size_t)st0 * Lv.nn * kCoef2 : nullptr,
-                     Lv.nn * kCoef2, dinv, s, bl, bufs[1]);
+                     Lv.nn * kCoef2, dinv, s_d, bl, bufs[1]);
       }
       w = 1;
       k0 = 2;
@@ -776,16 +768,7 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2) {
       KScope k(h, cls(Lv, IRK_K_RESTRICT), (nf + nc) * S * p, 30.0 * nc * S);
       MG3T::restrict_(S, st, Lv.nx, (const T*)Lv.r, Lc.nx, (T*)Lc.b);
     } else {
-      bool done = false;
-      if constexpr (f32c) {
-        if (use_kappa(Lv)) {
-          KScope k(h, cls(Lv, IRK_K_RESIDUAL), nf * S * 3 * p + nf * 4.0, 36.0 * nf * S);
-          MG2K<T, C>::residual(S, st, Lv.nx, (const C*)h->kappa_f, Lv.hm, sig, cur[l], bl, (T*)Lv.r);
-          done = true;
-        }
-      }
-      if (done) {
-      } else if (const C* rec = P::rec(Lv)) {
+      if (const C* rec = P::rec(Lv)) {
         KScope k(h, cls(Lv, IRK_K_RESIDUAL), nf * S * (3 * p + kCoef2 * c), 18.0 * nf * S);
         MG::residual_rec(S, st, Lv.nx, rec + (size_t)st0 * Lv.nn * kCoef2, Lv.nn * kCoef2, cur[l], bl, (T*)Lv.r);
       } else {
@@ -813,7 +796,7 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2) {
     Level& Lv = h->lev[l];
     Level& Lc = h->lev[l + 1];
     const C* cf = d3 ? nullptr : P::cf(Lv);
-    const C* dinv = d3 ? nullptr : P::dinv(Lv) + st0;
+    const C* dinv = d3 ? nullptr : dinv_of(Lv);
     const T* bfine = (l == 0) ? b0 : (const T*)Lv.b;
     const double nf = interior(Lv), nc = interior(Lc);
     if (fused_leg(l)) {
@@ -821,7 +804,7 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2) {
       const bool rec = P::rec(Lv) != nullptr;
       KScope k(h, coarse_cls(Lv), nf * S * (4 * p + c) + nf * kCoef2 * c * (rec ? S : 1) + nc * S * p,
                nf * S * (rec ? 45.0 : 69.0));
-      MG::up_leg(S, st, Lv.nx, cf, Lv.hm, sig, rec_of(Lv), Lv.nn * kCoef2, dinv, s, cur[l], bfine, Lc.nx,
+      MG::up_leg(S, st, Lv.nx, cf, Lv.hm, sig, rec_of(Lv), Lv.nn * kCoef2, dinv, s_d, cur[l], bfine, Lc.nx,
                  cur[l + 1], xo);
       cur[l] = xo;
       continue;
@@ -910,8 +893,6 @@ int precond_apply(irk_handle* h, const double* v, double* z, bool transpose) {
         MG::block_rhs_mass(s, st, L0.nx, L0.hm, v, z, i, cj, (T*)L0.b);
       } else if (d3) {
         MG3<T, C>::block_rhs(s, st, L0.nx, kc, v, z, i, cj, (T*)L0.b);
-      } else if constexpr (std::is_same<C, float>::value) {
-        MG2K<T, C>::block_rhs(s, st, L0.nx, (const C*)h->kappa_f, v, z, i, cj, (T*)L0.b);
       } else {
         MG::block_rhs(s, st, L0.nx, cf, v, z, i, cj, (T*)L0.b);
       }

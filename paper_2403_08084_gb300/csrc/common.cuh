@@ -56,35 +56,40 @@ inline VecT<C> to_vec(const Vec8& a) {
 // ----------------------------------------------------------------------------
 // programmatic dependent launch
 // ----------------------------------------------------------------------------
-// Every kernel of the library is launched with programmatic stream serialization
-// and starts with IRK_PDL_ENTRY: it waits until the previous kernel in the stream
-// has completed and its writes are visible (griddepcontrol.wait), then lets the
-// next kernel be scheduled (griddepcontrol.launch_dependents).  The next kernel's
-// launch latency and CTA scheduling thus overlap this kernel's tail, which is
-// most of the cost of the small coarse-level grids.  Without the launch attribute
-// both instructions are no-ops.
+// Every kernel of the library starts with IRK_PDL_ENTRY: it waits until the previous
+// kernel in the stream has completed and its writes are visible (griddepcontrol.wait),
+// then lets the next kernel be scheduled (griddepcontrol.launch_dependents).  A kernel
+// launched with programmatic stream serialization can thus be scheduled while its
+// predecessor finishes, so its launch latency overlaps that kernel's tail, which is
+// most of the cost of the small coarse-level grids.  Without the launch attribute both
+// instructions are no-ops.
 #define IRK_PDL_ENTRY                                      \
   do {                                                     \
     asm volatile("griddepcontrol.wait;" ::: "memory");     \
     asm volatile("griddepcontrol.launch_dependents;" ::);  \
   } while (0)
 
-// The attribute is off unless IRK_PDL=1 is set: measured on GB300 (heat2d-1024-radau3
-// inside CUDA graphs) the steps ran about 4% slower with it than without.
-inline bool pdl_enabled() {
-  static const bool on = [] {
+// Which launches carry the attribute (environment IRK_PDL): none by default; IRK_PDL=1 puts it
+// on the small-level multigrid kernels and the coarsest solve (launch_k_tail), IRK_PDL=2 on every
+// launch.  Measured on GB300 (heat2d-1024-radau3 inside CUDA graphs): on every launch the steps
+// ran about 4% slower (the dependent kernel's blocks sit on SMs that large kernels still need);
+// on the small-level kernels alone it made no difference.
+inline int pdl_mode() {
+  static const int mode = [] {
     const char* e = getenv("IRK_PDL");
-    return e && e[0] == '1';
+    if (e && e[0] == '2') return 2;
+    if (e && e[0] == '1') return 1;
+    return 0;
   }();
-  return on;
+  return mode;
 }
 
 template <typename... KArgs, typename... Args>
-inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
-                     Args&&... args) {
+inline void launch_pdl(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                       Args&&... args) {
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
+  attr[0].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = block;
@@ -93,6 +98,19 @@ inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t sme
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+template <typename... KArgs, typename... Args>
+inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                     Args&&... args) {
+  launch_pdl(pdl_mode() == 2, kernel, grid, block, smem, stream, std::forward<Args>(args)...);
+}
+
+// small-level multigrid kernels and the coarsest solve
+template <typename... KArgs, typename... Args>
+inline void launch_k_tail(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                          Args&&... args) {
+  launch_pdl(pdl_mode() >= 1, kernel, grid, block, smem, stream, std::forward<Args>(args)...);
 }
 
 // ----------------------------------------------------------------------------

@@ -57,18 +57,6 @@ struct MG2 {
 // on large tiles (and count as IRK_K_MG_COARSE); smaller ones use small tiles (IRK_K_MG_TAIL).
 constexpr int kMgLargeNx = 513;
 
-// Finest-level 2D kernels forming the stencil from per-cell kappa (mg2d_kappa.cuh);
-// instantiated for the FP32 and BF16 V-cycles.
-template <typename T, typename C>
-struct MG2K {
-  static void jacobi(int S, cudaStream_t st, int nx, const C* kap, double hm, const Vec8& sigma, double omega,
-                     const T* xin, const T* b, T* xout, int two_from_zero);
-  static void residual(int S, cudaStream_t st, int nx, const C* kap, double hm, const Vec8& sigma, const T* x,
-                       const T* b, T* r);
-  static void block_rhs(int SF, cudaStream_t st, int nx, const C* kap, const double* v, const double* z, int i,
-                        const Vec8& cj, T* out);
-};
-
 // 3D multigrid kernels (mg3d.cuh), constant-coefficient stencils.
 template <typename T, typename C>
 struct MG3 {

@@ -275,10 +275,12 @@ __device__ __forceinline__ int coarse_node(int c, int nxc) {
   return (c % m + 1) + nxc * (c / m + 1);
 }
 
+// Launched with programmatic serialization: the row loads (the inverse is fixed for the handle)
+// are issued before griddepcontrol.wait, so they overlap the previous kernel.
 template <typename T, typename C, int S>
 __global__ void __launch_bounds__(kCoarseThreads) coarse_solve_kernel(int nint, int nxc, const C* __restrict__ binv,
                                                                       const T* __restrict__ b, T* __restrict__ x) {
-  IRK_PDL_ENTRY;
+  asm volatile("griddepcontrol.launch_dependents;" ::);
   extern __shared__ unsigned char smem_raw[];
   C* bs = reinterpret_cast<C*>(smem_raw);
   const int i = blockIdx.y;
@@ -294,6 +296,7 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_solve_kernel(int nint, 
       a[k] = (r < nint && c < nint) ? row[c] : C(0);
     }
     if (c0 == 0) {
+      asm volatile("griddepcontrol.wait;" ::: "memory");  // b is the previous kernel's output
 #pragma unroll 8
       for (int c = threadIdx.x; c < nint; c += kCoarseThreads) bs[c] = ld<C>(b + (size_t)coarse_node(c, nxc) * S + i);
       __syncthreads();
@@ -419,7 +422,7 @@ void MG2<T, C>::coarse_solve(int S, cudaStream_t st, int nxc, const C* binv, con
   const int gx = (nint + kCoarseThreads / 32 - 1) / (kCoarseThreads / 32);  // one warp per row
   dim3 g(gx, S);
   size_t shm = sizeof(C) * (size_t)nint;
-  IRK_DISPATCH_S(S, launch_k(coarse_solve_kernel<T, C, SS>, g, kCoarseThreads, shm, st, nint, nxc, binv, b, x));
+  IRK_DISPATCH_S(S, launch_k_tail(coarse_solve_kernel<T, C, SS>, g, kCoarseThreads, shm, st, nint, nxc, binv, b, x));
 }
 
 }  // namespace irk

@@ -247,7 +247,8 @@ void launch_down_leg(cudaStream_t st, int nxf, const BlockOp<C, REC>& op, const 
   leg_smem_attr(kern, smem);
   const int m = nxf - 2;
   dim3 g((m + 2 * CX - 1) / (2 * CX), (m + 2 * CY - 1) / (2 * CY));
-  launch_k(kern, g, dim3(NT), smem, st, nxf, op, dinv, dstride, b, xout, nxc, bc);
+  launch_pdl(CX < 16 ? pdl_mode() >= 1 : pdl_mode() == 2, kern, g, dim3(NT), smem, st, nxf, op, dinv, dstride, b,
+             xout, nxc, bc);
 }
 
 template <typename T, typename C, int S, int TX, int TY, int NT, bool REC>
@@ -258,7 +259,8 @@ void launch_up_leg(cudaStream_t st, int nxf, const BlockOp<C, REC>& op, const C*
   leg_smem_attr(kern, smem);
   const int m = nxf - 2;
   dim3 g((m + TX - 1) / TX, (m + TY - 1) / TY);
-  launch_k(kern, g, dim3(NT), smem, st, nxf, op, dinv, dstride, xin, b, nxc, ec, xout);
+  launch_pdl(TX < 32 ? pdl_mode() >= 1 : pdl_mode() == 2, kern, g, dim3(NT), smem, st, nxf, op, dinv, dstride, xin,
+             b, nxc, ec, xout);
 }
 
 // Levels whose fine grid has at least kMgLargeNx nodes per axis use the large tiles (fewer halo
@@ -266,11 +268,16 @@ void launch_up_leg(cudaStream_t st, int nxf, const BlockOp<C, REC>& op, const C*
 // per block so that each phase is one round of loads and there are many blocks in flight.
 constexpr int kLegLargeNx = kMgLargeNx;
 
+// Levels with kLegMediumNx <= nxf < kLegLargeNx use 16 x 16 owned nodes per block.
+constexpr int kLegMediumNx = 257;
+
 template <typename T, typename C, int S, bool REC>
 void down_leg_s(cudaStream_t st, int nxf, const BlockOp<C, REC>& op, const C* dinv, int dstride, const T* b, T* xout,
                 int nxc, T* bc) {
   if (nxf >= kLegLargeNx)
     launch_down_leg<T, C, S, 16, 8, 256, REC>(st, nxf, op, dinv, dstride, b, xout, nxc, bc);
+  else if (nxf >= kLegMediumNx)  // regions 21 x 21, 19 x 19, 17 x 17
+    launch_down_leg<T, C, S, 8, 8, 256, REC>(st, nxf, op, dinv, dstride, b, xout, nxc, bc);
   else  // regions 13 x 13, 11 x 11, 9 x 9
     launch_down_leg<T, C, S, 4, 4, 192, REC>(st, nxf, op, dinv, dstride, b, xout, nxc, bc);
 }
@@ -280,6 +287,8 @@ void up_leg_s(cudaStream_t st, int nxf, const BlockOp<C, REC>& op, const C* dinv
               const T* b, int nxc, const T* ec, T* xout) {
   if (nxf >= kLegLargeNx)
     launch_up_leg<T, C, S, 32, 16, 256, REC>(st, nxf, op, dinv, dstride, xin, b, nxc, ec, xout);
+  else if (nxf >= kLegMediumNx)  // regions 20 x 20, 18 x 18, 16 x 16
+    launch_up_leg<T, C, S, 16, 16, 256, REC>(st, nxf, op, dinv, dstride, xin, b, nxc, ec, xout);
   else  // regions 12 x 12, 10 x 10, 8 x 8
     launch_up_leg<T, C, S, 8, 8, 160, REC>(st, nxf, op, dinv, dstride, xin, b, nxc, ec, xout);
 }
