@@ -325,12 +325,14 @@ def gpu_arm(args, rank, world):
         "dtype": "f64" if vcycle == "fp64" else f"f64 outer / {vcycle} V-cycles",
         "data": "synthetic",
         "config": {"workload": wl.name, "mesh": "x".join([str(wl.N)] * wl.dim) + " Q1", "dofs": dof, "stages": s,
-                   "tableau": tab_label(tab), "dt": wl.dt, "kappa": "lognormal sigma=0.5 seed %s" % wl.kappa_seed,
+                   "tableau": tab_label(tab), "dt": wl.dt,
+                   "kappa": ("lognormal sigma=0.5 seed %s" % wl.kappa_seed) if wl.kappa_seed is not None else "1",
                    "precond": precond, "splitting": SPLIT_LABEL[args.splitting], "vcycle": vcycle,
                    "levels": wl.levels, "rtol": wl.rtol, "orth": args.orth,
                    "restart": args.restart,
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
-                   "l2_policy": "working set > L2: Krylov basis of ~its x 25 MB stage vectors per step"},
+                   "l2_policy": "working set > L2: Krylov basis of ~its x %.0f MB stage vectors per step"
+                                % (dof * s * 8 / 1e6)},
         "dof_stage_per_s": round(steps_per_s * dof * s, 1),
         "fgmres_its_per_step": round(sum(its) / len(its), 2),
         "vcycles_per_step": round(sum(st["vcycles"] for st in stats) / len(stats), 2),
