@@ -642,8 +642,10 @@ struct Prec<__nv_bfloat16, float> {
 // x0 = V(b0) for blocks st0 .. st0+S-1 (S == s: all blocks batched; S == 1: block st0).
 // b0 and x0 are S-interleaved level-0 vectors of precision T; x0 may be nullptr, in
 // which case the result is left in an internal buffer that is returned.
+// first_done: the finest level's first sweep from a zero guess has already been written to the
+// buffer first_sweep_buffer() names (by the kernel that formed b0).
 template <typename T, typename C>
-T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2) {
+T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2, bool first_done = false) {
   using MG = MG2<T, C>;
   using MG3T = MG3<T, C>;
   using P = Prec<T, C>;
@@ -730,9 +732,11 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2) {
       bufs[0] = other, bufs[1] = last;
     }
     int w = 0;
+    // the first sweep's result is already in bufs[0] (written together with b0)
+    const bool skip_first = first_done && l == 0 && nu1 >= 1;
     // two sweeps from zero fused into one pass: always for FP32 / BF16; for FP64 only on the
     // coarse levels (on the finest level it would add FP64 work to an FP64-pipe-bound sweep)
-    const bool fuse2 = nu1 >= 2 && (!std::is_same<C, double>::value || l > 0);
+    const bool fuse2 = !skip_first && nu1 >= 2 && (!std::is_same<C, double>::value || l > 0);
     int k0 = 1;
     if (fuse2) {
       const double n = interior(Lv);
@@ -751,7 +755,7 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2) {
       }
       w = 1;
       k0 = 2;
-    } else {
+    } else if (!skip_first) {
       sweep(Lv, cf, dinv, nullptr, bl, bufs[w]);
     }
     for (int k = k0; k < nu1; ++k, w ^= 1) sweep(Lv, cf, dinv, bufs[w], bl, bufs[w ^ 1]);
@@ -872,6 +876,10 @@ int precond_apply(irk_handle* h, const double* v, double* z, bool transpose) {
   const double n = d3 ? (double)(L0.nx - 2) * (L0.nx - 2) * (L0.nx - 2) : n_int(L0.nx);
   Cls4 kc{};
   for (int k = 0; k < 4; ++k) kc.v[0][k] = L0.kcls[k];
+  // FP64, 2D: the kernel forming a block's right-hand side also writes the first Jacobi sweep from a
+  // zero guess (pointwise), into the buffer where the V-cycle's first sweep would land
+  const bool fuse_first = !d3 && std::is_same<C, double>::value && nu1 >= 1;
+  T* x1buf = ((nu1 + nu2) % 2 == 1) ? (T*)L0.xa : (T*)L0.xb;
   for (int step = 0; step < s; ++step) {
     const int i = lower ? step : s - 1 - step;
     Vec8 cj{};
@@ -884,20 +892,22 @@ int precond_apply(irk_handle* h, const double* v, double* z, bool transpose) {
       done += (solved && a != 0.0) ? 1 : 0;
     }
     {  // single-stage right-hand side in level-0 b (precision T)
-      KScope k(h, IRK_K_BLOCK_RHS, n * (8 + done * 8 + (d3 ? 0 : kCoef2 * c) + p), (d3 ? 32.0 : 19.0) * done * n);
+      const C* d1 = fuse_first ? Prec<T, C>::dinv(L0) + L0.nn * s + (size_t)i * L0.nn : nullptr;
+      KScope k(h, IRK_K_BLOCK_RHS, n * (8 + done * 8 + (d3 ? 0 : kCoef2 * c) + p + (fuse_first ? c + p : 0)),
+               (d3 ? 32.0 : 19.0) * done * n + (fuse_first ? n : 0));
       if (ia && d3) {
         Cls4 mc{};
         for (int q = 0; q < 4; ++q) mc.v[0][q] = L0.mcls[q];
         MG3<T, C>::block_rhs(s, st, L0.nx, mc, v, z, i, cj, (T*)L0.b);
       } else if (ia) {
-        MG::block_rhs_mass(s, st, L0.nx, L0.hm, v, z, i, cj, (T*)L0.b);
+        MG::block_rhs_mass(s, st, L0.nx, L0.hm, v, z, i, cj, (T*)L0.b, fuse_first ? d1 : nullptr, x1buf);
       } else if (d3) {
         MG3<T, C>::block_rhs(s, st, L0.nx, kc, v, z, i, cj, (T*)L0.b);
       } else {
-        MG::block_rhs(s, st, L0.nx, cf, v, z, i, cj, (T*)L0.b);
+        MG::block_rhs(s, st, L0.nx, cf, v, z, i, cj, (T*)L0.b, fuse_first ? d1 : nullptr, x1buf);
       }
     }
-    T* x = vcycle<T, C>(h, 1, i, (const T*)L0.b, nullptr, nu1, nu2);
+    T* x = vcycle<T, C>(h, 1, i, (const T*)L0.b, nullptr, nu1, nu2, fuse_first);
     KScope k(h, IRK_K_OTHER, n * (p + 8), 0);
     const double scale = ia ? h->Tm[i * s + i] : 1.0;
     if (d3)

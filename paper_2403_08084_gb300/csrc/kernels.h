@@ -34,12 +34,13 @@ struct MG2 {
                            T* r);
   static void restrict_(int S, cudaStream_t st, int nxf, const T* rf, int nxc, T* bc);
   static void prolong_add(int S, cudaStream_t st, int nxc, const T* ec, int nxf, T* xf);
+  // d1 != nullptr: also x1 = d1 * out (the block V-cycle's first sweep from a zero guess)
   static void block_rhs(int SF, cudaStream_t st, int nx, const C* cf, const double* v, const double* z, int i,
-                        const Vec8& cj, T* out);
+                        const Vec8& cj, T* out, const C* d1 = nullptr, T* x1 = nullptr);
   static void scatter_stage(int SF, cudaStream_t st, int nx, const T* x, int i, double* z, double scale = 1.0);
   // IA form: out = v_i - sum_j cj[j] M z_j
   static void block_rhs_mass(int SF, cudaStream_t st, int nx, double hm, const double* v, const double* z, int i,
-                             const Vec8& cj, T* out);
+                             const Vec8& cj, T* out, const C* d1 = nullptr, T* x1 = nullptr);
   static void cast_to(cudaStream_t st, const double* src, T* dst, size_t n);
   static void cast_from(cudaStream_t st, const T* src, double* dst, size_t n);
   // coarsest level (nxc nodes per axis, (nxc - 2)^2 unknowns in row-major interior order)

@@ -184,11 +184,14 @@ __global__ void __launch_bounds__(kBX* kBY) prolong_add_kernel(int nxc, const T*
 
 // Right-hand side of one block of the triangular preconditioners:
 // out = v_i - sum_j cj[j] K z_j  (cj[j] = dt a_ij for the stages already solved, else 0).
+// d1 != nullptr: also x1 = d1 * out, the first Jacobi sweep of the block's V-cycle from a zero guess
+// (d1 = omega / diag of the block), so that the V-cycle starts at its second sweep.
 template <typename T, typename C, int SF>
 __global__ void __launch_bounds__(kBX* kBY) block_rhs_kernel(int nx, const C* __restrict__ cf,
                                                              const double* __restrict__ v,
                                                              const double* __restrict__ z, int i, VecT<C> cj,
-                                                             unsigned used, T* __restrict__ out) {
+                                                             unsigned used, T* __restrict__ out,
+                                                             const C* __restrict__ d1, T* __restrict__ x1) {
   IRK_PDL_ENTRY;
   const int ix = 1 + blockIdx.x * kBX + threadIdx.x;
   const int iy = 1 + blockIdx.y * kBY + threadIdx.y;
@@ -200,15 +203,18 @@ __global__ void __launch_bounds__(kBX* kBY) block_rhs_kernel(int nx, const C* __
     if (used & (1u << j)) acc -= cj.v[j] * k_apply<SF, C>(cf, z, p, nx, j);
   }
   st(out + p, acc);
+  if (d1 != nullptr) st(x1 + p, d1[p] * ld<C>(out + p));
 }
 
 // IA form: out = v_i - sum_j cj[j] M z_j (M: the level's Q1 mass stencil; cjh = cj h^2 / 36).
 // The mass stencil is separable, [1 4 1] (x) [1 4 1]: each thread takes two vertically adjacent
 // interior nodes and shares the row sums of rows iy - 1 .. iy + 2 between them.
+// d1 / x1: as for block_rhs_kernel.
 template <typename T, typename C, int SF>
 __global__ void __launch_bounds__(kBX* kBY) block_rhs_mass_kernel(int nx, const double* __restrict__ v,
                                                                   const double* __restrict__ z, int i, VecT<C> cjh,
-                                                                  unsigned used, T* __restrict__ out) {
+                                                                  unsigned used, T* __restrict__ out,
+                                                                  const C* __restrict__ d1, T* __restrict__ x1) {
   IRK_PDL_ENTRY;
   const int ix = 1 + blockIdx.x * kBX + threadIdx.x;
   const int iy0 = 1 + 2 * (blockIdx.y * kBY + threadIdx.y);
@@ -231,6 +237,10 @@ __global__ void __launch_bounds__(kBX* kBY) block_rhs_mass_kernel(int nx, const 
   }
   st(out + p0, acc0);
   if (two) st(out + p0 + nx, acc1);
+  if (d1 != nullptr) {
+    st(x1 + p0, d1[p0] * ld<C>(out + p0));
+    if (two) st(x1 + p0 + nx, d1[p0 + nx] * ld<C>(out + p0 + nx));
+  }
 }
 
 // z[:, i] = scale * x on interior nodes (single-stage x into an SF-interleaved double vector).
@@ -375,13 +385,13 @@ void MG2<T, C>::prolong_add(int S, cudaStream_t st, int nxc, const T* ec, int nx
 }
 template <typename T, typename C>
 void MG2<T, C>::block_rhs(int SF, cudaStream_t st, int nx, const C* cf, const double* v, const double* z, int i,
-                          const Vec8& cj, T* out) {
+                          const Vec8& cj, T* out, const C* d1, T* x1) {
   dim3 g = interior_grid(nx), blk(kBX, kBY);
   unsigned used = 0;
   for (int j = 0; j < SF; ++j)
     if (cj.v[j] != 0.0) used |= 1u << j;
   const VecT<C> c = to_vec<C>(cj);
-  IRK_DISPATCH_S(SF, launch_k(block_rhs_kernel<T, C, SS>, g, blk, 0, st, nx, cf, v, z, i, c, used, out));
+  IRK_DISPATCH_S(SF, launch_k(block_rhs_kernel<T, C, SS>, g, blk, 0, st, nx, cf, v, z, i, c, used, out, d1, x1));
 }
 template <typename T, typename C>
 void MG2<T, C>::scatter_stage(int SF, cudaStream_t st, int nx, const T* x, int i, double* z, double scale) {
@@ -390,7 +400,7 @@ void MG2<T, C>::scatter_stage(int SF, cudaStream_t st, int nx, const T* x, int i
 }
 template <typename T, typename C>
 void MG2<T, C>::block_rhs_mass(int SF, cudaStream_t st, int nx, double hm, const double* v, const double* z, int i,
-                               const Vec8& cj, T* out) {
+                               const Vec8& cj, T* out, const C* d1, T* x1) {
   const int m = nx - 2;
   dim3 g((m + kBX - 1) / kBX, ((m + 1) / 2 + kBY - 1) / kBY), blk(kBX, kBY);  // two rows per thread
   unsigned used = 0;
@@ -400,7 +410,7 @@ void MG2<T, C>::block_rhs_mass(int SF, cudaStream_t st, int nx, double hm, const
     cjh.v[j] = cj.v[j] * hm;
   }
   const VecT<C> c = to_vec<C>(cjh);
-  IRK_DISPATCH_S(SF, launch_k(block_rhs_mass_kernel<T, C, SS>, g, blk, 0, st, nx, v, z, i, c, used, out));
+  IRK_DISPATCH_S(SF, launch_k(block_rhs_mass_kernel<T, C, SS>, g, blk, 0, st, nx, v, z, i, c, used, out, d1, x1));
 }
 template <typename T, typename C>
 void MG2<T, C>::cast_to(cudaStream_t st, const double* src, T* dst, size_t n) {
