@@ -16,7 +16,9 @@ GPU V-cycle can be compared with it application by application:
   K_{l+1} = P^T K_l P, so B_{l+1} = M_{l+1} + sigma K_{l+1} for sigma = dt a_ii;
 * smoother: weighted Jacobi x <- x + omega D^{-1} (b - B x), D = diag(B);
 * coarsest level: sparse LU (exact solve);
-* V(nu1, nu2) cycle with zero initial guess, nu1 pre- and nu2 post-sweeps.
+* V(nu1, nu2) cycle with zero initial guess, nu1 pre- and nu2 post-sweeps;
+* MonolithicVCycle: the same cycle on the whole stage system with a stage-coupled
+  point-block Jacobi relaxation (Sec. 3, 'Monolithic multigrid').
 """
 from __future__ import annotations
 
@@ -111,3 +113,57 @@ class ExactBlock:
 
     def __call__(self, b: np.ndarray) -> np.ndarray:
         return self.lu.solve(b)
+
+
+class MonolithicVCycle:
+    """Monolithic multigrid for the whole stage system (Sec. 3, 'Monolithic multigrid').
+
+    One V(nu1, nu2) cycle on S_l = I (x) M_l + dt A (x) K_l over the Galerkin hierarchy.  The
+    relaxation is additive Schwarz over vertex patches with all s stages of a patch coupled; for Q1
+    a vertex patch holds one node, so a sweep is point-block Jacobi
+
+        x <- x + omega D^{-1} (b - S_l x),   D = blockdiag_p (M_l[p, p] I_s + dt K_l[p, p] A).
+
+    Transfers act stage by stage (I (x) P, I (x) P^T) and the coarsest level is solved exactly.
+    Vectors are stage-major arrays of shape (s, n), the oracle's convention.
+    """
+
+    def __init__(self, hier: Hierarchy, A: np.ndarray, dt: float, nu1: int = 2, nu2: int = 2,
+                 omega: float = 2.0 / 3.0):
+        from .rk import kronecker_operator
+
+        self.h, self.A, self.dt = hier, np.asarray(A, dtype=np.float64), float(dt)
+        self.nu1, self.nu2, self.omega = nu1, nu2, omega
+        self.s = self.A.shape[0]
+        self.S = [kronecker_operator(hier.M[l], hier.K[l], self.A, self.dt).tocsr() for l in range(hier.levels)]
+        eye = np.eye(self.s)
+        self.Dinv = []
+        for l in range(hier.levels):
+            m, k = hier.M[l].diagonal(), hier.K[l].diagonal()
+            blocks = m[:, None, None] * eye[None] + self.dt * k[:, None, None] * self.A[None]
+            self.Dinv.append(np.linalg.inv(blocks))  # (n, s, s)
+        self.coarse = spla.splu(self.S[-1].tocsc())
+
+    def _apply_S(self, lev: int, x: np.ndarray) -> np.ndarray:
+        return (self.S[lev] @ x.reshape(-1)).reshape(x.shape)
+
+    def relax(self, lev: int, x: np.ndarray, b: np.ndarray, sweeps: int) -> np.ndarray:
+        for _ in range(sweeps):
+            r = b - self._apply_S(lev, x)
+            x = x + self.omega * np.einsum("pij,jp->ip", self.Dinv[lev], r)
+        return x
+
+    def cycle(self, b: np.ndarray, lev: int = 0) -> np.ndarray:
+        b = np.asarray(b, dtype=np.float64).reshape(self.s, -1)
+        if lev == self.h.levels - 1:
+            return self.coarse.solve(b.reshape(-1)).reshape(b.shape)
+        x = self.relax(lev, np.zeros_like(b), b, self.nu1)
+        r = b - self._apply_S(lev, x)
+        P = self.h.P[lev]
+        e = self.cycle((P.T @ r.T).T, lev + 1)
+        x = x + (P @ e.T).T
+        return self.relax(lev, x, b, self.nu2)
+
+    def __call__(self, v: np.ndarray) -> np.ndarray:
+        """Preconditioner interface of oracle.krylov.fgmres: flat stage-major vectors."""
+        return self.cycle(np.asarray(v).reshape(self.s, -1)).reshape(-1)

@@ -228,3 +228,73 @@ def test_ia_rana_ld_iterations_flat_in_s():
     assert its[("rana", 4)] - its[("rana", 2)] < its[("lower", 4)] - its[("lower", 2)]
     for s in (2, 3, 4):
         assert its[("rana", s)] <= its[("lower", s)]
+
+
+# ----------------------------------------------------------------------------
+# monolithic multigrid (Sec. 3, 'Monolithic multigrid')
+# ----------------------------------------------------------------------------
+def _mmg_setup(N=24, levels=3, seed=40):
+    d = fem.Discretisation(2, N, W.lognormal_kappa(2, N, 0.5, seed))
+    return d, mg.Hierarchy(d, levels)
+
+
+def test_mmg_single_stage_is_the_block_vcycle():
+    """s = 1: the stage-coupled relaxation is plain weighted Jacobi on M + dt a K, so one monolithic
+    cycle equals the single-block V-cycle (itself pinned above)."""
+    d, h = _mmg_setup()
+    dt, a = 0.05, 0.7
+    b = np.random.default_rng(41).standard_normal(d.n)
+    x_m = mg.MonolithicVCycle(h, np.array([[a]]), dt)(b)
+    x_v = mg.VCycle(h, dt * a)(b)
+    assert np.abs(x_m - x_v).max() <= 1e-13 * np.abs(x_v).max()
+
+
+def test_mmg_decouples_for_diagonal_A():
+    """Diagonal A: the system and its point blocks are block diagonal over stages, so the cycle is
+    the stack of single-block V-cycles with sigma_i = dt a_ii."""
+    d, h = _mmg_setup(seed=42)
+    dt, A = 0.03, np.diag([0.2, 0.55, 1.0])
+    b = np.random.default_rng(43).standard_normal((3, d.n))
+    x = mg.MonolithicVCycle(h, A, dt).cycle(b)
+    for i in range(3):
+        xi = mg.VCycle(h, dt * A[i, i])(b[i])
+        assert np.abs(x[i] - xi).max() <= 1e-13 * np.abs(xi).max()
+
+
+def test_mmg_one_level_is_exact():
+    d, h = _mmg_setup(N=12, levels=1)
+    tab, dt = T.radau_iia(3), 0.1
+    r = np.random.default_rng(44).standard_normal((3, d.n))
+    x = mg.MonolithicVCycle(h, tab.A, dt).cycle(r)
+    k = rk.KroneckerSolver(d.M, d.K, tab.A, dt).solve(r)
+    assert np.abs(x - k).max() <= 1e-12 * np.abs(k).max()
+
+
+def test_mmg_relaxation_is_point_block_jacobi():
+    """One sweep from zero: x = omega D^{-1} b with D_p = M[p,p] I + dt K[p,p] A solved node by node
+    (checked against a dense solve of each 3 x 3 block)."""
+    d, h = _mmg_setup(N=8, levels=2)
+    tab, dt = T.radau_iia(3), 0.2
+    b = np.random.default_rng(45).standard_normal((3, d.n))
+    x = mg.MonolithicVCycle(h, tab.A, dt).relax(0, np.zeros_like(b), b, 1)
+    m, k = d.M.diagonal(), d.K.diagonal()
+    for p in range(d.n):
+        Dp = m[p] * np.eye(3) + dt * k[p] * tab.A
+        assert np.allclose(x[:, p], (2.0 / 3.0) * np.linalg.solve(Dp, b[:, p]), rtol=1e-13, atol=0)
+
+
+def test_mmg_iterations_nearly_independent_of_s():
+    """The paper reports stage-independent iteration counts for monolithic multigrid; FGMRES with one
+    cycle per iteration on RadauIIA(1..4): counts within two of each other and at most 12."""
+    d, h = _mmg_setup(N=32, levels=3, seed=46)
+    dt = 1 / 32
+    its = []
+    for s in (1, 2, 3, 4):
+        tab = T.radau_iia(s)
+        S = rk.kronecker_operator(d.M, d.K, tab.A, dt)
+        r = np.random.default_rng(47).standard_normal(s * d.n)
+        _, it, res, _ = krylov.fgmres(lambda v: S @ v, r, mg.MonolithicVCycle(h, tab.A, dt), rtol=1e-10)
+        assert res <= 1e-10
+        its.append(it)
+    assert max(its) - min(its) <= 2, its
+    assert max(its) <= 12, its
