@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="heat2d-1024-radau3", choices=sorted(W.WORKLOADS))
-    ap.add_argument("--precond", default="lower", choices=["diag", "lower", "upper", "rana_ld"])
+    ap.add_argument("--precond", default="lower", choices=["diag", "lower", "upper", "rana_ld", "monolithic"])
     ap.add_argument("--vcycle", default=None, choices=["fp64", "fp32", "bf16"])
     ap.add_argument("--orth", default="cgs", choices=["cgs2", "dgks", "cgs"],
                     help="Arnoldi orthogonalisation; cgs (one pass, true residual checked at convergence) is the "
@@ -221,6 +221,8 @@ def gpu_arm(args, rank, world):
     if args.tableau:
         name, _, s_ = args.tableau.partition(":")
         tab_override = (name, int(s_ or 3))
+    if precond == "monolithic":  # monolithic multigrid is built for the AI form
+        args.splitting = "ai"
     sv, tab = make_solver(wl, precond, vcycle, args.orth, tab_override, args.splitting)
     nn = (wl.N + 1) ** wl.dim
     u0 = torch.from_numpy(W.sine_initial(wl.dim, wl.N)).cuda()
@@ -349,7 +351,7 @@ def gpu_arm(args, rank, world):
     if rank == 0 and not args.no_variants:
         out["variants"] = variants_leg(wl, u5.cpu().numpy(), args, vcycle, precond)
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline_leg(wl, precond, args.splitting if precond != "upper" else "ai")
+        out["cpu_baseline"] = cpu_baseline_leg(wl, precond, args.splitting if precond not in ("upper", "monolithic") else "ai")
     out["final_u_norm"] = float(torch.linalg.vector_norm(u_final).item())
     return out
 
@@ -397,6 +399,7 @@ def variants_leg(wl, u5_ref, args, vcycle0, precond0):
                 ("lower", "fp32", "cgs", None, "ia"), ("rana_ld", "fp32", "cgs", None, "ia"),
                 ("lower", "fp64", "cgs2", None, "ia"), ("lower", "fp32", "cgs2", None, "ia"),
                 ("rana_ld", "fp64", "cgs", None, "ia"), ("lower", "bf16", "cgs", None, "ia"),
+                ("monolithic", "fp64", "cgs", None, "ai"), ("monolithic", "fp32", "cgs", None, "ai"),
                 ("lower", "fp64", "cgs2", None, "ai"), ("diag", "fp64", "cgs2", None, "ai"),
                 ("rana_ld", "fp64", "cgs2", None, "ai"), ("lower", "fp32", "cgs2", None, "ai"),
                 ("lower", "bf16", "cgs2", None, "ai"),
@@ -446,7 +449,11 @@ def oracle_stepper(wl, N, levels, kind, split):
     h = mg.Hierarchy(d, levels)
     ot = OT.by_name(wl.tableau, wl.s)
     Ap = krylov.rana_ld(ot.A) if kind == "rana_ld" else ot.A
-    if split == "ia":
+    if kind == "monolithic":  # AI form only
+        S = rk.kronecker_operator(d.M, d.K, ot.A, wl.dt)
+        P = mg.MonolithicVCycle(h, ot.A, wl.dt)
+        Ainv = np.eye(wl.s)
+    elif split == "ia":
         T = np.diag(np.diag(Ap)) if kind == "diag" else np.tril(Ap)
         solves = [mg.VCycle(h, wl.dt * T[i, i]) for i in range(wl.s)]
         S = krylov.ia_operator(d.M, d.K, ot.A, wl.dt)
@@ -494,7 +501,7 @@ def reference_arm(args):
     # every step is a few seconds of CPU work; throughput is scaled to the full DOF count
     Ns = max(wl.N // 2, 32) if wl.dim == 2 else min(wl.N, 64)
     lv = max(1, wl.levels - int(round(np.log2(wl.N // Ns))))
-    split = args.splitting if args.precond != "upper" else "ai"
+    split = args.splitting if args.precond not in ("upper", "monolithic") else "ai"
     one, u0 = oracle_stepper(wl, Ns, lv, args.precond, split)
 
     u = u0.copy()

@@ -54,6 +54,11 @@ extern "C" {
 #define IRK_PC_UPPER 2 /* P_U = I (x) M + dt (U + D) (x) K    (Sec. 3.1)              */
 #define IRK_PC_RANA_LD 3 /* I (x) M + dt (L D) (x) K with A = L D U, L unit lower, U unit
                             upper: the Rana-type preconditioner (eq. pcranald, AI form)   */
+#define IRK_PC_MONOLITHIC 4 /* monolithic multigrid (Sec. 3, monolithic multigrid): one V-cycle
+                            on the whole stage system with stage-coupled point-block Jacobi
+                            relaxation (additive Schwarz on Q1 vertex patches) and an exact
+                            coupled coarsest solve; dim = 2, AI splitting, FGMRES; not
+                            available for the adjoint (transposed) preconditioner         */
 
 /* Arnoldi orthogonalisation (the paper does not fix one) */
 #define IRK_ORTH_CGS2 0 /* classical Gram-Schmidt, always two passes                       */

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_PKG, "libirk.so")
 HEADER = os.path.join(os.path.dirname(_PKG), "include", "irk.h")
 
 IRK_OK, IRK_EINVAL, IRK_ENOMEM, IRK_ECUDA, IRK_ENOCONV, IRK_ENONFINITE = 0, -1, -2, -3, -4, -5
-PC = {"diag": 0, "lower": 1, "upper": 2, "rana_ld": 3}
+PC = {"diag": 0, "lower": 1, "upper": 2, "rana_ld": 3, "monolithic": 4}
 PREC = {"fp64": 0, "fp32": 1, "bf16": 2}
 ORTH = {"cgs2": 0, "dgks": 1, "cgs": 2}
 SOLVER = {"fgmres": 0, "dirk_cg": 1}

@@ -69,6 +69,8 @@ struct Level {
   float* cf_f = nullptr;      // stencil records, float
   double* brec_d = nullptr;   // FP64 V-cycles: records of M + dt a_ii K, stage-major
   float* brec_f = nullptr;    // FP32 / BF16 V-cycles: the same records in FP32
+  double* mblk_d = nullptr;   // monolithic multigrid: omega (M_pp I + dt K_pp A)^{-1} per node (s x s)
+  float* mblk_f = nullptr;
   double* dinv_d = nullptr;   // omega / diag(B_i): node-major (s per node), then stage-major (nn per stage)
   float* dinv_f = nullptr;
   void* xa = nullptr;         // V-cycle vectors (s per node, V-cycle precision)
@@ -101,6 +103,8 @@ struct irk_handle {
   double* binv_d = nullptr;
   float* binv_f = nullptr;
   double* kappa_d = nullptr;
+  double* minv_d = nullptr;  // monolithic multigrid: dense inverse of the coupled coarsest system
+  float* minv_f = nullptr;
   // Krylov space
   size_t ne = 0;  // entries of a stage vector
   int m = 0;
@@ -339,7 +343,16 @@ int validate(const irk_mesh* mesh, const irk_tableau* tab, double dt, const irk_
   }
   if (std::fabs(bsum - 1.0) > 1e-6) return fail(IRK_EINVAL, "sum(b) = %.17g != 1", bsum);
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(IRK_EINVAL, "dt = %g must be positive", dt);
-  if (opt->precond < IRK_PC_DIAG || opt->precond > IRK_PC_RANA_LD) return fail(IRK_EINVAL, "bad precond %d", opt->precond);
+  if (opt->precond < IRK_PC_DIAG || opt->precond > IRK_PC_MONOLITHIC) return fail(IRK_EINVAL, "bad precond %d", opt->precond);
+  if (opt->precond == IRK_PC_MONOLITHIC &&
+      (mesh->dim != 2 || opt->splitting != IRK_SPLIT_AI || opt->solver != IRK_SOLVER_FGMRES))
+    return fail(IRK_EINVAL, "monolithic multigrid is implemented for dim = 2, the AI splitting and FGMRES");
+  if (opt->precond == IRK_PC_MONOLITHIC) {  // the coupled coarsest system is inverted densely
+    const int m = mesh->n_cells / (1 << (mesh->levels - 1)) - 1;
+    if ((long long)tab->s * m * m > 4096)
+      return fail(IRK_EINVAL, "monolithic multigrid: the coupled coarsest system has %lld > 4096 unknowns; add levels",
+                  (long long)tab->s * m * m);
+  }
   if (opt->vcycle_prec < IRK_PREC_FP64 || opt->vcycle_prec > IRK_PREC_BF16)
     return fail(IRK_EINVAL, "bad vcycle_prec %d", opt->vcycle_prec);
   if (opt->nu_pre < 1 || opt->nu_post < 1 || opt->nu_pre > 16 || opt->nu_post > 16)
@@ -410,6 +423,15 @@ int build_operators(irk_handle* h) {
     CK(cudaMemcpyAsync(Lv.dinv_d, dinv.data(), dinv.size() * 8, cudaMemcpyHostToDevice, h->st));
     CK(cudaMemcpyAsync(Lv.cf_f, cff.data(), cff.size() * 4, cudaMemcpyHostToDevice, h->st));
     CK(cudaMemcpyAsync(Lv.dinv_f, dinvf.data(), dinvf.size() * 4, cudaMemcpyHostToDevice, h->st));
+    if (Lv.mblk_d) {  // monolithic multigrid: stage-coupled point blocks of this level
+      std::vector<double> blk;
+      if (!mmg_block_inverses_2d(Lv.N, Lv.cf_host, Lv.hm, h->A.data(), s, h->dt, h->opt.omega, blk))
+        return fail(IRK_EINVAL, "a point block M_pp I + dt K_pp A of level %d is singular", l);
+      std::vector<float> blkf(blk.begin(), blk.end());
+      CK(cudaMemcpyAsync(Lv.mblk_d, blk.data(), blk.size() * 8, cudaMemcpyHostToDevice, h->st));
+      CK(cudaMemcpyAsync(Lv.mblk_f, blkf.data(), blkf.size() * 4, cudaMemcpyHostToDevice, h->st));
+      CK(cudaStreamSynchronize(h->st));
+    }
     std::vector<double> brec;
     std::vector<float> brecf;
     if (Lv.brec_d || Lv.brec_f) block_records_2d(Lv.N, Lv.cf_host, Lv.hm, sigma.data(), s, brec);
@@ -432,6 +454,15 @@ int build_operators(irk_handle* h) {
     std::copy(inv.begin(), inv.end(), all.begin() + (size_t)i * nint * nint);
   }
   std::vector<float> allf(all.begin(), all.end());
+  if (h->minv_d) {  // monolithic multigrid: the coupled coarsest system
+    std::vector<double> minv;
+    if (!mmg_coarse_inverse_2d(Lc.N, Lc.cf_host, Lc.hm, h->A.data(), s, h->dt, minv))
+      return fail(IRK_EINVAL, "the coupled coarsest system is singular");
+    std::vector<float> minvf(minv.begin(), minv.end());
+    CK(cudaMemcpyAsync(h->minv_d, minv.data(), minv.size() * 8, cudaMemcpyHostToDevice, h->st));
+    CK(cudaMemcpyAsync(h->minv_f, minvf.data(), minvf.size() * 4, cudaMemcpyHostToDevice, h->st));
+    CK(cudaStreamSynchronize(h->st));
+  }
   CK(cudaMemcpyAsync(h->cmap, map.data(), map.size() * sizeof(int), cudaMemcpyHostToDevice, h->st));
   CK(cudaMemcpyAsync(h->binv_d, all.data(), all.size() * 8, cudaMemcpyHostToDevice, h->st));
   CK(cudaMemcpyAsync(h->binv_f, allf.data(), allf.size() * 4, cudaMemcpyHostToDevice, h->st));
@@ -445,9 +476,10 @@ void destroy(irk_handle* h) {
   if (!h) return;
   for (Level& Lv : h->lev) {
     dfree(Lv.cf_d), dfree(Lv.cf_f), dfree(Lv.brec_d), dfree(Lv.brec_f), dfree(Lv.dinv_d), dfree(Lv.dinv_f);
+    dfree(Lv.mblk_d), dfree(Lv.mblk_f);
     dfree(Lv.xa), dfree(Lv.xb), dfree(Lv.b), dfree(Lv.r);
   }
-  dfree(h->cmap), dfree(h->binv_d), dfree(h->binv_f), dfree(h->kappa_d);
+  dfree(h->cmap), dfree(h->binv_d), dfree(h->binv_f), dfree(h->kappa_d), dfree(h->minv_d), dfree(h->minv_f);
   dfree(h->V), dfree(h->Z), dfree(h->H), dfree(h->cs), dfree(h->sn), dfree(h->g), dfree(h->y);
   dfree(h->h1), dfree(h->h2), dfree(h->partial), dfree(h->scal), dfree(h->iflag);
   dfree(h->rhs), dfree(h->k), dfree(h->tmp), dfree(h->bnd);
@@ -550,6 +582,9 @@ int create(irk_handle** out, const irk_mesh* mesh, const irk_tableau* tab, doubl
       // records of each diagonal block B_i = M + dt a_ii K, in the V-cycle's arithmetic precision
       if (opt->vcycle_prec == IRK_PREC_FP64 && (r = dalloc(&Lv.brec_d, Lv.nn * kCoef2 * s * 8))) return bail(r);
       if (opt->vcycle_prec != IRK_PREC_FP64 && (r = dalloc(&Lv.brec_f, Lv.nn * kCoef2 * s * 4))) return bail(r);
+      if (opt->precond == IRK_PC_MONOLITHIC &&
+          ((r = dalloc(&Lv.mblk_d, Lv.nn * s * s * 8)) || (r = dalloc(&Lv.mblk_f, Lv.nn * s * s * 4))))
+        return bail(r);
       if ((r = dalloc(&Lv.cf_d, Lv.nn * kCoef2 * 8)) || (r = dalloc(&Lv.cf_f, Lv.nn * kCoef2 * 4)) ||
           (r = dalloc(&Lv.dinv_d, Lv.nn * s * 2 * 8)) || (r = dalloc(&Lv.dinv_f, Lv.nn * s * 2 * 4)))
         return bail(r);
@@ -570,6 +605,10 @@ int create(irk_handle** out, const irk_mesh* mesh, const irk_tableau* tab, doubl
       (r = dalloc(&h->binv_f, (size_t)s * h->nint * h->nint * 4)) ||
       (r = dalloc(&h->kappa_d, dim == 2 ? (size_t)h->N * h->N * 8 : 16)))
     return bail(r);
+  if (opt->precond == IRK_PC_MONOLITHIC) {
+    const size_t nm = (size_t)s * h->nint;
+    if ((r = dalloc(&h->minv_d, nm * nm * 8)) || (r = dalloc(&h->minv_f, nm * nm * 4))) return bail(r);
+  }
   h->ne = h->lev[0].nn * s;
   h->m = opt->restart;
   const size_t ne = h->ne, m = h->m;
@@ -834,6 +873,91 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2, b
   return cur[0];
 }
 
+// One monolithic multigrid V-cycle (Sec. 3, monolithic multigrid) on the s-interleaved stage
+// vectors: x0 = V(b0) for the whole system I (x) M + dt A (x) K, with stage-coupled point-block
+// Jacobi relaxation on every level and the exact coupled coarsest solve.  x0 may be nullptr (the
+// result stays in a level buffer, which is returned).
+template <typename T, typename C>
+T* mmg_vcycle(irk_handle* h, const T* b0, T* x0, int nu1, int nu2) {
+  using MG = MG2<T, C>;
+  using P = Prec<T, C>;
+  constexpr bool f64 = std::is_same<C, double>::value;
+  const int s = h->s, L = h->L;
+  const double p = sizeof(T), c = sizeof(C);
+  cudaStream_t st = h->st;
+  Mat4 mix{};
+  for (int e = 0; e < s * s; ++e) mix.v[e] = h->dt * h->A[e];
+  auto cls = [&](const Level& Lv, int fine_class) {
+    if (&Lv == &h->lev[0]) return fine_class;
+    return Lv.nx >= kMgLargeNx ? IRK_K_MG_COARSE : IRK_K_MG_TAIL;
+  };
+  auto blk = [&](const Level& Lv) { return f64 ? (const C*)Lv.mblk_d : (const C*)Lv.mblk_f; };
+  auto interior = [&](const Level& Lv) { return (double)(Lv.nx - 2) * (Lv.nx - 2); };
+  auto smooth = [&](Level& Lv, const T* xin, const T* b, T* xout) {
+    const double n = interior(Lv);
+    KScope k(h, cls(Lv, IRK_K_JACOBI), n * (s * (xin ? 3 : 2) * p + kCoef2 * c + s * s * c),
+             n * (xin ? s * (20.0 + 2 * s) + 2.0 * s * s : 2.0 * s * s));
+    MG::mmg_smooth(s, st, Lv.nx, P::cf(Lv), Lv.hm, mix, blk(Lv), xin, b, xout);
+  };
+  std::vector<T*> cur(L, nullptr);
+  const T* bl = b0;
+  for (int l = 0; l < L - 1; ++l) {
+    Level& Lv = h->lev[l];
+    Level& Lc = h->lev[l + 1];
+    T* last = (l == 0 && x0) ? x0 : (T*)Lv.xa;
+    T* other = (l == 0 && x0) ? (T*)Lv.xa : (T*)Lv.xb;
+    T* bufs[2];
+    if ((nu1 + nu2) % 2 == 1) {
+      bufs[0] = last, bufs[1] = other;
+    } else {
+      bufs[0] = other, bufs[1] = last;
+    }
+    int w = 0;
+    smooth(Lv, nullptr, bl, bufs[0]);
+    for (int k = 1; k < nu1; ++k, w ^= 1) smooth(Lv, bufs[w], bl, bufs[w ^ 1]);
+    cur[l] = bufs[w];
+    const double nf = interior(Lv), nc = interior(Lc);
+    {
+      KScope k(h, cls(Lv, IRK_K_RESIDUAL), nf * (3 * s * p + kCoef2 * c), nf * s * (20.0 + 2 * s));
+      MG::mmg_residual(s, st, Lv.nx, P::cf(Lv), Lv.hm, mix, cur[l], bl, (T*)Lv.r);
+    }
+    {
+      KScope k(h, cls(Lv, IRK_K_RESTRICT), (nf + nc) * s * p, 12.0 * nc * s);
+      MG::restrict_(s, st, Lv.nx, (const T*)Lv.r, Lc.nx, (T*)Lc.b);
+    }
+    bl = (const T*)Lc.b;
+  }
+  {  // coarsest level: exact coupled solve
+    Level& Lc = h->lev[L - 1];
+    T* xc = (L == 1 && x0) ? x0 : (T*)Lc.xa;
+    const double nm = (double)s * h->nint;
+    KScope k(h, IRK_K_COARSE, nm * nm * c + 2 * nm * p, 2.0 * nm * nm);
+    MG::mmg_coarse_solve(s, st, Lc.nx, f64 ? (const C*)h->minv_d : (const C*)h->minv_f, bl, xc);
+    cur[L - 1] = xc;
+  }
+  for (int l = L - 2; l >= 0; --l) {
+    Level& Lv = h->lev[l];
+    Level& Lc = h->lev[l + 1];
+    const T* bfine = (l == 0) ? b0 : (const T*)Lv.b;
+    const double nf = interior(Lv), nc = interior(Lc);
+    {
+      KScope k(h, cls(Lv, IRK_K_PROLONG), (nc + 2 * nf) * s * p, 5.0 * nf * s);
+      MG::prolong_add(s, st, Lc.nx, cur[l + 1], Lv.nx, cur[l]);
+    }
+    T* last = (l == 0 && x0) ? x0 : (T*)Lv.xa;
+    T* other = (l == 0 && x0) ? (T*)Lv.xa : (T*)Lv.xb;
+    T* a = cur[l];
+    T* bnext = (a == last) ? other : last;
+    for (int k = 0; k < nu2; ++k) {
+      smooth(Lv, a, bfine, bnext);
+      std::swap(a, bnext);
+    }
+    cur[l] = a;
+  }
+  h->vcycles += 1;
+  return cur[0];
+}
+
 // z = P^{-1} v with the configured block preconditioner (v, z: double stage vectors).
 // transpose: apply P^T (the triangular sweep runs the other way with A^T couplings
 // and every V(nu1, nu2) cycle becomes V(nu2, nu1), its transpose).
@@ -847,6 +971,22 @@ int precond_apply(irk_handle* h, const double* v, double* z, bool transpose) {
   cudaStream_t st = h->st;
   const double p = sizeof(T), c = sizeof(C), ne = (double)h->ne;
   const bool ia = (h->opt.splitting == IRK_SPLIT_IA);
+  if (h->opt.precond == IRK_PC_MONOLITHIC) {
+    if (transpose) return fail(IRK_EINVAL, "the transposed monolithic multigrid cycle is not implemented");
+    if constexpr (std::is_same<T, double>::value) {
+      mmg_vcycle<T, C>(h, v, z, nu1, nu2);
+    } else {
+      {
+        KScope k(h, IRK_K_OTHER, ne * (8 + p), 0);
+        MG::cast_to(st, v, (T*)L0.b, h->ne);
+      }
+      T* x = mmg_vcycle<T, C>(h, (const T*)L0.b, nullptr, nu1, nu2);
+      KScope k(h, IRK_K_OTHER, ne * (8 + p), 0);
+      MG::cast_from(st, x, z, h->ne);
+    }
+    CK_LAUNCH();
+    return IRK_OK;
+  }
   if (h->opt.precond == IRK_PC_DIAG || s == 1) {
     if constexpr (std::is_same<T, double>::value) {
       vcycle<T, C>(h, s, 0, v, z, nu1, nu2);
@@ -1702,6 +1842,8 @@ int irk_step_adjoint(irk_handle* h, const double* u_n, const double* stages, con
   if (!h || !u_n || !stages || !lam_np1 || !lam_n) return fail(IRK_EINVAL, "null argument");
   if (h->dim != 2) return fail(IRK_EINVAL, "irk_step_adjoint is implemented for dim = 2");
   if (h->opt.splitting != IRK_SPLIT_AI) return fail(IRK_EINVAL, "irk_step_adjoint needs the AI splitting");
+  if (h->opt.precond == IRK_PC_MONOLITHIC)
+    return fail(IRK_EINVAL, "irk_step_adjoint: the transposed monolithic multigrid cycle is not implemented");
   const int s = h->s;
   const size_t nn = h->lev[0].nn, nb = nn * 8, sb = h->ne * 8, gb = (size_t)h->N * h->N * 8;
   const void *ud, *kd, *ld;

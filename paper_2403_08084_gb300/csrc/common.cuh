@@ -47,6 +47,16 @@ struct ClsT {
   C v[kMaxS][4];
 };
 template <typename C>
+struct MatT {
+  C v[kMaxS * kMaxS];
+};
+template <typename C>
+inline MatT<C> to_mat(const Mat4& a) {
+  MatT<C> r;
+  for (int i = 0; i < kMaxS * kMaxS; ++i) r.v[i] = static_cast<C>(a.v[i]);
+  return r;
+}
+template <typename C>
 inline VecT<C> to_vec(const Vec8& a) {
   VecT<C> r;
   for (int i = 0; i < 8; ++i) r.v[i] = static_cast<C>(a.v[i]);

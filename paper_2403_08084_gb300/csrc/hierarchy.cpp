@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstddef>
+#include <thread>
 #include <utility>
 
 namespace irk {
@@ -135,6 +136,113 @@ void interior_nodes_2d(int N, std::vector<int>& map) {
   map.clear();
   for (int iy = 1; iy < nx - 1; ++iy)
     for (int ix = 1; ix < nx - 1; ++ix) map.push_back(ix + nx * iy);
+}
+
+bool mmg_block_inverses_2d(int N, const std::vector<double>& cf, double hm, const double* A, int s, double dt,
+                           double omega, std::vector<double>& dblk) {
+  const int nx = N + 1;
+  dblk.assign((size_t)nx * nx * s * s, 0.0);
+  std::vector<double> D((size_t)s * s), W((size_t)s * 2 * s);
+  for (int iy = 1; iy < nx - 1; ++iy)
+    for (int ix = 1; ix < nx - 1; ++ix) {
+      const size_t p = (size_t)ix + (size_t)nx * iy;
+      const double m = 16.0 * hm, k = cf[p * kRec + kD];
+      // Gauss-Jordan with partial pivoting on [D | I], D = m I + dt k A
+      for (int i = 0; i < s; ++i)
+        for (int j = 0; j < 2 * s; ++j)
+          W[(size_t)i * 2 * s + j] = (j < s) ? (i == j ? m : 0.0) + dt * k * A[i * s + j] : (j - s == i ? 1.0 : 0.0);
+      for (int c = 0; c < s; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < s; ++r)
+          if (std::fabs(W[(size_t)r * 2 * s + c]) > std::fabs(W[(size_t)piv * 2 * s + c])) piv = r;
+        const double d = W[(size_t)piv * 2 * s + c];
+        if (!(std::fabs(d) > 0.0) || !std::isfinite(d)) return false;
+        if (piv != c)
+          for (int j = 0; j < 2 * s; ++j) std::swap(W[(size_t)c * 2 * s + j], W[(size_t)piv * 2 * s + j]);
+        for (int j = 0; j < 2 * s; ++j) W[(size_t)c * 2 * s + j] /= d;
+        for (int r = 0; r < s; ++r) {
+          if (r == c) continue;
+          const double f = W[(size_t)r * 2 * s + c];
+          for (int j = 0; j < 2 * s; ++j) W[(size_t)r * 2 * s + j] -= f * W[(size_t)c * 2 * s + j];
+        }
+      }
+      for (int i = 0; i < s; ++i)
+        for (int j = 0; j < s; ++j) dblk[p * s * s + (size_t)i * s + j] = omega * W[(size_t)i * 2 * s + s + j];
+    }
+  return true;
+}
+
+bool mmg_coarse_inverse_2d(int N, const std::vector<double>& cf, double hm, const double* A, int s, double dt,
+                           std::vector<double>& inv) {
+  const int nx = N + 1, m = nx - 2, nint = m * m, n = s * nint;
+  // assemble the interleaved system densely (its band: |row - col| <= s (m + 1) + s - 1)
+  std::vector<double> F((size_t)n * n, 0.0);
+  for (int iy = 1; iy < nx - 1; ++iy)
+    for (int ix = 1; ix < nx - 1; ++ix) {
+      const int q = (ix - 1) + m * (iy - 1);
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int jx = ix + dx, jy = iy + dy;
+          if (!interior(jx, jy, nx)) continue;
+          const int qc = (jx - 1) + m * (jy - 1);
+          const double mv = hm * ((dx == 0 ? 4.0 : 1.0) * (dy == 0 ? 4.0 : 1.0));
+          const double kv = coupling(cf, nx, ix, iy, dx, dy);
+          for (int i = 0; i < s; ++i)
+            for (int j = 0; j < s; ++j)
+              F[(size_t)(q * s + i) * n + (qc * s + j)] = (i == j ? mv : 0.0) + dt * A[i * s + j] * kv;
+        }
+    }
+  // Banded LU with partial pivoting in the scheme of LAPACK's band solver: the interchange at step k
+  // swaps only the not yet eliminated columns, so column k of L keeps the multipliers of the rows as
+  // they stood at step k and the forward solve replays interchange and elimination step by step.
+  const int bl = s * (m + 1) + s - 1;  // lower bandwidth; row interchanges widen the upper one to 2 bl
+  const int bu = 2 * bl;
+  std::vector<int> perm(n);
+  for (int k = 0; k < n; ++k) {
+    const int rmax = std::min(n - 1, k + bl), cmax = std::min(n - 1, k + bu);
+    int piv = k;
+    for (int r = k + 1; r <= rmax; ++r)
+      if (std::fabs(F[(size_t)r * n + k]) > std::fabs(F[(size_t)piv * n + k])) piv = r;
+    const double d = F[(size_t)piv * n + k];
+    if (!(std::fabs(d) > 0.0) || !std::isfinite(d)) return false;
+    perm[k] = piv;
+    if (piv != k)
+      for (int c = k; c <= cmax; ++c) std::swap(F[(size_t)k * n + c], F[(size_t)piv * n + c]);
+    for (int r = k + 1; r <= rmax; ++r) {
+      const double f = F[(size_t)r * n + k] / d;
+      F[(size_t)r * n + k] = f;
+      if (f == 0.0) continue;
+      for (int c = k + 1; c <= cmax; ++c) F[(size_t)r * n + c] -= f * F[(size_t)k * n + c];
+    }
+  }
+  // columns of the inverse, spread over the host's threads
+  inv.assign((size_t)n * n, 0.0);
+  auto solve_columns = [&](int c0, int c1) {
+    std::vector<double> y(n);
+    for (int col = c0; col < c1; ++col) {
+      std::fill(y.begin(), y.end(), 0.0);
+      y[col] = 1.0;
+      for (int k = 0; k < n; ++k) {
+        if (perm[k] != k) std::swap(y[k], y[perm[k]]);
+        const double yk = y[k];
+        if (yk == 0.0) continue;
+        const int rmax = std::min(n - 1, k + bl);
+        for (int r = k + 1; r <= rmax; ++r) y[r] -= F[(size_t)r * n + k] * yk;
+      }
+      for (int r = n - 1; r >= 0; --r) {
+        double v = y[r];
+        const int cmax = std::min(n - 1, r + bu);
+        for (int c = r + 1; c <= cmax; ++c) v -= F[(size_t)r * n + c] * y[c];
+        y[r] = v / F[(size_t)r * n + r];
+      }
+      for (int r = 0; r < n; ++r) inv[(size_t)r * n + col] = y[r];
+    }
+  };
+  const int nt = std::max(1, std::min(32, (int)std::thread::hardware_concurrency()));
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nt; ++t) pool.emplace_back(solve_columns, (int)((long long)n * t / nt), (int)((long long)n * (t + 1) / nt));
+  for (auto& th : pool) th.join();
+  return true;
 }
 
 bool dense_block_inverse_2d(int N, const std::vector<double>& cf, double hm, double sigma,

@@ -31,6 +31,17 @@ void interior_nodes_2d(int N, std::vector<int>& map);
 bool dense_block_inverse_2d(int N, const std::vector<double>& cf, double hm, double sigma,
                             const std::vector<int>& map, std::vector<double>& inv);
 
+// Monolithic multigrid (stage-coupled point-block Jacobi): omega (M[p,p] I + dt K[p,p] A)^{-1} per
+// node (row-major s x s, 0 on the boundary), node-major.  Returns false if a block is singular.
+bool mmg_block_inverses_2d(int N, const std::vector<double>& cf, double hm, const double* A, int s, double dt,
+                           double omega, std::vector<double>& dblk);
+
+// Dense inverse of the coupled coarsest system I (x) M + dt A (x) K on the interior nodes, unknowns
+// interleaved (row q s + i: stage i of interior node q, x fastest); banded LU with partial pivoting.
+// Returns false if the matrix is singular to working precision.
+bool mmg_coarse_inverse_2d(int N, const std::vector<double>& cf, double hm, const double* A, int s, double dt,
+                           std::vector<double>& inv);
+
 // 3D, kappa = 1: values of the Q1 mass and stiffness 27-point stencils on a grid
 // of spacing h by offset class (number of nonzero offset coordinates 0..3).
 void q1_classes_3d(double h, double mass[4], double stiff[4]);

@@ -52,6 +52,14 @@ struct MG2 {
   static void up_leg(int S, cudaStream_t st, int nxf, const C* cf, double hm, const Vec8& sigma, const C* rec,
                      size_t rstride, const C* dinv, int dstride, const T* xin, const T* b, int nxc, const T* ec,
                      T* xout);
+  // monolithic multigrid (mmg2d.cuh) on S-interleaved level vectors, mix = dt A (or dt A^T):
+  // x_out = x_in + omega D^{-1} (b - S_l x_in) with the per-node s x s inverses dblk (x_in == nullptr:
+  // zero guess); r = b - S_l x; exact coarsest solve with the dense inverse of the coupled system.
+  static void mmg_smooth(int S, cudaStream_t st, int nx, const C* cf, double hm, const Mat4& mix, const C* dblk,
+                         const T* xin, const T* b, T* xout);
+  static void mmg_residual(int S, cudaStream_t st, int nx, const C* cf, double hm, const Mat4& mix, const T* x,
+                           const T* b, T* r);
+  static void mmg_coarse_solve(int S, cudaStream_t st, int nxc, const C* inv, const T* b, T* x);
 };
 
 // Coarse levels whose finer grid has at least this many nodes per axis run the fused V-cycle legs

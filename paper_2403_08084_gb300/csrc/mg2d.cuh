@@ -438,3 +438,4 @@ void MG2<T, C>::coarse_solve(int S, cudaStream_t st, int nxc, const C* binv, con
 }  // namespace irk
 
 #include "mg2d_legs.cuh"
+#include "mmg2d.cuh"

@@ -1,0 +1,98 @@
+"""GPU parity for monolithic multigrid (Sec. 3, monolithic multigrid): one V-cycle on the whole stage
+system with stage-coupled point-block Jacobi relaxation, against the oracle's MonolithicVCycle."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import fem, krylov, mg, rk
+from oracle import tableaux as OT
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("CUDA GPU required", allow_module_level=True)
+
+from paper_2403_08084_gb300 import IRKError, Solver  # noqa: E402
+from paper_2403_08084_gb300 import tableaux as PT  # noqa: E402
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+def setup(N, s, seed):
+    kap = W.lognormal_kappa(2, N, 0.5, seed)
+    d = fem.Discretisation(2, N, kap)
+    return kap, d, OT.radau_iia(s), PT.radau_iia(s)
+
+
+@pytest.mark.parametrize("N,levels,s", [(40, 3, 3), (64, 4, 2), (48, 2, 4), (32, 1, 3)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5), ("bf16", 3e-2)])
+def test_mmg_cycle_matches_oracle(N, levels, s, prec, tol):
+    """One application of the preconditioner against the oracle's cycle (1 level: the exact solve)."""
+    kap, d, ot, tab = setup(N, s, 80)
+    dt = 1 / 48
+    v_full = W.random_nodal(2, N, seed=81, s=s)
+    v = d.to_interior(v_full, s)
+    z_ref = mg.MonolithicVCycle(mg.Hierarchy(d, levels), ot.A, dt).cycle(v)
+    with Solver(N, tab, dt, kappa=kap, levels=levels, precond="monolithic", vcycle=prec) as sv:
+        z = torch.empty(sv.n_nodes * s, dtype=torch.float64, device="cuda")
+        sv.apply_preconditioner(torch.from_numpy(v_full).cuda(), z)
+        z = z.cpu().numpy()
+    assert rel(d.to_interior(z, s), z_ref) < tol
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_mmg_solve_matches_direct_and_iteration_count(prec):
+    N, levels, s, dt = 64, 3, 3, 1 / 64
+    kap, d, ot, tab = setup(N, s, 82)
+    r_full = W.random_nodal(2, N, seed=83, s=s)
+    r = d.to_interior(r_full, s)
+    k_ref = rk.KroneckerSolver(d.M, d.K, ot.A, dt).solve(r)
+    with Solver(N, tab, dt, kappa=kap, levels=levels, precond="monolithic", vcycle=prec, rtol=1e-12) as sv:
+        k = np.empty(sv.n_nodes * s)
+        st = sv.solve(r_full, k)
+    assert st["converged"] and rel(d.to_interior(k, s), k_ref) < 1e-10
+    S = rk.kronecker_operator(d.M, d.K, ot.A, dt)
+    _, its, _, _ = krylov.fgmres(lambda x: S @ x, r.reshape(-1), mg.MonolithicVCycle(mg.Hierarchy(d, levels), ot.A, dt),
+                                 rtol=1e-12)
+    assert abs(st["fgmres_its"] - its) <= (1 if prec == "fp64" else 2), (st["fgmres_its"], its)
+
+
+def test_mmg_steps_match_oracle_and_iterations_flat_in_s():
+    """RK steps with the monolithic preconditioner reproduce the oracle; iteration counts for
+    RadauIIA(1..4) stay within two of each other (the paper's stage independence)."""
+    N, levels, dt, steps = 48, 3, 1 / 32, 3
+    kap = W.lognormal_kappa(2, N, 0.5, 84)
+    d = fem.Discretisation(2, N, kap)
+    its = {}
+    for s in (1, 2, 3, 4):
+        ot, tab = OT.radau_iia(s), PT.radau_iia(s)
+        u0 = d.to_interior(W.sine_initial(2, N))
+        Fs = d.to_interior(W.sine_load_space(2, N))
+        uN, _ = rk.run(d, ot, dt, steps, u0, lambda t: W.sine_load_time(2, t) * Fs)
+        with Solver(N, tab, dt, kappa=kap, levels=levels, precond="monolithic", rtol=1e-12) as sv:
+            u = W.sine_initial(2, N)
+            f = W.sine_load_space(2, N)
+            n_its = []
+            for n in range(steps):
+                st = sv.step(u, u, f_space=f, f_coef=[W.sine_load_time(2, (n + c) * dt) for c in tab.c])
+                n_its.append(st["fgmres_its"])
+        assert rel(d.to_interior(u), uN) < 1e-10
+        its[s] = max(n_its)
+    assert max(its.values()) - min(its.values()) <= 2, its
+
+
+def test_mmg_rejects_unsupported_configurations():
+    tab = PT.radau_iia(2)
+    with pytest.raises(IRKError):
+        Solver(16, tab, 0.1, precond="monolithic", splitting="ia")
+    with pytest.raises(IRKError):
+        Solver(16, tab, 0.1, dim=3, levels=2, precond="monolithic")
+    with Solver(16, tab, 0.1, levels=2, precond="monolithic") as sv:
+        nn = sv.n_nodes
+        with pytest.raises(IRKError):
+            sv.apply_preconditioner(np.zeros(nn * 2), np.zeros(nn * 2), transpose=True)
+        with pytest.raises(IRKError):
+            sv.step_adjoint(np.zeros(nn), np.zeros(nn * 2), np.zeros(nn), np.zeros(nn))
