@@ -546,8 +546,8 @@ def reference_arm(args):
 # ----------------------------------------------------------------------------
 def study_long_horizon(args):
     """2048^2 Q1, lognormal kappa (seed 0), integrated to T = 1 with Alexander's 3-stage SDIRK (sequential
-    per-stage V-cycle-preconditioned CG) and RadauIIA(3) (FGMRES, P_L, IA and AI forms), each with FP64 and
-    FP32 V-cycles,
+    per-stage V-cycle-preconditioned CG) and RadauIIA(3) (FGMRES with P_L in the IA and AI forms, or monolithic
+    multigrid), each with FP64 and FP32 V-cycles,
     over a sweep of step sizes.  The error is ||u_N - u_ref||_M / ||u_ref||_M against RadauIIA(4) at
     dt = 1/200 (order 7; its own error is estimated from the same scheme at dt = 1/100).  Time is the
     wall time of the step loop (setup reported apart); at a target error, each form's time is
@@ -596,14 +596,15 @@ def study_long_horizon(args):
     ref_norm = mnorm(ref)
     ref_err_est = mnorm(ref2 - ref) / ref_norm / (2**7 - 1)
 
-    forms = [("RadauIIA(3) IA", PT.radau_iia(3), "fgmres", (2, 4, 8, 16, 32, 64), "ia"),
-             ("RadauIIA(3) AI", PT.radau_iia(3), "fgmres", (2, 4, 8, 16, 32, 64), "ai"),
-             ("Alexander SDIRK", PT.alexander(), "dirk_cg", (10, 25, 50, 100, 200, 400), "ai")]
+    forms = [("RadauIIA(3) IA", PT.radau_iia(3), "fgmres", (2, 4, 8, 16, 32, 64), "ia", "lower"),
+             ("RadauIIA(3) AI", PT.radau_iia(3), "fgmres", (2, 4, 8, 16, 32, 64), "ai", "lower"),
+             ("RadauIIA(3) monolithic MG", PT.radau_iia(3), "fgmres", (2, 4, 8, 16, 32, 64), "ai", "monolithic"),
+             ("Alexander SDIRK", PT.alexander(), "dirk_cg", (10, 25, 50, 100, 200, 400), "ai", "lower")]
     rows = []
-    for label, tab, solver, sweep, split in forms:
+    for label, tab, solver, sweep, split, precond in forms:
         for vcycle in ("fp64", "fp32"):
             for nsteps in sweep:
-                u, wall, setup, its = integrate(tab, nsteps, vcycle, solver, wl.rtol, split)
+                u, wall, setup, its = integrate(tab, nsteps, vcycle, solver, wl.rtol, split, precond)
                 rows.append({"scheme": label, "vcycle": vcycle, "dt": 1 / nsteps, "steps": nsteps,
                              "loop_s": round(wall, 4), "setup_s": round(setup, 3), "its_per_step": round(its, 2),
                              "rel_l2_err": mnorm(u - ref) / ref_norm})
@@ -620,13 +621,13 @@ def study_long_horizon(args):
     matched = []
     for target in (1e-4, 1e-5, 1e-6, 1e-7, 1e-8, 1e-9):
         entry = {"target_rel_l2_err": target}
-        for label, _, _, _, _ in forms:
+        for label, _, _, _, _, _ in forms:
             for vcycle in ("fp64", "fp32"):
                 entry[f"{label} {vcycle}"] = time_at(label, vcycle, target)
         matched.append(entry)
     return {"study": "long-horizon time-to-solution at equal final L2 error",
             "workload": wl.name, "mesh": f"{N}x{N} Q1", "dofs": (N + 1) ** 2, "T": T, "rtol": wl.rtol,
-            "levels": wl.levels, "precond": "P_L (RadauIIA, IA and AI forms); per-stage V(2,2)-PCG (SDIRK)",
+            "levels": wl.levels, "precond": "P_L (RadauIIA, IA and AI forms) or monolithic MG; per-stage V(2,2)-PCG (SDIRK)",
             "reference": {"scheme": "RadauIIA(4), IA form", "dt": 1 / 200, "rtol": 1e-13, "loop_s": round(ref_wall, 2),
                           "its_per_step": round(ref_its, 2), "est_rel_err": ref_err_est},
             "runs": rows, "loop_seconds_at_matched_error": matched}
