@@ -115,6 +115,7 @@ struct irk_handle {
   int* iflag = nullptr;  // device flags (re-orthogonalisation decision)
   double* pinned = nullptr;  // host-visible copies of the residual estimate
   double *rhs = nullptr, *k = nullptr, *tmp = nullptr;
+  void* zt = nullptr;  // FP32 / BF16 triangular sweeps: the blocks' V-cycle outputs, stage-major, precision T
   double* bnd = nullptr;  // boundary unknowns of irk_step_dirichlet (allocated on first use)
   DevBuf stage_bufs[8];
   int vcycles = 0;
@@ -482,7 +483,7 @@ void destroy(irk_handle* h) {
   dfree(h->cmap), dfree(h->binv_d), dfree(h->binv_f), dfree(h->kappa_d), dfree(h->minv_d), dfree(h->minv_f);
   dfree(h->V), dfree(h->Z), dfree(h->H), dfree(h->cs), dfree(h->sn), dfree(h->g), dfree(h->y);
   dfree(h->h1), dfree(h->h2), dfree(h->partial), dfree(h->scal), dfree(h->iflag);
-  dfree(h->rhs), dfree(h->k), dfree(h->tmp), dfree(h->bnd);
+  dfree(h->rhs), dfree(h->k), dfree(h->tmp), dfree(h->bnd), dfree(h->zt);
   for (DevBuf& b : h->stage_bufs) dfree(b.p);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   for (auto& gv : h->graphs)
@@ -611,6 +612,12 @@ int create(irk_handle** out, const irk_mesh* mesh, const irk_tableau* tab, doubl
   }
   h->ne = h->lev[0].nn * s;
   h->m = opt->restart;
+  const bool sweeps = opt->precond == IRK_PC_LOWER || opt->precond == IRK_PC_UPPER || opt->precond == IRK_PC_RANA_LD;
+  if (sweeps && s > 1 && opt->vcycle_prec != IRK_PREC_FP64) {
+    if ((r = dalloc(&h->zt, h->lev[0].nn * s * vb))) return bail(r);
+    // boundary entries are read by the stencils next to the boundary and must stay zero
+    if (cudaMemsetAsync(h->zt, 0, h->lev[0].nn * s * vb, h->st)) return bail(fail(IRK_ECUDA, "cudaMemsetAsync failed"));
+  }
   const size_t ne = h->ne, m = h->m;
   if ((r = dalloc(&h->V, (m + 1) * ne * 8)) || (r = dalloc(&h->Z, m * ne * 8)) ||
       (r = dalloc(&h->H, (m + 1) * m * 8)) || (r = dalloc(&h->cs, m * 8)) || (r = dalloc(&h->sn, m * 8)) ||
@@ -1020,6 +1027,9 @@ int precond_apply(irk_handle* h, const double* v, double* z, bool transpose) {
   // zero guess (pointwise), into the buffer where the V-cycle's first sweep would land
   const bool fuse_first = !d3 && std::is_same<C, double>::value && nu1 >= 1;
   T* x1buf = ((nu1 + nu2) % 2 == 1) ? (T*)L0.xa : (T*)L0.xb;
+  // FP32 / BF16: the solved stages are read back in precision T (stage-major copies in h->zt)
+  T* zt = std::is_same<T, double>::value ? nullptr : (T*)h->zt;
+  const size_t zs = L0.nn;
   for (int step = 0; step < s; ++step) {
     const int i = lower ? step : s - 1 - step;
     Vec8 cj{};
@@ -1029,6 +1039,8 @@ int precond_apply(irk_handle* h, const double* v, double* z, bool transpose) {
       // AI: dt (Ap)_ij couples through K; IA: (T^{-1})_ij couples through M
       const double a = ia ? h->Tinv[i * s + j] : (transpose ? h->Ap[j * s + i] : h->Ap[i * s + j]);
       cj.v[j] = solved ? (ia ? a : h->dt * a) : 0.0;
+      // reading the unscaled V-cycle outputs (zt): fold in the scale z_j = T_jj x_j (IA)
+      if (zt && ia) cj.v[j] *= h->Tm[j * s + j];
       done += (solved && a != 0.0) ? 1 : 0;
     }
     {  // single-stage right-hand side in level-0 b (precision T)
@@ -1038,22 +1050,23 @@ int precond_apply(irk_handle* h, const double* v, double* z, bool transpose) {
       if (ia && d3) {
         Cls4 mc{};
         for (int q = 0; q < 4; ++q) mc.v[0][q] = L0.mcls[q];
-        MG3<T, C>::block_rhs(s, st, L0.nx, mc, v, z, i, cj, (T*)L0.b);
+        MG3<T, C>::block_rhs(s, st, L0.nx, mc, v, z, i, cj, (T*)L0.b, zt, zs);
       } else if (ia) {
-        MG::block_rhs_mass(s, st, L0.nx, L0.hm, v, z, i, cj, (T*)L0.b, fuse_first ? d1 : nullptr, x1buf);
+        MG::block_rhs_mass(s, st, L0.nx, L0.hm, v, z, i, cj, (T*)L0.b, fuse_first ? d1 : nullptr, x1buf, zt, zs);
       } else if (d3) {
-        MG3<T, C>::block_rhs(s, st, L0.nx, kc, v, z, i, cj, (T*)L0.b);
+        MG3<T, C>::block_rhs(s, st, L0.nx, kc, v, z, i, cj, (T*)L0.b, zt, zs);
       } else {
-        MG::block_rhs(s, st, L0.nx, cf, v, z, i, cj, (T*)L0.b, fuse_first ? d1 : nullptr, x1buf);
+        MG::block_rhs(s, st, L0.nx, cf, v, z, i, cj, (T*)L0.b, fuse_first ? d1 : nullptr, x1buf, zt, zs);
       }
     }
     T* x = vcycle<T, C>(h, 1, i, (const T*)L0.b, nullptr, nu1, nu2, fuse_first);
     KScope k(h, IRK_K_OTHER, n * (p + 8), 0);
     const double scale = ia ? h->Tm[i * s + i] : 1.0;
+    T* zti = zt ? zt + (size_t)i * zs : nullptr;
     if (d3)
-      MG3<T, C>::scatter_stage(s, st, L0.nx, x, i, z, scale);
+      MG3<T, C>::scatter_stage(s, st, L0.nx, x, i, z, scale, zti);
     else
-      MG::scatter_stage(s, st, L0.nx, x, i, z, scale);
+      MG::scatter_stage(s, st, L0.nx, x, i, z, scale, zti);
   }
   CK_LAUNCH();
   return IRK_OK;

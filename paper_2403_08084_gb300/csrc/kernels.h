@@ -35,12 +35,18 @@ struct MG2 {
   static void restrict_(int S, cudaStream_t st, int nxf, const T* rf, int nxc, T* bc);
   static void prolong_add(int S, cudaStream_t st, int nxc, const T* ec, int nxf, T* xf);
   // d1 != nullptr: also x1 = d1 * out (the block V-cycle's first sweep from a zero guess)
+  // zt != nullptr: the solved stages from zt + j * zstride (V-cycle outputs in precision T, cj scaled
+  // accordingly) instead of the FP64 stage vector z
   static void block_rhs(int SF, cudaStream_t st, int nx, const C* cf, const double* v, const double* z, int i,
-                        const Vec8& cj, T* out, const C* d1 = nullptr, T* x1 = nullptr);
-  static void scatter_stage(int SF, cudaStream_t st, int nx, const T* x, int i, double* z, double scale = 1.0);
+                        const Vec8& cj, T* out, const C* d1 = nullptr, T* x1 = nullptr, const T* zt = nullptr,
+                        size_t zstride = 0);
+  // zt != nullptr: also a copy of x in precision T
+  static void scatter_stage(int SF, cudaStream_t st, int nx, const T* x, int i, double* z, double scale = 1.0,
+                            T* zt = nullptr);
   // IA form: out = v_i - sum_j cj[j] M z_j
   static void block_rhs_mass(int SF, cudaStream_t st, int nx, double hm, const double* v, const double* z, int i,
-                             const Vec8& cj, T* out, const C* d1 = nullptr, T* x1 = nullptr);
+                             const Vec8& cj, T* out, const C* d1 = nullptr, T* x1 = nullptr, const T* zt = nullptr,
+                             size_t zstride = 0);
   static void cast_to(cudaStream_t st, const double* src, T* dst, size_t n);
   static void cast_from(cudaStream_t st, const T* src, double* dst, size_t n);
   // coarsest level (nxc nodes per axis, (nxc - 2)^2 unknowns in row-major interior order)
@@ -76,8 +82,9 @@ struct MG3 {
   static void restrict_(int S, cudaStream_t st, int nf, const T* rf, int nc, T* bc);
   static void prolong_add(int S, cudaStream_t st, int nc, const T* ec, int nf, T* xf);
   static void block_rhs(int SF, cudaStream_t st, int n, const Cls4& kc, const double* v, const double* z, int i,
-                        const Vec8& cj, T* out);
-  static void scatter_stage(int SF, cudaStream_t st, int n, const T* x, int i, double* z, double scale = 1.0);
+                        const Vec8& cj, T* out, const T* zt = nullptr, size_t zstride = 0);
+  static void scatter_stage(int SF, cudaStream_t st, int n, const T* x, int i, double* z, double scale = 1.0,
+                            T* zt = nullptr);
   static void coarse_solve(int S, cudaStream_t st, int nint, const C* binv, const int* map, const T* b, T* x);
 };
 

@@ -186,11 +186,16 @@ __global__ void __launch_bounds__(kBX* kBY) prolong_add_kernel(int nxc, const T*
 // out = v_i - sum_j cj[j] K z_j  (cj[j] = dt a_ij for the stages already solved, else 0).
 // d1 != nullptr: also x1 = d1 * out, the first Jacobi sweep of the block's V-cycle from a zero guess
 // (d1 = omega / diag of the block), so that the V-cycle starts at its second sweep.
-template <typename T, typename C, int SF>
+// LOWZ (FP32 / BF16 V-cycles): the solved stages are read from zt + j * zstride, a stage-major copy
+// of the V-cycle outputs in their own precision, instead of the FP64 stage vector z (no
+// double-to-float conversions, which occupy the FP64 pipe on GB300); cj then includes each stage's
+// output scale.
+template <typename T, typename C, int SF, bool LOWZ>
 __global__ void __launch_bounds__(kBX* kBY) block_rhs_kernel(int nx, const C* __restrict__ cf,
                                                              const double* __restrict__ v,
-                                                             const double* __restrict__ z, int i, VecT<C> cj,
-                                                             unsigned used, T* __restrict__ out,
+                                                             const double* __restrict__ z,
+                                                             const T* __restrict__ zt, size_t zstride, int i,
+                                                             VecT<C> cj, unsigned used, T* __restrict__ out,
                                                              const C* __restrict__ d1, T* __restrict__ x1) {
   IRK_PDL_ENTRY;
   const int ix = 1 + blockIdx.x * kBX + threadIdx.x;
@@ -200,7 +205,12 @@ __global__ void __launch_bounds__(kBX* kBY) block_rhs_kernel(int nx, const C* __
   C acc = static_cast<C>(v[(size_t)p * SF + i]);
 #pragma unroll
   for (int j = 0; j < SF; ++j) {
-    if (used & (1u << j)) acc -= cj.v[j] * k_apply<SF, C>(cf, z, p, nx, j);
+    if (used & (1u << j)) {
+      if constexpr (LOWZ)
+        acc -= cj.v[j] * k_apply<1, C>(cf, zt + (size_t)j * zstride, p, nx, 0);
+      else
+        acc -= cj.v[j] * k_apply<SF, C>(cf, z, p, nx, j);
+    }
   }
   st(out + p, acc);
   if (d1 != nullptr) st(x1 + p, d1[p] * ld<C>(out + p));
@@ -209,11 +219,12 @@ __global__ void __launch_bounds__(kBX* kBY) block_rhs_kernel(int nx, const C* __
 // IA form: out = v_i - sum_j cj[j] M z_j (M: the level's Q1 mass stencil; cjh = cj h^2 / 36).
 // The mass stencil is separable, [1 4 1] (x) [1 4 1]: each thread takes two vertically adjacent
 // interior nodes and shares the row sums of rows iy - 1 .. iy + 2 between them.
-// d1 / x1: as for block_rhs_kernel.
-template <typename T, typename C, int SF>
+// d1 / x1, LOWZ / zt: as for block_rhs_kernel.
+template <typename T, typename C, int SF, bool LOWZ>
 __global__ void __launch_bounds__(kBX* kBY) block_rhs_mass_kernel(int nx, const double* __restrict__ v,
-                                                                  const double* __restrict__ z, int i, VecT<C> cjh,
-                                                                  unsigned used, T* __restrict__ out,
+                                                                  const double* __restrict__ z,
+                                                                  const T* __restrict__ zt, size_t zstride, int i,
+                                                                  VecT<C> cjh, unsigned used, T* __restrict__ out,
                                                                   const C* __restrict__ d1, T* __restrict__ x1) {
   IRK_PDL_ENTRY;
   const int ix = 1 + blockIdx.x * kBX + threadIdx.x;
@@ -226,10 +237,13 @@ __global__ void __launch_bounds__(kBX* kBY) block_rhs_mass_kernel(int nx, const 
 #pragma unroll
   for (int j = 0; j < SF; ++j) {
     if (!(used & (1u << j))) continue;
-    auto row = [&](int q) {
-      return fma(C(4), ld<C>(z + (size_t)q * SF + j), ld<C>(z + (size_t)(q - 1) * SF + j)) +
-             ld<C>(z + (size_t)(q + 1) * SF + j);
+    auto Z = [&](int q) {
+      if constexpr (LOWZ)
+        return ld<C>(zt + (size_t)j * zstride + q);
+      else
+        return ld<C>(z + (size_t)q * SF + j);
     };
+    auto row = [&](int q) { return fma(C(4), Z(q), Z(q - 1)) + Z(q + 1); };
     const C r_m = row(p0 - nx), r_0 = row(p0), r_1 = row(p0 + nx);
     const C r_2 = (iy0 + 2 <= nx - 1) ? row(p0 + 2 * nx) : C(0);
     acc0 -= cjh.v[j] * (fma(C(4), r_0, r_m) + r_1);
@@ -243,16 +257,20 @@ __global__ void __launch_bounds__(kBX* kBY) block_rhs_mass_kernel(int nx, const 
   }
 }
 
-// z[:, i] = scale * x on interior nodes (single-stage x into an SF-interleaved double vector).
+// z[:, i] = scale * x on interior nodes (single-stage x into an SF-interleaved double vector);
+// zt != nullptr: also zt[p] = x[p] (the unscaled V-cycle output kept in its own precision).
 template <typename T, typename C, int SF>
 __global__ void __launch_bounds__(kBX* kBY) scatter_stage_kernel(int nx, const T* __restrict__ x, int i,
-                                                                 double* __restrict__ z, double scale) {
+                                                                 double* __restrict__ z, double scale,
+                                                                 T* __restrict__ zt) {
   IRK_PDL_ENTRY;
   const int ix = 1 + blockIdx.x * kBX + threadIdx.x;
   const int iy = 1 + blockIdx.y * kBY + threadIdx.y;
   if (ix > nx - 2 || iy > nx - 2) return;
   const int p = ix + nx * iy;
-  z[(size_t)p * SF + i] = scale * static_cast<double>(ld<C>(x + p));
+  const T xv = x[p];
+  z[(size_t)p * SF + i] = scale * static_cast<double>(ld<C>(&xv));
+  if (zt != nullptr) zt[p] = xv;
 }
 
 template <typename T, typename C>
@@ -385,22 +403,28 @@ void MG2<T, C>::prolong_add(int S, cudaStream_t st, int nxc, const T* ec, int nx
 }
 template <typename T, typename C>
 void MG2<T, C>::block_rhs(int SF, cudaStream_t st, int nx, const C* cf, const double* v, const double* z, int i,
-                          const Vec8& cj, T* out, const C* d1, T* x1) {
+                          const Vec8& cj, T* out, const C* d1, T* x1, const T* zt, size_t zstride) {
   dim3 g = interior_grid(nx), blk(kBX, kBY);
   unsigned used = 0;
   for (int j = 0; j < SF; ++j)
     if (cj.v[j] != 0.0) used |= 1u << j;
   const VecT<C> c = to_vec<C>(cj);
-  IRK_DISPATCH_S(SF, launch_k(block_rhs_kernel<T, C, SS>, g, blk, 0, st, nx, cf, v, z, i, c, used, out, d1, x1));
+  if (zt != nullptr) {
+    IRK_DISPATCH_S(SF, launch_k(block_rhs_kernel<T, C, SS, true>, g, blk, 0, st, nx, cf, v, z, zt, zstride, i, c,
+                                used, out, d1, x1));
+  } else {
+    IRK_DISPATCH_S(SF, launch_k(block_rhs_kernel<T, C, SS, false>, g, blk, 0, st, nx, cf, v, z, zt, zstride, i, c,
+                                used, out, d1, x1));
+  }
 }
 template <typename T, typename C>
-void MG2<T, C>::scatter_stage(int SF, cudaStream_t st, int nx, const T* x, int i, double* z, double scale) {
+void MG2<T, C>::scatter_stage(int SF, cudaStream_t st, int nx, const T* x, int i, double* z, double scale, T* zt) {
   dim3 g = interior_grid(nx), blk(kBX, kBY);
-  IRK_DISPATCH_S(SF, launch_k(scatter_stage_kernel<T, C, SS>, g, blk, 0, st, nx, x, i, z, scale));
+  IRK_DISPATCH_S(SF, launch_k(scatter_stage_kernel<T, C, SS>, g, blk, 0, st, nx, x, i, z, scale, zt));
 }
 template <typename T, typename C>
 void MG2<T, C>::block_rhs_mass(int SF, cudaStream_t st, int nx, double hm, const double* v, const double* z, int i,
-                               const Vec8& cj, T* out, const C* d1, T* x1) {
+                               const Vec8& cj, T* out, const C* d1, T* x1, const T* zt, size_t zstride) {
   const int m = nx - 2;
   dim3 g((m + kBX - 1) / kBX, ((m + 1) / 2 + kBY - 1) / kBY), blk(kBX, kBY);  // two rows per thread
   unsigned used = 0;
@@ -410,7 +434,13 @@ void MG2<T, C>::block_rhs_mass(int SF, cudaStream_t st, int nx, double hm, const
     cjh.v[j] = cj.v[j] * hm;
   }
   const VecT<C> c = to_vec<C>(cjh);
-  IRK_DISPATCH_S(SF, launch_k(block_rhs_mass_kernel<T, C, SS>, g, blk, 0, st, nx, v, z, i, c, used, out, d1, x1));
+  if (zt != nullptr) {
+    IRK_DISPATCH_S(SF, launch_k(block_rhs_mass_kernel<T, C, SS, true>, g, blk, 0, st, nx, v, z, zt, zstride, i, c,
+                                used, out, d1, x1));
+  } else {
+    IRK_DISPATCH_S(SF, launch_k(block_rhs_mass_kernel<T, C, SS, false>, g, blk, 0, st, nx, v, z, zt, zstride, i, c,
+                                used, out, d1, x1));
+  }
 }
 template <typename T, typename C>
 void MG2<T, C>::cast_to(cudaStream_t st, const double* src, T* dst, size_t n) {

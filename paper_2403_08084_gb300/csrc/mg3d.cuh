@@ -159,10 +159,12 @@ __global__ void __launch_bounds__(k3X* k3Y* k3Z) prolong_add3_kernel(int nc, con
 }
 
 // out = v_i - sum_j cj[j] K z_j (triangular preconditioners), K given by its class values kc.
-template <typename T, typename C, int SF>
+// LOWZ / zt: as for the 2D block_rhs_kernel.
+template <typename T, typename C, int SF, bool LOWZ>
 __global__ void __launch_bounds__(k3X* k3Y* k3Z) block_rhs3_kernel(int n, ClsT<C> kc, const double* __restrict__ v,
-                                                                   const double* __restrict__ z, int i, VecT<C> cj,
-                                                                   unsigned used, T* __restrict__ out) {
+                                                                   const double* __restrict__ z,
+                                                                   const T* __restrict__ zt, size_t zstride, int i,
+                                                                   VecT<C> cj, unsigned used, T* __restrict__ out) {
   IRK_PDL_ENTRY;
   IRK_3D_INDEX
   C acc = static_cast<C>(v[(size_t)p * SF + i]);
@@ -170,7 +172,10 @@ __global__ void __launch_bounds__(k3X* k3Y* k3Z) block_rhs3_kernel(int n, ClsT<C
   for (int j = 0; j < SF; ++j) {
     if (used & (1u << j)) {
       C cs[4];
-      class_sums3<SF, C>(z, p, n, j, cs);
+      if constexpr (LOWZ)
+        class_sums3<1, C>(zt + (size_t)j * zstride, p, n, 0, cs);
+      else
+        class_sums3<SF, C>(z, p, n, j, cs);
       acc -= cj.v[j] * class_apply<C>(kc.v[0], cs);
     }
   }
@@ -179,10 +184,13 @@ __global__ void __launch_bounds__(k3X* k3Y* k3Z) block_rhs3_kernel(int n, ClsT<C
 
 template <typename T, typename C, int SF>
 __global__ void __launch_bounds__(k3X* k3Y* k3Z) scatter_stage3_kernel(int n, const T* __restrict__ x, int i,
-                                                                       double* __restrict__ z, double scale) {
+                                                                       double* __restrict__ z, double scale,
+                                                                       T* __restrict__ zt) {
   IRK_PDL_ENTRY;
   IRK_3D_INDEX
-  z[(size_t)p * SF + i] = scale * static_cast<double>(ld<C>(x + p));
+  const T xv = x[p];
+  z[(size_t)p * SF + i] = scale * static_cast<double>(ld<C>(&xv));
+  if (zt != nullptr) zt[p] = xv;
 }
 
 template <typename T, typename C>
@@ -251,17 +259,24 @@ void MG3<T, C>::prolong_add(int S, cudaStream_t st, int nc, const T* ec, int nf,
 }
 template <typename T, typename C>
 void MG3<T, C>::block_rhs(int SF, cudaStream_t st, int n, const Cls4& kc, const double* v, const double* z, int i,
-                          const Vec8& cj, T* out) {
+                          const Vec8& cj, T* out, const T* zt, size_t zstride) {
   unsigned used = 0;
   for (int j = 0; j < SF; ++j)
     if (cj.v[j] != 0.0) used |= 1u << j;
   const ClsT<C> c = to_cls<C>(kc);
   const VecT<C> w = to_vec<C>(cj);
-  IRK_DISPATCH_S3(SF, launch_k(block_rhs3_kernel<T, C, SS>, interior_grid3(n), dim3(k3X, k3Y, k3Z), 0, st, n, c, v, z, i, w, used, out));
+  if (zt != nullptr) {
+    IRK_DISPATCH_S3(SF, launch_k(block_rhs3_kernel<T, C, SS, true>, interior_grid3(n), dim3(k3X, k3Y, k3Z), 0, st, n, c,
+                                 v, z, zt, zstride, i, w, used, out));
+  } else {
+    IRK_DISPATCH_S3(SF, launch_k(block_rhs3_kernel<T, C, SS, false>, interior_grid3(n), dim3(k3X, k3Y, k3Z), 0, st, n, c,
+                                 v, z, zt, zstride, i, w, used, out));
+  }
 }
 template <typename T, typename C>
-void MG3<T, C>::scatter_stage(int SF, cudaStream_t st, int n, const T* x, int i, double* z, double scale) {
-  IRK_DISPATCH_S3(SF, launch_k(scatter_stage3_kernel<T, C, SS>, interior_grid3(n), dim3(k3X, k3Y, k3Z), 0, st, n, x, i, z, scale));
+void MG3<T, C>::scatter_stage(int SF, cudaStream_t st, int n, const T* x, int i, double* z, double scale, T* zt) {
+  IRK_DISPATCH_S3(SF, launch_k(scatter_stage3_kernel<T, C, SS>, interior_grid3(n), dim3(k3X, k3Y, k3Z), 0, st, n, x, i, z,
+                               scale, zt));
 }
 template <typename T, typename C>
 void MG3<T, C>::coarse_solve(int S, cudaStream_t st, int nint, const C* binv, const int* map, const T* b, T* x) {
