@@ -57,8 +57,8 @@ extern "C" {
 #define IRK_PC_MONOLITHIC 4 /* monolithic multigrid (Sec. 3, monolithic multigrid): one V-cycle
                             on the whole stage system with stage-coupled point-block Jacobi
                             relaxation (additive Schwarz on Q1 vertex patches) and an exact
-                            coupled coarsest solve; dim = 2, AI splitting, FGMRES; not
-                            available for the adjoint (transposed) preconditioner         */
+                            coupled coarsest solve; dim = 2, AI splitting, FGMRES; the
+                            transposed preconditioner is the exactly transposed cycle     */
 
 /* Arnoldi orthogonalisation (the paper does not fix one) */
 #define IRK_ORTH_CGS2 0 /* classical Gram-Schmidt, always two passes                       */

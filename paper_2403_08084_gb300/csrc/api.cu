@@ -884,8 +884,10 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2, b
 // vectors: x0 = V(b0) for the whole system I (x) M + dt A (x) K, with stage-coupled point-block
 // Jacobi relaxation on every level and the exact coupled coarsest solve.  x0 may be nullptr (the
 // result stays in a level buffer, which is returned).
+// transpose: the transposed cycle (the adjoint's preconditioner): S^T = I (x) M + dt A^T (x) K, D^{-T},
+// inv^T; the caller swaps nu1 and nu2, and R = P^T keeps the transfer pair.
 template <typename T, typename C>
-T* mmg_vcycle(irk_handle* h, const T* b0, T* x0, int nu1, int nu2) {
+T* mmg_vcycle(irk_handle* h, const T* b0, T* x0, int nu1, int nu2, bool transpose = false) {
   using MG = MG2<T, C>;
   using P = Prec<T, C>;
   constexpr bool f64 = std::is_same<C, double>::value;
@@ -893,7 +895,8 @@ T* mmg_vcycle(irk_handle* h, const T* b0, T* x0, int nu1, int nu2) {
   const double p = sizeof(T), c = sizeof(C);
   cudaStream_t st = h->st;
   Mat4 mix{};
-  for (int e = 0; e < s * s; ++e) mix.v[e] = h->dt * h->A[e];
+  for (int i = 0; i < s; ++i)
+    for (int j = 0; j < s; ++j) mix.v[i * s + j] = h->dt * (transpose ? h->A[j * s + i] : h->A[i * s + j]);
   auto cls = [&](const Level& Lv, int fine_class) {
     if (&Lv == &h->lev[0]) return fine_class;
     return Lv.nx >= kMgLargeNx ? IRK_K_MG_COARSE : IRK_K_MG_TAIL;
@@ -904,7 +907,7 @@ T* mmg_vcycle(irk_handle* h, const T* b0, T* x0, int nu1, int nu2) {
     const double n = interior(Lv);
     KScope k(h, cls(Lv, IRK_K_JACOBI), n * (s * (xin ? 3 : 2) * p + kCoef2 * c + s * s * c),
              n * (xin ? s * (20.0 + 2 * s) + 2.0 * s * s : 2.0 * s * s));
-    MG::mmg_smooth(s, st, Lv.nx, P::cf(Lv), Lv.hm, mix, blk(Lv), xin, b, xout);
+    MG::mmg_smooth(s, st, Lv.nx, P::cf(Lv), Lv.hm, mix, blk(Lv), xin, b, xout, transpose);
   };
   std::vector<T*> cur(L, nullptr);
   const T* bl = b0;
@@ -939,7 +942,7 @@ T* mmg_vcycle(irk_handle* h, const T* b0, T* x0, int nu1, int nu2) {
     T* xc = (L == 1 && x0) ? x0 : (T*)Lc.xa;
     const double nm = (double)s * h->nint;
     KScope k(h, IRK_K_COARSE, nm * nm * c + 2 * nm * p, 2.0 * nm * nm);
-    MG::mmg_coarse_solve(s, st, Lc.nx, f64 ? (const C*)h->minv_d : (const C*)h->minv_f, bl, xc);
+    MG::mmg_coarse_solve(s, st, Lc.nx, f64 ? (const C*)h->minv_d : (const C*)h->minv_f, bl, xc, transpose);
     cur[L - 1] = xc;
   }
   for (int l = L - 2; l >= 0; --l) {
@@ -979,15 +982,14 @@ int precond_apply(irk_handle* h, const double* v, double* z, bool transpose) {
   const double p = sizeof(T), c = sizeof(C), ne = (double)h->ne;
   const bool ia = (h->opt.splitting == IRK_SPLIT_IA);
   if (h->opt.precond == IRK_PC_MONOLITHIC) {
-    if (transpose) return fail(IRK_EINVAL, "the transposed monolithic multigrid cycle is not implemented");
     if constexpr (std::is_same<T, double>::value) {
-      mmg_vcycle<T, C>(h, v, z, nu1, nu2);
+      mmg_vcycle<T, C>(h, v, z, nu1, nu2, transpose);
     } else {
       {
         KScope k(h, IRK_K_OTHER, ne * (8 + p), 0);
         MG::cast_to(st, v, (T*)L0.b, h->ne);
       }
-      T* x = mmg_vcycle<T, C>(h, (const T*)L0.b, nullptr, nu1, nu2);
+      T* x = mmg_vcycle<T, C>(h, (const T*)L0.b, nullptr, nu1, nu2, transpose);
       KScope k(h, IRK_K_OTHER, ne * (8 + p), 0);
       MG::cast_from(st, x, z, h->ne);
     }
@@ -1855,8 +1857,6 @@ int irk_step_adjoint(irk_handle* h, const double* u_n, const double* stages, con
   if (!h || !u_n || !stages || !lam_np1 || !lam_n) return fail(IRK_EINVAL, "null argument");
   if (h->dim != 2) return fail(IRK_EINVAL, "irk_step_adjoint is implemented for dim = 2");
   if (h->opt.splitting != IRK_SPLIT_AI) return fail(IRK_EINVAL, "irk_step_adjoint needs the AI splitting");
-  if (h->opt.precond == IRK_PC_MONOLITHIC)
-    return fail(IRK_EINVAL, "irk_step_adjoint: the transposed monolithic multigrid cycle is not implemented");
   const int s = h->s;
   const size_t nn = h->lev[0].nn, nb = nn * 8, sb = h->ne * 8, gb = (size_t)h->N * h->N * 8;
   const void *ud, *kd, *ld;

@@ -61,11 +61,13 @@ struct MG2 {
   // monolithic multigrid (mmg2d.cuh) on S-interleaved level vectors, mix = dt A (or dt A^T):
   // x_out = x_in + omega D^{-1} (b - S_l x_in) with the per-node s x s inverses dblk (x_in == nullptr:
   // zero guess); r = b - S_l x; exact coarsest solve with the dense inverse of the coupled system.
+  // transpose: the relaxation with D^{-T} (pass mix = dt A^T) and the coarsest solve with inv^T
   static void mmg_smooth(int S, cudaStream_t st, int nx, const C* cf, double hm, const Mat4& mix, const C* dblk,
-                         const T* xin, const T* b, T* xout);
+                         const T* xin, const T* b, T* xout, bool transpose = false);
   static void mmg_residual(int S, cudaStream_t st, int nx, const C* cf, double hm, const Mat4& mix, const T* x,
                            const T* b, T* r);
-  static void mmg_coarse_solve(int S, cudaStream_t st, int nxc, const C* inv, const T* b, T* x);
+  static void mmg_coarse_solve(int S, cudaStream_t st, int nxc, const C* inv, const T* b, T* x,
+                               bool transpose = false);
 };
 
 // Coarse levels whose finer grid has at least this many nodes per axis run the fused V-cycle legs

@@ -12,7 +12,8 @@
 namespace irk {
 
 // x_out = x_in + omega D^{-1} (b - S_l x_in) at interior nodes (x_in == nullptr: zero guess).
-template <typename T, typename C, int S>
+// TRANS: the transposed relaxation (D^{-T}; mix is then dt A^T), for the adjoint's transposed cycle.
+template <typename T, typename C, int S, bool TRANS>
 __global__ void __launch_bounds__(kBX* kBY) mmg_smooth_kernel(int nx, const C* __restrict__ cf, C hm, MatT<C> mix,
                                                               const C* __restrict__ dblk, const T* __restrict__ xin,
                                                               const T* __restrict__ b, T* __restrict__ xout) {
@@ -42,7 +43,7 @@ __global__ void __launch_bounds__(kBX* kBY) mmg_smooth_kernel(int nx, const C* _
   for (int i = 0; i < S; ++i) {
     C acc = (xin != nullptr) ? ld<C>(xin + (size_t)p * S + i) : C(0);
 #pragma unroll
-    for (int j = 0; j < S; ++j) acc += D[i * S + j] * r[j];
+    for (int j = 0; j < S; ++j) acc += (TRANS ? D[j * S + i] : D[i * S + j]) * r[j];
     st(xout + (size_t)p * S + i, acc);
   }
 }
@@ -109,6 +110,31 @@ __global__ void __launch_bounds__(kCoarseThreads) mmg_coarse_solve_kernel(int n,
   if (lane == 0 && r < n) st(x + (size_t)coarse_node(r / S, nxc) * S + r % S, acc);
 }
 
+// The transposed coarsest solve x = inv^T b: one thread per output r, reading column r of inv
+// (coalesced across a warp's consecutive r); b staged in shared memory.
+template <typename T, typename C, int S>
+__global__ void __launch_bounds__(kCoarseThreads) mmg_coarse_solve_t_kernel(int n, int nxc, const C* __restrict__ inv,
+                                                                            const T* __restrict__ b,
+                                                                            T* __restrict__ x) {
+  IRK_PDL_ENTRY;
+  extern __shared__ unsigned char smem_raw[];
+  C* bs = reinterpret_cast<C*>(smem_raw);
+  for (int c = threadIdx.x; c < n; c += kCoarseThreads) bs[c] = ld<C>(b + (size_t)coarse_node(c / S, nxc) * S + c % S);
+  __syncthreads();
+  const int r = blockIdx.x * kCoarseThreads + threadIdx.x;
+  if (r >= n) return;
+  C a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+  int c = 0;
+  for (; c + 3 < n; c += 4) {
+    a0 += inv[(size_t)c * n + r] * bs[c];
+    a1 += inv[(size_t)(c + 1) * n + r] * bs[c + 1];
+    a2 += inv[(size_t)(c + 2) * n + r] * bs[c + 2];
+    a3 += inv[(size_t)(c + 3) * n + r] * bs[c + 3];
+  }
+  for (; c < n; ++c) a0 += inv[(size_t)c * n + r] * bs[c];
+  st(x + (size_t)coarse_node(r / S, nxc) * S + r % S, (a0 + a1) + (a2 + a3));
+}
+
 #define IRK_MMG_DISPATCH(S, ...)                              \
   switch (S) {                                                \
     case 1: { constexpr int SS = 1; __VA_ARGS__; } break;     \
@@ -120,10 +146,15 @@ __global__ void __launch_bounds__(kCoarseThreads) mmg_coarse_solve_kernel(int n,
 
 template <typename T, typename C>
 void MG2<T, C>::mmg_smooth(int S, cudaStream_t st, int nx, const C* cf, double hm, const Mat4& mix, const C* dblk,
-                           const T* xin, const T* b, T* xout) {
+                           const T* xin, const T* b, T* xout, bool transpose) {
   const MatT<C> m = to_mat<C>(mix);
-  IRK_MMG_DISPATCH(S, launch_k(mmg_smooth_kernel<T, C, SS>, interior_grid(nx), dim3(kBX, kBY), 0, st, nx, cf,
-                               (C)hm, m, dblk, xin, b, xout));
+  if (transpose) {
+    IRK_MMG_DISPATCH(S, launch_k(mmg_smooth_kernel<T, C, SS, true>, interior_grid(nx), dim3(kBX, kBY), 0, st, nx, cf,
+                                 (C)hm, m, dblk, xin, b, xout));
+  } else {
+    IRK_MMG_DISPATCH(S, launch_k(mmg_smooth_kernel<T, C, SS, false>, interior_grid(nx), dim3(kBX, kBY), 0, st, nx, cf,
+                                 (C)hm, m, dblk, xin, b, xout));
+  }
 }
 
 template <typename T, typename C>
@@ -135,10 +166,19 @@ void MG2<T, C>::mmg_residual(int S, cudaStream_t st, int nx, const C* cf, double
 }
 
 template <typename T, typename C>
-void MG2<T, C>::mmg_coarse_solve(int S, cudaStream_t st, int nxc, const C* inv, const T* b, T* x) {
+void MG2<T, C>::mmg_coarse_solve(int S, cudaStream_t st, int nxc, const C* inv, const T* b, T* x, bool transpose) {
   const int n = S * (nxc - 2) * (nxc - 2);
-  const int g = (n + kCoarseThreads / 32 - 1) / (kCoarseThreads / 32);
   const size_t shm = sizeof(C) * (size_t)n;
+  if (transpose) {
+    const int g = (n + kCoarseThreads - 1) / kCoarseThreads;  // one thread per output
+    IRK_MMG_DISPATCH(S, {
+      auto kern = mmg_coarse_solve_t_kernel<T, C, SS>;
+      if (shm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+      launch_k(kern, dim3(g), dim3(kCoarseThreads), shm, st, n, nxc, inv, b, x);
+    });
+    return;
+  }
+  const int g = (n + kCoarseThreads / 32 - 1) / (kCoarseThreads / 32);  // one warp per row
   IRK_MMG_DISPATCH(S, {
     auto kern = mmg_coarse_solve_kernel<T, C, SS>;
     if (shm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);

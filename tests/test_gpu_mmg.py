@@ -90,9 +90,52 @@ def test_mmg_rejects_unsupported_configurations():
         Solver(16, tab, 0.1, precond="monolithic", splitting="ia")
     with pytest.raises(IRKError):
         Solver(16, tab, 0.1, dim=3, levels=2, precond="monolithic")
-    with Solver(16, tab, 0.1, levels=2, precond="monolithic") as sv:
-        nn = sv.n_nodes
-        with pytest.raises(IRKError):
-            sv.apply_preconditioner(np.zeros(nn * 2), np.zeros(nn * 2), transpose=True)
-        with pytest.raises(IRKError):
-            sv.step_adjoint(np.zeros(nn), np.zeros(nn * 2), np.zeros(nn), np.zeros(nn))
+    with pytest.raises(IRKError):  # coupled coarsest system above 4096 unknowns
+        Solver(128, PT.radau_iia(3), 0.1, levels=2, precond="monolithic")
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_mmg_transposed_cycle_is_the_transpose(prec, tol):
+    """<P^{-T} u, v> = <u, P^{-1} v> for random u, v: the transposed cycle (V(2,2) with A^T, D^{-T}, the
+    transposed coarse inverse and the same transfer pair) is the exact transpose of the forward cycle."""
+    N, levels, s, dt = 48, 3, 3, 1 / 32
+    kap = W.lognormal_kappa(2, N, 0.5, 85)
+    with Solver(N, PT.radau_iia(s), dt, kappa=kap, levels=levels, precond="monolithic", vcycle=prec) as sv:
+        u = torch.from_numpy(W.random_nodal(2, N, seed=86, s=s)).cuda()
+        v = torch.from_numpy(W.random_nodal(2, N, seed=87, s=s)).cuda()
+        pu, pv = torch.empty_like(u), torch.empty_like(v)
+        sv.apply_preconditioner(u, pu, transpose=True)
+        sv.apply_preconditioner(v, pv)
+        lhs, rhs = float(torch.dot(pu, v)), float(torch.dot(u, pv))
+    assert abs(lhs - rhs) <= tol * abs(rhs)
+
+
+def test_mmg_adjoint_gradient_matches_oracle():
+    """The discrete adjoint with the transposed monolithic preconditioner gives the oracle's gradient."""
+    from oracle import adjoint as OA
+    from paper_2403_08084_gb300 import adjoint as AD
+
+    N, dt, steps = 32, 1 / 50, 3
+    kap = W.lognormal_kappa(2, N, 0.5, 88)
+    tab, ot = PT.radau_iia(3), OT.radau_iia(3)
+    sv = Solver(N, tab, dt, kappa=kap, levels=2, precond="monolithic", rtol=1e-13)
+    u0 = torch.from_numpy(W.sine_initial(2, N)).cuda()
+    f = torch.from_numpy(W.sine_load_space(2, N)).cuda()
+    ut = torch.from_numpy(W.random_nodal(2, N, seed=89)).cuda()
+
+    def coef(n):
+        return [W.sine_load_time(2, (n + c) * dt) for c in tab.c]
+
+    th = torch.from_numpy(np.log(kap)).cuda().requires_grad_(True)
+    uN = AD.trajectory(sv, th, u0, steps, f_space=f, f_coef=coef, checkpoint=2)
+    J = AD.mass_norm2(sv, uN - ut)
+    J.backward()
+    g = th.grad.cpu().numpy()
+    sv.close()
+    d = fem.Discretisation(2, N, kap)
+    Fs = d.to_interior(W.sine_load_space(2, N))
+    loads = np.stack([np.stack([W.sine_load_time(2, (n + c) * dt) * Fs for c in ot.c]) for n in range(steps)])
+    J_ref, g_ref, _ = OA.gradient(2, N, kap, ot, dt, steps, d.to_interior(u0.cpu().numpy()), loads,
+                                  d.to_interior(ut.cpu().numpy()))
+    assert abs(J.item() - J_ref) <= 1e-10 * abs(J_ref)
+    assert np.linalg.norm(g - g_ref) <= 1e-9 * np.linalg.norm(g_ref)
