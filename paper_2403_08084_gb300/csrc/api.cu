@@ -688,8 +688,9 @@ struct Prec<__nv_bfloat16, float> {
 // x0 = V(b0) for blocks st0 .. st0+S-1 (S == s: all blocks batched; S == 1: block st0).
 // b0 and x0 are S-interleaved level-0 vectors of precision T; x0 may be nullptr, in
 // which case the result is left in an internal buffer that is returned.
-// first_done: the finest level's first sweep from a zero guess has already been written to the
-// buffer first_sweep_buffer() names (by the kernel that formed b0).
+// first_done: the finest level's first sweep from a zero guess has already been written, by the
+// kernel that formed b0, to the buffer that sweep would write (level 0's xa if nu1 + nu2 is odd,
+// else xb; see precond_apply).
 template <typename T, typename C>
 T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2, bool first_done = false) {
   using MG = MG2<T, C>;
@@ -1164,7 +1165,7 @@ int norm2(irk_handle* h, const double* v, int slot) {
 }
 
 // ----------------------------------------------------------------------------
-// FGMRES (right preconditioned, CGS2 Arnoldi, Givens on the device)
+// FGMRES (right preconditioned; CGS2, one-pass CGS or DGKS Arnoldi; Givens on the device)
 // ----------------------------------------------------------------------------
 // One Arnoldi step of FGMRES for basis index j: z_j = P^{-1} v_j, w = S z_j,
 // orthogonalisation, Givens update and normalisation; ends by copying
