@@ -142,19 +142,16 @@ def source_hash() -> str:
 
 
 def ncu_traffic(kernel_class: str, workload: str):
-    """DRAM bytes per launch of a kernel class from the committed ncu summary, if it
-    was taken on the current kernel sources; else None."""
+    """The committed ncu record of a kernel class (DRAM bytes per launch, FP64 pipe activity), if it
+    was taken on the current kernel sources and this workload; else None."""
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
             t = json.load(f)
     except Exception:
         return None
-    if t.get("source_sha") != source_hash():
+    if t.get("source_sha") != source_hash() or t.get("workload") != workload:
         return None
-    e = t.get("classes", {}).get(kernel_class)
-    if not e:
-        return None
-    return e.get("bytes_per_launch_full_size")
+    return t.get("classes", {}).get(kernel_class)
 
 
 # ----------------------------------------------------------------------------
@@ -307,7 +304,9 @@ def gpu_arm(args, rank, world):
         else:
             roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(gbs / hbm, 4),
                     "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)"}
-        roof.update({"kernel": dominant, "traffic": ncu_traffic(dominant, wl.name), "launches": cls["timed_launches"],
+        rec = ncu_traffic(dominant, wl.name) or {}
+        roof.update({"kernel": dominant, "traffic": rec.get("bytes_per_launch_full_size"),
+                     "ncu_fp64_pipe_active_pct": rec.get("fp64_pipe_active_pct"), "launches": cls["timed_launches"],
                      "timing": "CUDA events on the library stream around each launch, replay of the K timed steps",
                      "avg_launch_us": round(avg_s * 1e6, 2), "algorithmic_bytes_per_launch": round(bpl),
                      "algorithmic_flops_per_launch": round(fpl), "achieved_gbs": round(gbs, 1),
