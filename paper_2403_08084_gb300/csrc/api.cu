@@ -64,12 +64,13 @@ struct Level {
   size_t nn = 0;
   double hm = 0.0;  // h^2 / 36 (2D mass stencil scale)
   double mcls[4] = {0, 0, 0, 0}, kcls[4] = {0, 0, 0, 0};  // 3D: Q1 mass / stiffness class values
-  std::vector<double> cf_host;
+  std::vector<double> cf_host;  // stencil records {D, E, N, NE, NW} per node (node-major)
+  // device copies are planar (one plane of nn values per coefficient, see planar())
   double* cf_d = nullptr;     // stencil records, double
   float* cf_f = nullptr;      // stencil records, float
   double* brec_d = nullptr;   // FP64 V-cycles: records of M + dt a_ii K, stage-major
   float* brec_f = nullptr;    // FP32 / BF16 V-cycles: the same records in FP32
-  double* mblk_d = nullptr;   // monolithic multigrid: omega (M_pp I + dt K_pp A)^{-1} per node (s x s)
+  double* mblk_d = nullptr;   // monolithic multigrid: omega (M_pp I + dt K_pp A)^{-1} per node (s x s planes)
   float* mblk_f = nullptr;
   double* dinv_d = nullptr;   // omega / diag(B_i): node-major (s per node), then stage-major (nn per stage)
   float* dinv_f = nullptr;
@@ -380,6 +381,18 @@ int validate(const irk_mesh* mesh, const irk_tableau* tab, double dt, const irk_
   return IRK_OK;
 }
 
+// Device copy of per-node host data: `aos` holds blocks of nn nodes x k values (node-major); the
+// device layout is planar, value c of node q of block b at [(b k + c) nn + q] (coalesced warp loads).
+template <typename D>
+std::vector<D> planar(const std::vector<double>& aos, size_t nn, int k) {
+  std::vector<D> out(aos.size());
+  const size_t blocks = aos.size() / (nn * k);
+  for (size_t b = 0; b < blocks; ++b)
+    for (size_t q = 0; q < nn; ++q)
+      for (int c = 0; c < k; ++c) out[(b * k + c) * nn + q] = (D)aos[(b * nn + q) * k + c];
+  return out;
+}
+
 // Build the hierarchy's host data and upload it (also used by irk_set_kappa).
 int build_operators_3d(irk_handle* h, const std::vector<double>& sigma) {
   const int s = h->s;
@@ -419,8 +432,10 @@ int build_operators(irk_handle* h) {
     dinv.resize(2 * Lv.nn * s);
     for (size_t q = 0; q < Lv.nn; ++q)
       for (int i = 0; i < s; ++i) dinv[Lv.nn * s + (size_t)i * Lv.nn + q] = dinv[q * s + i];
-    std::vector<float> cff(Lv.cf_host.begin(), Lv.cf_host.end()), dinvf(dinv.begin(), dinv.end());
-    CK(cudaMemcpyAsync(Lv.cf_d, Lv.cf_host.data(), Lv.cf_host.size() * 8, cudaMemcpyHostToDevice, h->st));
+    const std::vector<double> cfd = planar<double>(Lv.cf_host, Lv.nn, kCoef2);
+    const std::vector<float> cff = planar<float>(Lv.cf_host, Lv.nn, kCoef2);
+    std::vector<float> dinvf(dinv.begin(), dinv.end());
+    CK(cudaMemcpyAsync(Lv.cf_d, cfd.data(), cfd.size() * 8, cudaMemcpyHostToDevice, h->st));
     CK(cudaMemcpyAsync(Lv.dinv_d, dinv.data(), dinv.size() * 8, cudaMemcpyHostToDevice, h->st));
     CK(cudaMemcpyAsync(Lv.cf_f, cff.data(), cff.size() * 4, cudaMemcpyHostToDevice, h->st));
     CK(cudaMemcpyAsync(Lv.dinv_f, dinvf.data(), dinvf.size() * 4, cudaMemcpyHostToDevice, h->st));
@@ -428,7 +443,8 @@ int build_operators(irk_handle* h) {
       std::vector<double> blk;
       if (!mmg_block_inverses_2d(Lv.N, Lv.cf_host, Lv.hm, h->A.data(), s, h->dt, h->opt.omega, blk))
         return fail(IRK_EINVAL, "a point block M_pp I + dt K_pp A of level %d is singular", l);
-      std::vector<float> blkf(blk.begin(), blk.end());
+      const std::vector<float> blkf = planar<float>(blk, Lv.nn, s * s);
+      blk = planar<double>(blk, Lv.nn, s * s);
       CK(cudaMemcpyAsync(Lv.mblk_d, blk.data(), blk.size() * 8, cudaMemcpyHostToDevice, h->st));
       CK(cudaMemcpyAsync(Lv.mblk_f, blkf.data(), blkf.size() * 4, cudaMemcpyHostToDevice, h->st));
       CK(cudaStreamSynchronize(h->st));
@@ -436,9 +452,10 @@ int build_operators(irk_handle* h) {
     std::vector<double> brec;
     std::vector<float> brecf;
     if (Lv.brec_d || Lv.brec_f) block_records_2d(Lv.N, Lv.cf_host, Lv.hm, sigma.data(), s, brec);
+    if (Lv.brec_f) brecf = planar<float>(brec, Lv.nn, kCoef2);
+    if (Lv.brec_d) brec = planar<double>(brec, Lv.nn, kCoef2);
     if (Lv.brec_d) CK(cudaMemcpyAsync(Lv.brec_d, brec.data(), brec.size() * 8, cudaMemcpyHostToDevice, h->st));
     if (Lv.brec_f) {
-      brecf.assign(brec.begin(), brec.end());
       CK(cudaMemcpyAsync(Lv.brec_f, brecf.data(), brecf.size() * 4, cudaMemcpyHostToDevice, h->st));
     }
     CK(cudaStreamSynchronize(h->st));  // host vectors above go out of scope
@@ -747,8 +764,13 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2, b
       MG::jacobi(S, st, Lv.nx, cf, Lv.hm, sig, dinv, s_d, xin, b, xout);
     }
   };
-  // 2D coarse levels under V(2, 2): one fused kernel per leg (mg2d_legs.cuh) instead of six launches
-  auto fused_leg = [&](int l) { return !d3 && l >= 1 && nu1 == 2 && nu2 == 2; };
+  // 2D levels under V(2, 2): one fused kernel per leg (mg2d_legs.cuh) instead of six launches; on the
+  // coarse levels, and for FP32 / BF16 cycles also on the finest one (memory-bound there: the legs read
+  // b, the records and the diagonal once instead of three times)
+  constexpr bool lowp = !std::is_same<C, double>::value;
+  auto fused_leg = [&](int l) {
+    return !d3 && nu1 == 2 && nu2 == 2 && (l >= 1 || (lowp && x0 == nullptr && !first_done));
+  };
   auto rec_of = [&](const Level& Lv) {
     const C* rec = P::rec(Lv);
     return rec ? rec + (size_t)st0 * Lv.nn * kCoef2 : nullptr;
@@ -761,7 +783,7 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2, b
     if (fused_leg(l)) {
       const double n = interior(Lv), nc = interior(Lc);
       const bool rec = P::rec(Lv) != nullptr;
-      KScope k(h, coarse_cls(Lv), n * S * (2 * p + c) + n * kCoef2 * c * (rec ? S : 1) + nc * S * p,
+      KScope k(h, cls(Lv, IRK_K_JACOBI), n * S * (2 * p + c) + n * kCoef2 * c * (rec ? S : 1) + nc * S * p,
                n * S * (rec ? 42.0 : 66.0));
       MG::down_leg(S, st, Lv.nx, cf, Lv.hm, sig, rec_of(Lv), Lv.nn * kCoef2, dinv, s_d, bl, (T*)Lv.xa, Lc.nx,
                    (T*)Lc.b);
@@ -853,7 +875,7 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2, b
     if (fused_leg(l)) {
       T* xo = (cur[l] == (T*)Lv.xa) ? (T*)Lv.xb : (T*)Lv.xa;
       const bool rec = P::rec(Lv) != nullptr;
-      KScope k(h, coarse_cls(Lv), nf * S * (4 * p + c) + nf * kCoef2 * c * (rec ? S : 1) + nc * S * p,
+      KScope k(h, cls(Lv, IRK_K_JACOBI), nf * S * (4 * p + c) + nf * kCoef2 * c * (rec ? S : 1) + nc * S * p,
                nf * S * (rec ? 45.0 : 69.0));
       MG::up_leg(S, st, Lv.nx, cf, Lv.hm, sig, rec_of(Lv), Lv.nn * kCoef2, dinv, s_d, cur[l], bfine, Lc.nx,
                  cur[l + 1], xo);
@@ -910,11 +932,31 @@ T* mmg_vcycle(irk_handle* h, const T* b0, T* x0, int nu1, int nu2, bool transpos
              n * (xin ? s * (20.0 + 2 * s) + 2.0 * s * s : 2.0 * s * s));
     MG::mmg_smooth(s, st, Lv.nx, P::cf(Lv), Lv.hm, mix, blk(Lv), xin, b, xout, transpose);
   };
+  // V(2, 2): one fused kernel per leg (mg2d_legs.cuh) instead of five or six launches.  FP32 / BF16 on
+  // every level (the finest one included: memory-bound, the fused legs read b, D and the records once
+  // instead of three times); FP64 only below kMgLargeNx nodes per axis (on larger levels the coupled
+  // relaxation is FP64-pipe-bound and the halo recomputation costs more than the launches it saves)
+  auto fused_leg = [&](int l) {
+    if (nu1 != 2 || nu2 != 2) return false;
+    if (f64) return l >= 1 && h->lev[l].nx < kMgLargeNx;
+    return l >= 1 || x0 == nullptr;
+  };
+  // per node: residual s (20 + 2 s), sweep that plus the block product 2 s^2
+  const double fres = s * (20.0 + 2 * s), fblk = 2.0 * s * s;
   std::vector<T*> cur(L, nullptr);
   const T* bl = b0;
   for (int l = 0; l < L - 1; ++l) {
     Level& Lv = h->lev[l];
     Level& Lc = h->lev[l + 1];
+    if (fused_leg(l)) {
+      const double n = interior(Lv), nc = interior(Lc);
+      KScope k(h, cls(Lv, IRK_K_JACOBI), n * (2 * s * p + kCoef2 * c + s * s * c) + nc * s * p,
+               n * (2 * fres + 3 * fblk) + 12.0 * nc * s);
+      MG::mmg_down_leg(s, st, Lv.nx, P::cf(Lv), Lv.hm, mix, blk(Lv), transpose, bl, (T*)Lv.xa, Lc.nx, (T*)Lc.b);
+      cur[l] = (T*)Lv.xa;
+      bl = (const T*)Lc.b;
+      continue;
+    }
     T* last = (l == 0 && x0) ? x0 : (T*)Lv.xa;
     T* other = (l == 0 && x0) ? (T*)Lv.xa : (T*)Lv.xb;
     T* bufs[2];
@@ -951,6 +993,14 @@ T* mmg_vcycle(irk_handle* h, const T* b0, T* x0, int nu1, int nu2, bool transpos
     Level& Lc = h->lev[l + 1];
     const T* bfine = (l == 0) ? b0 : (const T*)Lv.b;
     const double nf = interior(Lv), nc = interior(Lc);
+    if (fused_leg(l)) {
+      T* xo = (cur[l] == (T*)Lv.xa) ? (T*)Lv.xb : (T*)Lv.xa;
+      KScope k(h, cls(Lv, IRK_K_JACOBI), nf * (3 * s * p + kCoef2 * c + s * s * c) + nc * s * p,
+               nf * (2 * (fres + fblk) + 5.0 * s));
+      MG::mmg_up_leg(s, st, Lv.nx, P::cf(Lv), Lv.hm, mix, blk(Lv), transpose, cur[l], bfine, Lc.nx, cur[l + 1], xo);
+      cur[l] = xo;
+      continue;
+    }
     {
       KScope k(h, cls(Lv, IRK_K_PROLONG), (nc + 2 * nf) * s * p, 5.0 * nf * s);
       MG::prolong_add(s, st, Lc.nx, cur[l + 1], Lv.nx, cur[l]);

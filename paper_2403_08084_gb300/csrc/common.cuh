@@ -20,6 +20,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <cstdlib>
+#include <type_traits>
 #include <utility>
 
 namespace irk {
@@ -155,24 +156,28 @@ __device__ __forceinline__ void st<__nv_bfloat16, double>(__nv_bfloat16* p, doub
 // ----------------------------------------------------------------------------
 // 2D stencil primitives at an interior node p
 // ----------------------------------------------------------------------------
+// Stencil records on the device are planar: coefficient k in {D, E, N, NE, NW} of node q of a level
+// with nx nodes per axis is cf[k nx^2 + q] (a warp's loads of one coefficient are then coalesced).
+// The symmetric 9-point stencil at p, with the neighbour values given by X(dx, dy).
+template <typename C, typename F>
+__device__ __forceinline__ C rec_apply_xy(const C* __restrict__ cf, int p, int nx, F X) {
+  const size_t n = (size_t)nx * nx;
+  C y = cf[p] * X(0, 0);
+  y += cf[n + p] * X(1, 0);
+  y += cf[n + p - 1] * X(-1, 0);
+  y += cf[2 * n + p] * X(0, 1);
+  y += cf[2 * n + p - nx] * X(0, -1);
+  y += cf[3 * n + p] * X(1, 1);
+  y += cf[3 * n + p - nx - 1] * X(-1, -1);
+  y += cf[4 * n + p] * X(-1, 1);
+  y += cf[4 * n + p - nx + 1] * X(1, -1);
+  return y;
+}
+
 // (K x)(p) for one stage i of an S-interleaved vector.
 template <int S, typename C, typename T>
 __device__ __forceinline__ C k_apply(const C* __restrict__ cf, const T* __restrict__ x, int p, int nx, int i) {
-  const C* c0 = cf + (size_t)p * kCoef2;
-  const C* cw = cf + (size_t)(p - 1) * kCoef2;
-  const C* cs = cf + (size_t)(p - nx) * kCoef2;
-  const C* csw = cf + (size_t)(p - nx - 1) * kCoef2;
-  const C* cse = cf + (size_t)(p - nx + 1) * kCoef2;
-  C y = c0[0] * ld<C>(x + (size_t)p * S + i);
-  y += c0[1] * ld<C>(x + (size_t)(p + 1) * S + i);
-  y += cw[1] * ld<C>(x + (size_t)(p - 1) * S + i);
-  y += c0[2] * ld<C>(x + (size_t)(p + nx) * S + i);
-  y += cs[2] * ld<C>(x + (size_t)(p - nx) * S + i);
-  y += c0[3] * ld<C>(x + (size_t)(p + nx + 1) * S + i);
-  y += csw[3] * ld<C>(x + (size_t)(p - nx - 1) * S + i);
-  y += c0[4] * ld<C>(x + (size_t)(p + nx - 1) * S + i);
-  y += cse[4] * ld<C>(x + (size_t)(p - nx + 1) * S + i);
-  return y;
+  return rec_apply_xy<C>(cf, p, nx, [&](int dx, int dy) { return ld<C>(x + (size_t)(p + dx + nx * dy) * S + i); });
 }
 
 // 36/h^2 (M x)(p): the unscaled mass stencil [1 4 1; 4 16 4; 1 4 1].
@@ -188,21 +193,7 @@ __device__ __forceinline__ C m_apply_unscaled(const T* __restrict__ x, int p, in
 // functor F(q) (a vector that is never stored).
 template <typename C, typename F>
 __device__ __forceinline__ C k_apply_f(const C* __restrict__ cf, int p, int nx, F X) {
-  const C* c0 = cf + (size_t)p * kCoef2;
-  const C* cw = cf + (size_t)(p - 1) * kCoef2;
-  const C* cs = cf + (size_t)(p - nx) * kCoef2;
-  const C* csw = cf + (size_t)(p - nx - 1) * kCoef2;
-  const C* cse = cf + (size_t)(p - nx + 1) * kCoef2;
-  C y = c0[0] * X(p);
-  y += c0[1] * X(p + 1);
-  y += cw[1] * X(p - 1);
-  y += c0[2] * X(p + nx);
-  y += cs[2] * X(p - nx);
-  y += c0[3] * X(p + nx + 1);
-  y += csw[3] * X(p - nx - 1);
-  y += c0[4] * X(p + nx - 1);
-  y += cse[4] * X(p - nx + 1);
-  return y;
+  return rec_apply_xy<C>(cf, p, nx, [&](int dx, int dy) { return X(p + dx + nx * dy); });
 }
 
 template <typename C, typename F>

@@ -68,6 +68,12 @@ struct MG2 {
                            const T* b, T* r);
   static void mmg_coarse_solve(int S, cudaStream_t st, int nxc, const C* inv, const T* b, T* x,
                                bool transpose = false);
+  // fused V(2, 2) legs of a coarse level of the monolithic cycle (mg2d_legs.cuh), as down_leg / up_leg
+  // with the stage-coupled relaxation
+  static void mmg_down_leg(int S, cudaStream_t st, int nxf, const C* cf, double hm, const Mat4& mix, const C* dblk,
+                           bool transpose, const T* b, T* xout, int nxc, T* bc);
+  static void mmg_up_leg(int S, cudaStream_t st, int nxf, const C* cf, double hm, const Mat4& mix, const C* dblk,
+                         bool transpose, const T* xin, const T* b, int nxc, const T* ec, T* xout);
 };
 
 // Coarse levels whose finer grid has at least this many nodes per axis run the fused V-cycle legs

@@ -1,5 +1,6 @@
-// Fused legs of the 2D V-cycle on the coarse levels (Sec. 3.1's multigrid
-// approximation of a diagonal block B = M + sigma K), V(2, 2).
+// Fused legs of the 2D V-cycles on the coarse levels, V(2, 2): the block V-cycles of Sec. 3.1 (the
+// multigrid approximation of a diagonal block B = M + sigma K) and the monolithic cycle of Sec. 3
+// (monolithic multigrid, all stages coupled).
 //
 // On the coarse levels the six kernels of a level (two pre-sweeps, residual,
 // restriction, prolongation, two post-sweeps) each process so few nodes that a
@@ -12,38 +13,24 @@
 // stencils need on a halo in shared memory (x1 on a halo of 2 and x2 on a halo
 // of 1 for the down leg, y0 on 2 and y1 on 1 for the up leg).  The arithmetic at
 // every node is that of the separate kernels (same stencil records, same order of
-// operations); only the intermediate vectors stay in shared memory in the
-// arithmetic type C instead of being stored in T.
+// operations), and the intermediate vectors kept in shared memory (in the arithmetic
+// type C) are rounded to the storage type T as those kernels store them: with BF16
+// storage, a residual formed from the unrounded iterate would not belong to the
+// iterate that the coarse correction is added to.
 //
-// Stencil records: FP64 V-cycles (REC) store B_i per stage (stage-major, stride
-// rstride); FP32 / BF16 ones form hm M + sigma_i K from the stiffness records cf.
+// The relaxation J is a policy acting on all S stages of a node at once:
+//   BlockRelax  independent blocks, x_i += d_i (b_i - B_i x_i) with d_i = omega / diag(B_i); B_i from the
+//               stage's record (FP64 V-cycles: REC, stage-major with stride rstride) or hm M + sigma_i K
+//               formed from the stiffness records cf (FP32 / BF16);
+//   MonoRelax   the monolithic cycle's stage-coupled point-block Jacobi, x += W_p (b - S_l x) with
+//               S_l x_i = hm M x_i + sum_j mix_ij K x_j and W_p = omega D_p^{-1} per node (S x S,
+//               row-major; TRANS applies W_p^T, for the transposed cycle).
 #pragma once
 
 #include "common.cuh"
 #include "kernels.h"
 
 namespace irk {
-
-// The level's 9-point record stencil at node p, the neighbour values given by X(dx, dy).
-// Same products and order as k_apply.
-template <typename C, typename F>
-__device__ __forceinline__ C rec_apply_xy(const C* __restrict__ cf, int p, int nx, F X) {
-  const C* c0 = cf + (size_t)p * kCoef2;
-  const C* cw = cf + (size_t)(p - 1) * kCoef2;
-  const C* cs = cf + (size_t)(p - nx) * kCoef2;
-  const C* csw = cf + (size_t)(p - nx - 1) * kCoef2;
-  const C* cse = cf + (size_t)(p - nx + 1) * kCoef2;
-  C y = c0[0] * X(0, 0);
-  y += c0[1] * X(1, 0);
-  y += cw[1] * X(-1, 0);
-  y += c0[2] * X(0, 1);
-  y += cs[2] * X(0, -1);
-  y += c0[3] * X(1, 1);
-  y += csw[3] * X(-1, -1);
-  y += c0[4] * X(-1, 1);
-  y += cse[4] * X(1, -1);
-  return y;
-}
 
 // 36/h^2 (M x) at a node, neighbour values from X(dx, dy); same order as m_apply_unscaled.
 template <typename C, typename F>
@@ -53,14 +40,19 @@ __device__ __forceinline__ C mass_unscaled_xy(F X) {
   return C(16) * X(0, 0) + C(4) * edge + corner;
 }
 
-// B_i x at node p: the stage's B record (REC) or hm M + sigma_i K.
-template <typename C, bool REC>
-struct BlockOp {
+// Independent blocks B_i with their Jacobi scalings.
+template <typename C, int S, bool REC>
+struct BlockRelax {
+  // the two sweeps from zero of the separate kernels (jacobi2z) keep x1 in C
+  static constexpr bool kStoreFirst = false;
   const C* rec;    // REC: records of B_0 .. B_{S-1} of this V-cycle, stage-major
   size_t rstride;  // REC: distance between the stages' records
   const C* cf;     // !REC: stiffness records
   C hm;
   VecT<C> sigma;
+  const C* dinv;   // omega / diag(B_i): S values per node, node stride dstride
+  int dstride;
+
   template <typename F>
   __device__ __forceinline__ C apply(int i, int p, int nx, F X) const {
     if constexpr (REC) {
@@ -69,10 +61,110 @@ struct BlockOp {
       return hm * mass_unscaled_xy<C>(X) + sigma.v[i] * rec_apply_xy<C>(cf, p, nx, X);
     }
   }
+  // out = J(0; b)
+  __device__ __forceinline__ void zero_sweep(int p, int /*nx*/, const C (&b)[S], C (&out)[S]) const {
+#pragma unroll
+    for (int i = 0; i < S; ++i) out[i] = dinv[(size_t)p * dstride + i] * b[i];
+  }
+  // out = J(x; b), stage i of the neighbour (dx, dy) of p given by XS(i, dx, dy)
+  template <typename XS>
+  __device__ __forceinline__ void sweep(int p, int nx, XS xs, const C (&b)[S], C (&out)[S]) const {
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      auto X = [&](int dx, int dy) { return xs(i, dx, dy); };
+      out[i] = X(0, 0) + dinv[(size_t)p * dstride + i] * (b[i] - apply(i, p, nx, X));
+    }
+  }
+  // out = b - B x
+  template <typename XS>
+  __device__ __forceinline__ void residual(int p, int nx, XS xs, const C (&b)[S], C (&out)[S]) const {
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      auto X = [&](int dx, int dy) { return xs(i, dx, dy); };
+      out[i] = b[i] - apply(i, p, nx, X);
+    }
+  }
+};
+
+// Stage-coupled point-block Jacobi of the monolithic cycle (same arithmetic as mmg_smooth_kernel and
+// mmg_residual_kernel).
+template <typename C, int S, bool TRANS>
+struct MonoRelax {
+  // the separate sweeps store x1 in T
+  static constexpr bool kStoreFirst = true;
+  const C* cf;   // stiffness records
+  C hm;
+  MatT<C> mix;   // dt A (dt A^T for the transposed cycle)
+  const C* W;    // omega D_p^{-1}: entry (i, j) of node p at W[(i S + j) nx^2 + p]
+
+  // y = S_l x at p
+  template <typename XS>
+  __device__ __forceinline__ void apply_all(int p, int nx, XS xs, C (&y)[S]) const {
+    C kx[S];
+#pragma unroll
+    for (int j = 0; j < S; ++j) kx[j] = rec_apply_xy<C>(cf, p, nx, [&](int dx, int dy) { return xs(j, dx, dy); });
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      C v = hm * mass_unscaled_xy<C>([&](int dx, int dy) { return xs(i, dx, dy); });
+#pragma unroll
+      for (int j = 0; j < S; ++j) v += mix.v[i * S + j] * kx[j];
+      y[i] = v;
+    }
+  }
+  // out += W_p r (W_p^T r if TRANS)
+  __device__ __forceinline__ void block_add(int p, int nx, const C (&r)[S], C (&out)[S]) const {
+    const size_t n = (size_t)nx * nx;
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      C acc = out[i];
+#pragma unroll
+      for (int j = 0; j < S; ++j) acc += W[(size_t)(TRANS ? j * S + i : i * S + j) * n + p] * r[j];
+      out[i] = acc;
+    }
+  }
+  __device__ __forceinline__ void zero_sweep(int p, int nx, const C (&b)[S], C (&out)[S]) const {
+#pragma unroll
+    for (int i = 0; i < S; ++i) out[i] = C(0);
+    block_add(p, nx, b, out);
+  }
+  template <typename XS>
+  __device__ __forceinline__ void sweep(int p, int nx, XS xs, const C (&b)[S], C (&out)[S]) const {
+    C r[S];
+    residual(p, nx, xs, b, r);
+#pragma unroll
+    for (int i = 0; i < S; ++i) out[i] = xs(i, 0, 0);
+    block_add(p, nx, r, out);
+  }
+  template <typename XS>
+  __device__ __forceinline__ void residual(int p, int nx, XS xs, const C (&b)[S], C (&out)[S]) const {
+    C sx[S];
+    apply_all(p, nx, xs, sx);
+#pragma unroll
+    for (int i = 0; i < S; ++i) out[i] = b[i] - sx[i];
+  }
 };
 
 __device__ __forceinline__ bool interior_node(int ix, int iy, int nx) {
   return ix >= 1 && iy >= 1 && ix <= nx - 2 && iy <= nx - 2;
+}
+
+// v rounded to the storage type T (the identity when T == C).
+template <typename T, typename C>
+__device__ __forceinline__ C stored(C v) {
+  if constexpr (std::is_same<T, C>::value) {
+    return v;
+  } else {
+    T t;
+    st(&t, v);
+    return ld<C>(&t);
+  }
+}
+
+// Loads the S stages of b at node p.
+template <typename T, typename C, int S>
+__device__ __forceinline__ void load_stages(const T* __restrict__ b, int p, C (&bv)[S]) {
+#pragma unroll
+  for (int i = 0; i < S; ++i) bv[i] = ld<C>(b + (size_t)p * S + i);
 }
 
 // Down leg.  The block owns fine nodes [FX0, FX0 + 2CX) x [FY0, FY0 + 2CY), FX0 = 1 + 2 CX bx, and the
@@ -81,10 +173,9 @@ __device__ __forceinline__ bool interior_node(int ix, int iy, int nx) {
 //
 // NT threads; every phase loop has a compile-time trip count and is unrolled, so that all the
 // global loads of a phase are in flight together (the small levels are latency-bound).
-template <typename T, typename C, int S, int CX, int CY, int NT, bool REC>
-__global__ void __launch_bounds__(NT) down_leg_kernel(int nxf, BlockOp<C, REC> op, const C* __restrict__ dinv,
-                                                       int dstride, const T* __restrict__ b, T* __restrict__ xout,
-                                                       int nxc, T* __restrict__ bc) {
+template <typename T, typename C, int S, int CX, int CY, int NT, typename R>
+__global__ void __launch_bounds__(NT) down_leg_kernel(int nxf, R relax, const T* __restrict__ b,
+                                                       T* __restrict__ xout, int nxc, T* __restrict__ bc) {
   IRK_PDL_ENTRY;
   constexpr int W1 = 2 * CX + 5, H1 = 2 * CY + 5;
   constexpr int W2 = 2 * CX + 3, H2 = 2 * CY + 3;
@@ -92,21 +183,28 @@ __global__ void __launch_bounds__(NT) down_leg_kernel(int nxf, BlockOp<C, REC> o
   extern __shared__ unsigned char leg_smem[];
   C* X1 = reinterpret_cast<C*>(leg_smem);
   C* X2 = X1 + W1 * H1 * S;
-  C* R = X2 + W2 * H2 * S;
+  C* Rr = X2 + W2 * H2 * S;
   const int FX0 = 1 + 2 * CX * blockIdx.x, FY0 = 1 + 2 * CY * blockIdx.y;
 
-  // x1 = omega D^{-1} b (zero initial guess), 0 off the interior
+  // x1 = J(0; b), 0 off the interior
 #pragma unroll
   for (int t = threadIdx.x; t < W1 * H1; t += NT) {
     const int ix = FX0 - 2 + t % W1, iy = FY0 - 2 + t / W1;
-    const bool in = interior_node(ix, iy, nxf);
     const int p = ix + nxf * iy;
+    C out[S];
+    if (interior_node(ix, iy, nxf)) {
+      C bv[S];
+      load_stages<T, C, S>(b, p, bv);
+      relax.zero_sweep(p, nxf, bv, out);
+    } else {
 #pragma unroll
-    for (int i = 0; i < S; ++i)
-      X1[t * S + i] = in ? dinv[(size_t)p * dstride + i] * ld<C>(b + (size_t)p * S + i) : C(0);
+      for (int i = 0; i < S; ++i) out[i] = C(0);
+    }
+#pragma unroll
+    for (int i = 0; i < S; ++i) X1[t * S + i] = R::kStoreFirst ? stored<T>(out[i]) : out[i];
   }
   __syncthreads();
-  // x2 = x1 + omega D^{-1} (b - B x1); the owned part is the leg's smoothed iterate
+  // x2 = J(x1; b); the owned part is the leg's smoothed iterate
 #pragma unroll
   for (int t = threadIdx.x; t < W2 * H2; t += NT) {
     const int lx = t % W2, ly = t / W2;
@@ -114,16 +212,20 @@ __global__ void __launch_bounds__(NT) down_leg_kernel(int nxf, BlockOp<C, REC> o
     const bool in = interior_node(ix, iy, nxf);
     const bool own = in && ix >= FX0 && ix < FX0 + 2 * CX && iy >= FY0 && iy < FY0 + 2 * CY;
     const int p = ix + nxf * iy;
+    C out[S];
+    if (in) {
+      C bv[S];
+      load_stages<T, C, S>(b, p, bv);
+      auto xs = [&](int i, int dx, int dy) { return X1[((ly + 1 + dy) * W1 + (lx + 1 + dx)) * S + i]; };
+      relax.sweep(p, nxf, xs, bv, out);
+    } else {
+#pragma unroll
+      for (int i = 0; i < S; ++i) out[i] = C(0);
+    }
 #pragma unroll
     for (int i = 0; i < S; ++i) {
-      C v = C(0);
-      if (in) {
-        auto X = [&](int dx, int dy) { return X1[((ly + 1 + dy) * W1 + (lx + 1 + dx)) * S + i]; };
-        const C bx = op.apply(i, p, nxf, X);
-        v = X(0, 0) + dinv[(size_t)p * dstride + i] * (ld<C>(b + (size_t)p * S + i) - bx);
-      }
-      X2[t * S + i] = v;
-      if (own) st(xout + (size_t)p * S + i, v);
+      X2[t * S + i] = stored<T>(out[i]);
+      if (own) st(xout + (size_t)p * S + i, out[i]);
     }
   }
   __syncthreads();
@@ -132,17 +234,19 @@ __global__ void __launch_bounds__(NT) down_leg_kernel(int nxf, BlockOp<C, REC> o
   for (int t = threadIdx.x; t < W3 * H3; t += NT) {
     const int lx = t % W3, ly = t / W3;
     const int ix = FX0 + lx, iy = FY0 + ly;
-    const bool in = interior_node(ix, iy, nxf);
     const int p = ix + nxf * iy;
+    C out[S];
+    if (interior_node(ix, iy, nxf)) {
+      C bv[S];
+      load_stages<T, C, S>(b, p, bv);
+      auto xs = [&](int i, int dx, int dy) { return X2[((ly + 1 + dy) * W2 + (lx + 1 + dx)) * S + i]; };
+      relax.residual(p, nxf, xs, bv, out);
+    } else {
 #pragma unroll
-    for (int i = 0; i < S; ++i) {
-      C v = C(0);
-      if (in) {
-        auto X = [&](int dx, int dy) { return X2[((ly + 1 + dy) * W2 + (lx + 1 + dx)) * S + i]; };
-        v = ld<C>(b + (size_t)p * S + i) - op.apply(i, p, nxf, X);
-      }
-      R[t * S + i] = v;
+      for (int i = 0; i < S; ++i) out[i] = C(0);
     }
+#pragma unroll
+    for (int i = 0; i < S; ++i) Rr[t * S + i] = stored<T>(out[i]);
   }
   __syncthreads();
   // b_c = P^T r (full weighting), same order as restrict_kernel
@@ -153,7 +257,7 @@ __global__ void __launch_bounds__(NT) down_leg_kernel(int nxf, BlockOp<C, REC> o
     const int lx = 2 * I - FX0, ly = 2 * J - FY0;  // in [1, 2CX - 1]
 #pragma unroll
     for (int i = 0; i < S; ++i) {
-      auto Rv = [&](int dx, int dy) { return R[((ly + dy) * W3 + (lx + dx)) * S + i]; };
+      auto Rv = [&](int dx, int dy) { return Rr[((ly + dy) * W3 + (lx + dx)) * S + i]; };
       C v = Rv(0, 0) + C(0.5) * (Rv(-1, 0) + Rv(1, 0) + Rv(0, -1) + Rv(0, 1)) +
             C(0.25) * (Rv(-1, -1) + Rv(1, -1) + Rv(-1, 1) + Rv(1, 1));
       st(bc + (size_t)(I + nxc * J) * S + i, v);
@@ -164,10 +268,10 @@ __global__ void __launch_bounds__(NT) down_leg_kernel(int nxf, BlockOp<C, REC> o
 // Up leg.  The block owns fine nodes [FX0, FX0 + TX) x [FY0, FY0 + TY), FX0 = 1 + TX bx.  Regions:
 //   y0 = x + P e_c on [FX0 - 2, FX0 + TX + 1], y1 = J(y0) on [FX0 - 1, FX0 + TX], y2 = J(y1) owned.
 // xout must not alias xin (other blocks read xin on their halos).
-template <typename T, typename C, int S, int TX, int TY, int NT, bool REC>
-__global__ void __launch_bounds__(NT) up_leg_kernel(int nxf, BlockOp<C, REC> op, const C* __restrict__ dinv,
-                                                     int dstride, const T* __restrict__ xin, const T* __restrict__ b,
-                                                     int nxc, const T* __restrict__ ec, T* __restrict__ xout) {
+template <typename T, typename C, int S, int TX, int TY, int NT, typename R>
+__global__ void __launch_bounds__(NT) up_leg_kernel(int nxf, R relax, const T* __restrict__ xin,
+                                                     const T* __restrict__ b, int nxc, const T* __restrict__ ec,
+                                                     T* __restrict__ xout) {
   IRK_PDL_ENTRY;
   constexpr int W0 = TX + 4, H0 = TY + 4;
   constexpr int W1 = TX + 2, H1 = TY + 2;
@@ -191,41 +295,43 @@ __global__ void __launch_bounds__(NT) up_leg_kernel(int nxf, BlockOp<C, REC> op,
         const C pe = C(0.25) * ((E(I0, J0) + E(I1, J0)) + (E(I0, J1) + E(I1, J1)));
         v = ld<C>(xin + (size_t)p * S + i) + pe;
       }
-      Y0[t * S + i] = v;
+      Y0[t * S + i] = stored<T>(v);
     }
   }
   __syncthreads();
-  // y1 = y0 + omega D^{-1} (b - B y0)
+  // y1 = J(y0; b)
 #pragma unroll
   for (int t = threadIdx.x; t < W1 * H1; t += NT) {
     const int lx = t % W1, ly = t / W1;
     const int ix = FX0 - 1 + lx, iy = FY0 - 1 + ly;
-    const bool in = interior_node(ix, iy, nxf);
     const int p = ix + nxf * iy;
+    C out[S];
+    if (interior_node(ix, iy, nxf)) {
+      C bv[S];
+      load_stages<T, C, S>(b, p, bv);
+      auto xs = [&](int i, int dx, int dy) { return Y0[((ly + 1 + dy) * W0 + (lx + 1 + dx)) * S + i]; };
+      relax.sweep(p, nxf, xs, bv, out);
+    } else {
 #pragma unroll
-    for (int i = 0; i < S; ++i) {
-      C v = C(0);
-      if (in) {
-        auto X = [&](int dx, int dy) { return Y0[((ly + 1 + dy) * W0 + (lx + 1 + dx)) * S + i]; };
-        v = X(0, 0) + dinv[(size_t)p * dstride + i] * (ld<C>(b + (size_t)p * S + i) - op.apply(i, p, nxf, X));
-      }
-      Y1[t * S + i] = v;
+      for (int i = 0; i < S; ++i) out[i] = C(0);
     }
+#pragma unroll
+    for (int i = 0; i < S; ++i) Y1[t * S + i] = stored<T>(out[i]);
   }
   __syncthreads();
-  // y2 = y1 + omega D^{-1} (b - B y1) on the owned nodes
+  // y2 = J(y1; b) on the owned nodes
 #pragma unroll
   for (int t = threadIdx.x; t < TX * TY; t += NT) {
     const int lx = t % TX, ly = t / TX;
     const int ix = FX0 + lx, iy = FY0 + ly;
     if (!interior_node(ix, iy, nxf)) continue;
     const int p = ix + nxf * iy;
+    C bv[S], out[S];
+    load_stages<T, C, S>(b, p, bv);
+    auto xs = [&](int i, int dx, int dy) { return Y1[((ly + 1 + dy) * W1 + (lx + 1 + dx)) * S + i]; };
+    relax.sweep(p, nxf, xs, bv, out);
 #pragma unroll
-    for (int i = 0; i < S; ++i) {
-      auto X = [&](int dx, int dy) { return Y1[((ly + 1 + dy) * W1 + (lx + 1 + dx)) * S + i]; };
-      const C v = X(0, 0) + dinv[(size_t)p * dstride + i] * (ld<C>(b + (size_t)p * S + i) - op.apply(i, p, nxf, X));
-      st(xout + (size_t)p * S + i, v);
-    }
+    for (int i = 0; i < S; ++i) st(xout + (size_t)p * S + i, out[i]);
   }
 }
 
@@ -238,29 +344,27 @@ inline void leg_smem_attr(K kernel, size_t smem) {
   if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-template <typename T, typename C, int S, int CX, int CY, int NT, bool REC>
-void launch_down_leg(cudaStream_t st, int nxf, const BlockOp<C, REC>& op, const C* dinv, int dstride, const T* b,
-                     T* xout, int nxc, T* bc) {
+template <typename T, typename C, int S, int CX, int CY, int NT, typename R>
+void launch_down_leg(cudaStream_t st, int nxf, const R& relax, const T* b, T* xout, int nxc, T* bc) {
   constexpr int W1 = 2 * CX + 5, H1 = 2 * CY + 5, W2 = 2 * CX + 3, H2 = 2 * CY + 3, W3 = 2 * CX + 1, H3 = 2 * CY + 1;
   const size_t smem = sizeof(C) * S * (size_t)(W1 * H1 + W2 * H2 + W3 * H3);
-  auto kern = down_leg_kernel<T, C, S, CX, CY, NT, REC>;
+  auto kern = down_leg_kernel<T, C, S, CX, CY, NT, R>;
   leg_smem_attr(kern, smem);
   const int m = nxf - 2;
   dim3 g((m + 2 * CX - 1) / (2 * CX), (m + 2 * CY - 1) / (2 * CY));
-  launch_pdl(CX < 16 ? pdl_mode() >= 1 : pdl_mode() == 2, kern, g, dim3(NT), smem, st, nxf, op, dinv, dstride, b,
-             xout, nxc, bc);
+  launch_pdl(CX < 16 ? pdl_mode() >= 1 : pdl_mode() == 2, kern, g, dim3(NT), smem, st, nxf, relax, b, xout, nxc, bc);
 }
 
-template <typename T, typename C, int S, int TX, int TY, int NT, bool REC>
-void launch_up_leg(cudaStream_t st, int nxf, const BlockOp<C, REC>& op, const C* dinv, int dstride, const T* xin,
-                   const T* b, int nxc, const T* ec, T* xout) {
+template <typename T, typename C, int S, int TX, int TY, int NT, typename R>
+void launch_up_leg(cudaStream_t st, int nxf, const R& relax, const T* xin, const T* b, int nxc, const T* ec,
+                   T* xout) {
   const size_t smem = sizeof(C) * S * (size_t)((TX + 4) * (TY + 4) + (TX + 2) * (TY + 2));
-  auto kern = up_leg_kernel<T, C, S, TX, TY, NT, REC>;
+  auto kern = up_leg_kernel<T, C, S, TX, TY, NT, R>;
   leg_smem_attr(kern, smem);
   const int m = nxf - 2;
   dim3 g((m + TX - 1) / TX, (m + TY - 1) / TY);
-  launch_pdl(TX < 32 ? pdl_mode() >= 1 : pdl_mode() == 2, kern, g, dim3(NT), smem, st, nxf, op, dinv, dstride, xin,
-             b, nxc, ec, xout);
+  launch_pdl(TX < 32 ? pdl_mode() >= 1 : pdl_mode() == 2, kern, g, dim3(NT), smem, st, nxf, relax, xin, b, nxc, ec,
+             xout);
 }
 
 // Levels whose fine grid has at least kMgLargeNx nodes per axis use the large tiles (fewer halo
@@ -271,26 +375,24 @@ constexpr int kLegLargeNx = kMgLargeNx;
 // Levels with kLegMediumNx <= nxf < kLegLargeNx use 16 x 16 owned nodes per block.
 constexpr int kLegMediumNx = 257;
 
-template <typename T, typename C, int S, bool REC>
-void down_leg_s(cudaStream_t st, int nxf, const BlockOp<C, REC>& op, const C* dinv, int dstride, const T* b, T* xout,
-                int nxc, T* bc) {
+template <typename T, typename C, int S, typename R>
+void down_leg_s(cudaStream_t st, int nxf, const R& relax, const T* b, T* xout, int nxc, T* bc) {
   if (nxf >= kLegLargeNx)
-    launch_down_leg<T, C, S, 16, 8, 256, REC>(st, nxf, op, dinv, dstride, b, xout, nxc, bc);
+    launch_down_leg<T, C, S, 16, 8, 256>(st, nxf, relax, b, xout, nxc, bc);
   else if (nxf >= kLegMediumNx)  // regions 21 x 21, 19 x 19, 17 x 17
-    launch_down_leg<T, C, S, 8, 8, 256, REC>(st, nxf, op, dinv, dstride, b, xout, nxc, bc);
+    launch_down_leg<T, C, S, 8, 8, 256>(st, nxf, relax, b, xout, nxc, bc);
   else  // regions 13 x 13, 11 x 11, 9 x 9
-    launch_down_leg<T, C, S, 4, 4, 192, REC>(st, nxf, op, dinv, dstride, b, xout, nxc, bc);
+    launch_down_leg<T, C, S, 4, 4, 192>(st, nxf, relax, b, xout, nxc, bc);
 }
 
-template <typename T, typename C, int S, bool REC>
-void up_leg_s(cudaStream_t st, int nxf, const BlockOp<C, REC>& op, const C* dinv, int dstride, const T* xin,
-              const T* b, int nxc, const T* ec, T* xout) {
+template <typename T, typename C, int S, typename R>
+void up_leg_s(cudaStream_t st, int nxf, const R& relax, const T* xin, const T* b, int nxc, const T* ec, T* xout) {
   if (nxf >= kLegLargeNx)
-    launch_up_leg<T, C, S, 32, 16, 256, REC>(st, nxf, op, dinv, dstride, xin, b, nxc, ec, xout);
+    launch_up_leg<T, C, S, 32, 16, 256>(st, nxf, relax, xin, b, nxc, ec, xout);
   else if (nxf >= kLegMediumNx)  // regions 20 x 20, 18 x 18, 16 x 16
-    launch_up_leg<T, C, S, 16, 16, 256, REC>(st, nxf, op, dinv, dstride, xin, b, nxc, ec, xout);
+    launch_up_leg<T, C, S, 16, 16, 256>(st, nxf, relax, xin, b, nxc, ec, xout);
   else  // regions 12 x 12, 10 x 10, 8 x 8
-    launch_up_leg<T, C, S, 8, 8, 160, REC>(st, nxf, op, dinv, dstride, xin, b, nxc, ec, xout);
+    launch_up_leg<T, C, S, 8, 8, 160>(st, nxf, relax, xin, b, nxc, ec, xout);
 }
 
 #define IRK_LEG_DISPATCH(S, FN, ...)                                  \
@@ -306,11 +408,11 @@ template <typename T, typename C, int S>
 void down_leg_any(cudaStream_t st, int nxf, const C* cf, double hm, const Vec8& sigma, const C* rec, size_t rstride,
                   const C* dinv, int dstride, const T* b, T* xout, int nxc, T* bc) {
   if (rec != nullptr) {
-    BlockOp<C, true> op{rec, rstride, nullptr, C(0), {}};
-    down_leg_s<T, C, S, true>(st, nxf, op, dinv, dstride, b, xout, nxc, bc);
+    BlockRelax<C, S, true> r{rec, rstride, nullptr, C(0), {}, dinv, dstride};
+    down_leg_s<T, C, S>(st, nxf, r, b, xout, nxc, bc);
   } else {
-    BlockOp<C, false> op{nullptr, 0, cf, (C)hm, to_vec<C>(sigma)};
-    down_leg_s<T, C, S, false>(st, nxf, op, dinv, dstride, b, xout, nxc, bc);
+    BlockRelax<C, S, false> r{nullptr, 0, cf, (C)hm, to_vec<C>(sigma), dinv, dstride};
+    down_leg_s<T, C, S>(st, nxf, r, b, xout, nxc, bc);
   }
 }
 
@@ -318,11 +420,35 @@ template <typename T, typename C, int S>
 void up_leg_any(cudaStream_t st, int nxf, const C* cf, double hm, const Vec8& sigma, const C* rec, size_t rstride,
                 const C* dinv, int dstride, const T* xin, const T* b, int nxc, const T* ec, T* xout) {
   if (rec != nullptr) {
-    BlockOp<C, true> op{rec, rstride, nullptr, C(0), {}};
-    up_leg_s<T, C, S, true>(st, nxf, op, dinv, dstride, xin, b, nxc, ec, xout);
+    BlockRelax<C, S, true> r{rec, rstride, nullptr, C(0), {}, dinv, dstride};
+    up_leg_s<T, C, S>(st, nxf, r, xin, b, nxc, ec, xout);
   } else {
-    BlockOp<C, false> op{nullptr, 0, cf, (C)hm, to_vec<C>(sigma)};
-    up_leg_s<T, C, S, false>(st, nxf, op, dinv, dstride, xin, b, nxc, ec, xout);
+    BlockRelax<C, S, false> r{nullptr, 0, cf, (C)hm, to_vec<C>(sigma), dinv, dstride};
+    up_leg_s<T, C, S>(st, nxf, r, xin, b, nxc, ec, xout);
+  }
+}
+
+template <typename T, typename C, int S>
+void mmg_down_leg_any(cudaStream_t st, int nxf, const C* cf, double hm, const Mat4& mix, const C* dblk,
+                      bool transpose, const T* b, T* xout, int nxc, T* bc) {
+  if (transpose) {
+    MonoRelax<C, S, true> r{cf, (C)hm, to_mat<C>(mix), dblk};
+    down_leg_s<T, C, S>(st, nxf, r, b, xout, nxc, bc);
+  } else {
+    MonoRelax<C, S, false> r{cf, (C)hm, to_mat<C>(mix), dblk};
+    down_leg_s<T, C, S>(st, nxf, r, b, xout, nxc, bc);
+  }
+}
+
+template <typename T, typename C, int S>
+void mmg_up_leg_any(cudaStream_t st, int nxf, const C* cf, double hm, const Mat4& mix, const C* dblk, bool transpose,
+                    const T* xin, const T* b, int nxc, const T* ec, T* xout) {
+  if (transpose) {
+    MonoRelax<C, S, true> r{cf, (C)hm, to_mat<C>(mix), dblk};
+    up_leg_s<T, C, S>(st, nxf, r, xin, b, nxc, ec, xout);
+  } else {
+    MonoRelax<C, S, false> r{cf, (C)hm, to_mat<C>(mix), dblk};
+    up_leg_s<T, C, S>(st, nxf, r, xin, b, nxc, ec, xout);
   }
 }
 
@@ -337,6 +463,18 @@ void MG2<T, C>::up_leg(int S, cudaStream_t st, int nxf, const C* cf, double hm, 
                        size_t rstride, const C* dinv, int dstride, const T* xin, const T* b, int nxc, const T* ec,
                        T* xout) {
   IRK_LEG_DISPATCH(S, up_leg_any, st, nxf, cf, hm, sigma, rec, rstride, dinv, dstride, xin, b, nxc, ec, xout)
+}
+
+template <typename T, typename C>
+void MG2<T, C>::mmg_down_leg(int S, cudaStream_t st, int nxf, const C* cf, double hm, const Mat4& mix, const C* dblk,
+                             bool transpose, const T* b, T* xout, int nxc, T* bc) {
+  IRK_LEG_DISPATCH(S, mmg_down_leg_any, st, nxf, cf, hm, mix, dblk, transpose, b, xout, nxc, bc)
+}
+
+template <typename T, typename C>
+void MG2<T, C>::mmg_up_leg(int S, cudaStream_t st, int nxf, const C* cf, double hm, const Mat4& mix, const C* dblk,
+                           bool transpose, const T* xin, const T* b, int nxc, const T* ec, T* xout) {
+  IRK_LEG_DISPATCH(S, mmg_up_leg_any, st, nxf, cf, hm, mix, dblk, transpose, xin, b, nxc, ec, xout)
 }
 
 #undef IRK_LEG_DISPATCH

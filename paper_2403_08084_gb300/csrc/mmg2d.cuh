@@ -2,8 +2,8 @@
 //   S_l x = I (x) M_l x + (dt A) (x) K_l x
 // on S-interleaved level vectors (S = s, all stages at once), relaxed by additive Schwarz over
 // vertex patches with the stages coupled, which for Q1 is point-block Jacobi: at node p the s x s
-// block M_l[p, p] I + dt K_l[p, p] A, whose damped inverse omega D_p^{-1} is stored per node
-// (row-major, S^2 values).  Transfers reuse the stage-interleaved restriction and prolongation.
+// block M_l[p, p] I + dt K_l[p, p] A, whose damped inverse omega D_p^{-1} is stored planar like the
+// stencil records (entry (i, j) of node p at dblk[(i S + j) nx^2 + p]).  Transfers reuse the stage-interleaved restriction and prolongation.
 #pragma once
 
 #include "common.cuh"
@@ -38,12 +38,12 @@ __global__ void __launch_bounds__(kBX* kBY) mmg_smooth_kernel(int nx, const C* _
 #pragma unroll
     for (int i = 0; i < S; ++i) r[i] = ld<C>(b + (size_t)p * S + i);
   }
-  const C* D = dblk + (size_t)p * S * S;
+  const size_t n = (size_t)nx * nx;
 #pragma unroll
   for (int i = 0; i < S; ++i) {
     C acc = (xin != nullptr) ? ld<C>(xin + (size_t)p * S + i) : C(0);
 #pragma unroll
-    for (int j = 0; j < S; ++j) acc += (TRANS ? D[j * S + i] : D[i * S + j]) * r[j];
+    for (int j = 0; j < S; ++j) acc += dblk[(size_t)(TRANS ? j * S + i : i * S + j) * n + p] * r[j];
     st(xout + (size_t)p * S + i, acc);
   }
 }

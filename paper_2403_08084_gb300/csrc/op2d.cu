@@ -21,17 +21,7 @@ __device__ __forceinline__ double k_apply_masked(const double* __restrict__ cf, 
     const int jx = ix + dx, jy = iy + dy;
     return interior2(jx, jy, nx) ? u[jx + nx * jy] : 0.0;
   };
-  const double* c0 = cf + (size_t)p * kCoef2;
-  const double* cw = cf + (size_t)(p - 1) * kCoef2;
-  const double* cs = cf + (size_t)(p - nx) * kCoef2;
-  const double* csw = cf + (size_t)(p - nx - 1) * kCoef2;
-  const double* cse = cf + (size_t)(p - nx + 1) * kCoef2;
-  double y = c0[0] * U(0, 0);
-  y += c0[1] * U(1, 0) + cw[1] * U(-1, 0);
-  y += c0[2] * U(0, 1) + cs[2] * U(0, -1);
-  y += c0[3] * U(1, 1) + csw[3] * U(-1, -1);
-  y += c0[4] * U(-1, 1) + cse[4] * U(1, -1);
-  return y;
+  return rec_apply_xy<double>(cf, p, nx, U);
 }
 }  // namespace
 
