@@ -118,6 +118,10 @@ struct irk_handle {
   double *rhs = nullptr, *k = nullptr, *tmp = nullptr;
   void* zt = nullptr;  // FP32 / BF16 triangular sweeps: the blocks' V-cycle outputs, stage-major, precision T
   double* bnd = nullptr;  // boundary unknowns of irk_step_dirichlet (allocated on first use)
+  // FP64 triangular sweeps (2D, V(2, .) or V(., 2)): the finest level's scaled Jacobi stencils, nine planes per
+  // stage block (scaled_jacobi_records_2d), and the current block's first sweep x1 = d b
+  double* srec_d = nullptr;
+  double* x1_d = nullptr;
   DevBuf stage_bufs[8];
   int vcycles = 0;
   // one CUDA graph per FGMRES iteration index j and direction (captured on first use)
@@ -449,9 +453,16 @@ int build_operators(irk_handle* h) {
       CK(cudaMemcpyAsync(Lv.mblk_f, blkf.data(), blkf.size() * 4, cudaMemcpyHostToDevice, h->st));
       CK(cudaStreamSynchronize(h->st));
     }
-    std::vector<double> brec;
+    std::vector<double> brec, srec;
     std::vector<float> brecf;
     if (Lv.brec_d || Lv.brec_f) block_records_2d(Lv.N, Lv.cf_host, Lv.hm, sigma.data(), s, brec);
+    if (l == 0 && h->srec_d) {
+      srec.resize(9 * Lv.nn * s);
+      for (int i = 0; i < s; ++i)
+        scaled_jacobi_records_2d(Lv.N, brec.data() + (size_t)i * Lv.nn * kCoef2, dinv.data() + Lv.nn * s + (size_t)i * Lv.nn,
+                                 srec.data() + (size_t)i * 9 * Lv.nn);
+      CK(cudaMemcpyAsync(h->srec_d, srec.data(), srec.size() * 8, cudaMemcpyHostToDevice, h->st));
+    }
     if (Lv.brec_f) brecf = planar<float>(brec, Lv.nn, kCoef2);
     if (Lv.brec_d) brec = planar<double>(brec, Lv.nn, kCoef2);
     if (Lv.brec_d) CK(cudaMemcpyAsync(Lv.brec_d, brec.data(), brec.size() * 8, cudaMemcpyHostToDevice, h->st));
@@ -500,7 +511,7 @@ void destroy(irk_handle* h) {
   dfree(h->cmap), dfree(h->binv_d), dfree(h->binv_f), dfree(h->kappa_d), dfree(h->minv_d), dfree(h->minv_f);
   dfree(h->V), dfree(h->Z), dfree(h->H), dfree(h->cs), dfree(h->sn), dfree(h->g), dfree(h->y);
   dfree(h->h1), dfree(h->h2), dfree(h->partial), dfree(h->scal), dfree(h->iflag);
-  dfree(h->rhs), dfree(h->k), dfree(h->tmp), dfree(h->bnd), dfree(h->zt);
+  dfree(h->rhs), dfree(h->k), dfree(h->tmp), dfree(h->bnd), dfree(h->zt), dfree(h->srec_d), dfree(h->x1_d);
   for (DevBuf& b : h->stage_bufs) dfree(b.p);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   for (auto& gv : h->graphs)
@@ -630,6 +641,11 @@ int create(irk_handle** out, const irk_mesh* mesh, const irk_tableau* tab, doubl
   h->ne = h->lev[0].nn * s;
   h->m = opt->restart;
   const bool sweeps = opt->precond == IRK_PC_LOWER || opt->precond == IRK_PC_UPPER || opt->precond == IRK_PC_RANA_LD;
+  if (sweeps && s > 1 && dim == 2 && opt->vcycle_prec == IRK_PREC_FP64 && (opt->nu_pre == 2 || opt->nu_post == 2)) {
+    const size_t nn0 = h->lev[0].nn;
+    if ((r = dalloc(&h->srec_d, nn0 * 9 * s * 8)) || (r = dalloc(&h->x1_d, nn0 * 8))) return bail(r);
+    if (cudaMemsetAsync(h->x1_d, 0, nn0 * 8, h->st)) return bail(fail(IRK_ECUDA, "cudaMemsetAsync failed"));
+  }
   if (sweeps && s > 1 && opt->vcycle_prec != IRK_PREC_FP64) {
     if ((r = dalloc(&h->zt, h->lev[0].nn * s * vb))) return bail(r);
     // boundary entries are read by the stencils next to the boundary and must stay zero
@@ -741,9 +757,20 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2, b
   auto dinv_of = [&](const Level& Lv) {
     return S == 1 ? P::dinv(Lv) + (size_t)Lv.nn * s + (size_t)st0 * Lv.nn : P::dinv(Lv) + st0;
   };
+  // a block of the FP64 triangular sweeps whose first finest-level sweep x1 = d b is in h->x1_d: the
+  // later finest-level sweeps use the scaled stencil, x1 + sum_k c'_k x_k (jacobi_scaled)
+  constexpr bool f64 = std::is_same<T, double>::value && std::is_same<C, double>::value;
+  const bool scaled = f64 && !d3 && first_done && S == 1 && nu1 == 2 && h->srec_d != nullptr;
   auto sweep = [&](Level& Lv, const C* cf, const C* dinv, const T* xin, const T* b, T* xout) {
     const double n = interior(Lv);
     const int kj = cls(Lv, IRK_K_JACOBI);
+    if constexpr (f64) {
+      if (scaled && &Lv == &h->lev[0] && xin != nullptr) {  // x1, nine planes, x; out
+        KScope k(h, kj, n * (3 * p + 9 * c), 18.0 * n);
+        MG::jacobi_scaled(st, Lv.nx, h->srec_d + (size_t)st0 * 9 * Lv.nn, h->x1_d, xin, xout);
+        return;
+      }
+    }
     if (d3) {
       Cls4 bc{};
       Vec8 dv{};
@@ -801,8 +828,10 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2, b
       bufs[0] = other, bufs[1] = last;
     }
     int w = 0;
-    // the first sweep's result is already in bufs[0] (written together with b0)
+    // the first sweep's result is already in bufs[0] (written together with b0); with the scaled
+    // finest-level sweeps it is in h->x1_d instead, which they read on every sweep (nu1 == 2: never written)
     const bool skip_first = first_done && l == 0 && nu1 >= 1;
+    if (scaled && l == 0) bufs[0] = reinterpret_cast<T*>(h->x1_d);
     // two sweeps from zero fused into one pass: always for FP32 / BF16; for FP64 only on the
     // coarse levels (on the finest level it would add FP64 work to an FP64-pipe-bound sweep)
     const bool fuse2 = !skip_first && nu1 >= 2 && (!std::is_same<C, double>::value || l > 0);
@@ -1079,7 +1108,9 @@ int precond_apply(irk_handle* h, const double* v, double* z, bool transpose) {
   // FP64, 2D: the kernel forming a block's right-hand side also writes the first Jacobi sweep from a
   // zero guess (pointwise), into the buffer where the V-cycle's first sweep would land
   const bool fuse_first = !d3 && std::is_same<C, double>::value && nu1 >= 1;
-  T* x1buf = ((nu1 + nu2) % 2 == 1) ? (T*)L0.xa : (T*)L0.xb;
+  // (with the scaled finest-level sweeps: into h->x1_d, which the later sweeps read)
+  const bool scaled = fuse_first && nu1 == 2 && h->srec_d != nullptr;
+  T* x1buf = scaled ? reinterpret_cast<T*>(h->x1_d) : ((nu1 + nu2) % 2 == 1) ? (T*)L0.xa : (T*)L0.xb;
   // FP32 / BF16: the solved stages are read back in precision T (stage-major copies in h->zt)
   T* zt = std::is_same<T, double>::value ? nullptr : (T*)h->zt;
   const size_t zs = L0.nn;

@@ -131,6 +131,29 @@ void jacobi_inverse_diag_2d(int N, const std::vector<double>& cf, double hm, con
     }
 }
 
+void scaled_jacobi_records_2d(int N, const double* rec, const double* dinv, double* out) {
+  const int nx = N + 1;
+  const size_t nn = (size_t)nx * nx;
+  for (size_t q = 0; q < 9 * nn; ++q) out[q] = 0.0;
+  for (int iy = 1; iy < nx - 1; ++iy)
+    for (int ix = 1; ix < nx - 1; ++ix) {
+      const size_t p = (size_t)ix + (size_t)nx * iy;
+      const double d = dinv[p];
+      auto R = [&](size_t q, int k) { return rec[q * kRec + k]; };
+      // B_pk for the neighbours (dx, dy), from the symmetric records
+      const int dx[9] = {0, 1, -1, 0, 0, 1, -1, -1, 1};
+      const int dy[9] = {0, 0, 0, 1, -1, 1, -1, 1, -1};
+      const double b[9] = {R(p, kD),          R(p, 1), R(p - 1, 1),      R(p, 2),         R(p - nx, 2),
+                           R(p, 3),           R(p - nx - 1, 3),          R(p, 4),         R(p - nx + 1, 4)};
+      out[p] = 1.0 - d * b[0];
+      for (int k = 1; k < 9; ++k) {
+        const int jx = ix + dx[k], jy = iy + dy[k];
+        const bool inner = jx >= 1 && jy >= 1 && jx <= nx - 2 && jy <= nx - 2;
+        out[(size_t)k * nn + p] = inner ? -d * b[k] : 0.0;
+      }
+    }
+}
+
 void interior_nodes_2d(int N, std::vector<int>& map) {
   const int nx = N + 1;
   map.clear();

@@ -24,6 +24,14 @@ void block_records_2d(int N, const std::vector<double>& cf, double hm, const dou
 void jacobi_inverse_diag_2d(int N, const std::vector<double>& cf, double hm, const double* sigma, int S,
                             double omega, std::vector<double>& dinv);
 
+// Weighted Jacobi for one block B after its first sweep (Sec. 3.1's smoother, rewritten): with
+// d = omega / diag(B) and x1 = d b the sweep from a zero guess,
+//   x + d (b - B x) = x1 + sum_k c'_k x_k,   c'_centre = 1 - d B_pp,   c'_k = -d B_pk (k != p),
+// nine products per node instead of nine plus two.  rec: B's records {D, E, N, NE, NW} per node (node-major,
+// (N+1)^2 records); dinv: d per node; out: nine planes of (N+1)^2 values, neighbour order centre, E, W, N, S,
+// NE, SW, NW, SE; zero at boundary nodes and for couplings to boundary nodes.
+void scaled_jacobi_records_2d(int N, const double* rec, const double* dinv, double* out);
+
 // Interior node ids of an N-cell grid (x fastest) and the dense inverse of
 // M + sigma K restricted to them (row-major, nint x nint).  Returns false if the
 // matrix is singular to working precision.

@@ -30,6 +30,9 @@ struct MG2 {
   // the same with B_i = M + sigma_i K stored per stage (stage-major records, stride rstride)
   static void jacobi_rec(int S, cudaStream_t st, int nx, const C* rec, size_t rstride, const C* dinv, int dstride,
                          const T* xin, const T* b, T* xout);
+  // one block after its first sweep x1: x_out = x1 + sum_k c'_k x_k with the nine scaled planes sr
+  // (scaled_jacobi_records_2d); nine FMAs per node
+  static void jacobi_scaled(cudaStream_t st, int nx, const C* sr, const T* x1, const T* xin, T* xout);
   static void residual_rec(int S, cudaStream_t st, int nx, const C* rec, size_t rstride, const T* x, const T* b,
                            T* r);
   static void restrict_(int S, cudaStream_t st, int nxf, const T* rf, int nxc, T* bc);

@@ -84,6 +84,42 @@ def test_mmg_steps_match_oracle_and_iterations_flat_in_s():
     assert max(its.values()) - min(its.values()) <= 2, its
 
 
+@pytest.fixture(scope="module")
+def ragged_800():
+    """800^2 on 6 levels (801, 401, 201, 101, 51, 26 nodes per axis; coarsest 24^2 x 3 = 1728 coupled
+    unknowns): node counts that fill none of the fused-leg tiles exactly, and the finest level large
+    enough for the 32 x 16 tiles of the FP32 / BF16 legs."""
+    N, levels, s, dt = 800, 6, 3, 1 / 256
+    kap, d, ot, tab = setup(N, s, 90)
+    v_full = W.random_nodal(2, N, seed=91, s=s)
+    z_ref = mg.MonolithicVCycle(mg.Hierarchy(d, levels), ot.A, dt).cycle(d.to_interior(v_full, s))
+    return N, levels, s, dt, kap, d, tab, v_full, z_ref
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5), ("bf16", 3e-2)])
+def test_mmg_cycle_ragged_tiles_on_every_level(ragged_800, prec, tol):
+    N, levels, s, dt, kap, d, tab, v_full, z_ref = ragged_800
+    with Solver(N, tab, dt, kappa=kap, levels=levels, precond="monolithic", vcycle=prec) as sv:
+        z = torch.empty(sv.n_nodes * s, dtype=torch.float64, device="cuda")
+        sv.apply_preconditioner(torch.from_numpy(v_full).cuda(), z)
+        z = z.cpu().numpy()
+    assert rel(d.to_interior(z, s), z_ref) < tol
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_mmg_transposed_cycle_ragged(ragged_800, prec, tol):
+    """The transpose identity on the 800^2 hierarchy (every leg tile size, both relaxation orders)."""
+    N, levels, s, dt, kap, d, tab, v_full, _ = ragged_800
+    with Solver(N, tab, dt, kappa=kap, levels=levels, precond="monolithic", vcycle=prec) as sv:
+        u = torch.from_numpy(v_full).cuda()
+        v = torch.from_numpy(W.random_nodal(2, N, seed=92, s=s)).cuda()
+        pu, pv = torch.empty_like(u), torch.empty_like(v)
+        sv.apply_preconditioner(u, pu, transpose=True)
+        sv.apply_preconditioner(v, pv)
+        lhs, rhs = float(torch.dot(pu, v)), float(torch.dot(u, pv))
+    assert abs(lhs - rhs) <= tol * abs(rhs)
+
+
 def test_mmg_rejects_unsupported_configurations():
     tab = PT.radau_iia(2)
     with pytest.raises(IRKError):
