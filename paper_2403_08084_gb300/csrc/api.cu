@@ -122,6 +122,9 @@ struct irk_handle {
   // stage block (scaled_jacobi_records_2d), and the current block's first sweep x1 = d b
   double* srec_d = nullptr;
   double* x1_d = nullptr;
+  // IA form, 2D: per stage the planar records of A^{-1}_ii M + dt K (the stage operator's diagonal terms;
+  // A^{-T} has the same diagonal, so the transposed operator uses them too)
+  double* iarec_d = nullptr;
   DevBuf stage_bufs[8];
   int vcycles = 0;
   // one CUDA graph per FGMRES iteration index j and direction (captured on first use)
@@ -456,6 +459,19 @@ int build_operators(irk_handle* h) {
     std::vector<double> brec, srec;
     std::vector<float> brecf;
     if (Lv.brec_d || Lv.brec_f) block_records_2d(Lv.N, Lv.cf_host, Lv.hm, sigma.data(), s, brec);
+    std::vector<double> iarec;
+    if (l == 0 && h->iarec_d) {  // A^{-1}_ii M + dt K per stage; M's record is hm {16, 4, 4, 1, 1}
+      const double mrec[kCoef2] = {16.0, 4.0, 4.0, 1.0, 1.0};
+      iarec.resize(Lv.nn * kCoef2 * s);
+      for (int i = 0; i < s; ++i) {
+        const double am = h->Ainv[i * s + i] * Lv.hm;
+        for (size_t q = 0; q < Lv.nn; ++q)
+          for (int k = 0; k < kCoef2; ++k)
+            iarec[((size_t)i * Lv.nn + q) * kCoef2 + k] = am * mrec[k] + h->dt * Lv.cf_host[q * kCoef2 + k];
+      }
+      iarec = planar<double>(iarec, Lv.nn, kCoef2);
+      CK(cudaMemcpyAsync(h->iarec_d, iarec.data(), iarec.size() * 8, cudaMemcpyHostToDevice, h->st));
+    }
     if (l == 0 && h->srec_d) {
       srec.resize(9 * Lv.nn * s);
       for (int i = 0; i < s; ++i)
@@ -511,7 +527,7 @@ void destroy(irk_handle* h) {
   dfree(h->cmap), dfree(h->binv_d), dfree(h->binv_f), dfree(h->kappa_d), dfree(h->minv_d), dfree(h->minv_f);
   dfree(h->V), dfree(h->Z), dfree(h->H), dfree(h->cs), dfree(h->sn), dfree(h->g), dfree(h->y);
   dfree(h->h1), dfree(h->h2), dfree(h->partial), dfree(h->scal), dfree(h->iflag);
-  dfree(h->rhs), dfree(h->k), dfree(h->tmp), dfree(h->bnd), dfree(h->zt), dfree(h->srec_d), dfree(h->x1_d);
+  dfree(h->rhs), dfree(h->k), dfree(h->tmp), dfree(h->bnd), dfree(h->zt), dfree(h->srec_d), dfree(h->x1_d), dfree(h->iarec_d);
   for (DevBuf& b : h->stage_bufs) dfree(b.p);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   for (auto& gv : h->graphs)
@@ -641,6 +657,8 @@ int create(irk_handle** out, const irk_mesh* mesh, const irk_tableau* tab, doubl
   h->ne = h->lev[0].nn * s;
   h->m = opt->restart;
   const bool sweeps = opt->precond == IRK_PC_LOWER || opt->precond == IRK_PC_UPPER || opt->precond == IRK_PC_RANA_LD;
+  if (dim == 2 && opt->splitting == IRK_SPLIT_IA && (r = dalloc(&h->iarec_d, h->lev[0].nn * kCoef2 * s * 8)))
+    return bail(r);
   if (sweeps && s > 1 && dim == 2 && opt->vcycle_prec == IRK_PREC_FP64 && (opt->nu_pre == 2 || opt->nu_post == 2)) {
     const size_t nn0 = h->lev[0].nn;
     if ((r = dalloc(&h->srec_d, nn0 * 9 * s * 8)) || (r = dalloc(&h->x1_d, nn0 * 8))) return bail(r);
@@ -1192,12 +1210,14 @@ int apply_operator(irk_handle* h, const double* x, double* y, bool transpose) {
   if (h->opt.splitting == IRK_SPLIT_IA) {
     const double m = L0.nx - 2;
     const double ni = (h->dim == 3) ? m * m * m : m * m;
-    KScope k(h, IRK_K_STAGE_APPLY, (double)L0.nn * (16.0 * s + (h->dim == 3 ? 0.0 : 8.0 * kCoef2)),
-             ni * s * (30.0 + 2.0 * s));
+    // 2D: the per-stage records of A^{-1}_ii M + dt K, their stencils, the separable mass and the
+    // off-diagonal couplings; 3D: class stencils
+    KScope k(h, IRK_K_STAGE_APPLY, (double)L0.nn * (16.0 * s + (h->dim == 3 ? 0.0 : 8.0 * kCoef2 * s)),
+             ni * s * ((h->dim == 3 ? 30.0 : 27.0) + 2.0 * s));
     if (h->dim == 3)
       launch_stage_apply3_ia(s, h->st, L0.nx, mass_stiff_classes(L0), ia_mixing(h, transpose), h->dt, x, y);
     else
-      launch_stage_apply_ia(s, h->st, L0.nx, L0.cf_d, L0.hm, ia_mixing(h, transpose), h->dt, x, y);
+      launch_stage_apply_ia(s, h->st, L0.nx, h->iarec_d, L0.hm, ia_mixing(h, transpose), x, y);
     CK_LAUNCH();
     return IRK_OK;
   }

@@ -114,7 +114,8 @@ void launch_bc_stages3(int S, cudaStream_t st, int n, const Mat4& ainv_dt, const
 // FP64 stage-operator kernels (op2d.cu).
 void launch_stage_apply(int S, cudaStream_t st, int nx, const double* cf, double hm, const Mat4& mix, const double* x,
                         double* y);
-void launch_stage_apply_ia(int S, cudaStream_t st, int nx, const double* cf, double hm, const Mat4& mixM, double dt,
+// IA form, crec: per stage the planar records of A^{-1}_ii M + dt K (S blocks); mixM's off-diagonal couples
+void launch_stage_apply_ia(int S, cudaStream_t st, int nx, const double* crec, double hm, const Mat4& mixM,
                            const double* x, double* y);
 void launch_stage_mix(int S, cudaStream_t st, size_t nodes, const Mat4& mix, const double* in, double* out);
 void launch_stage_scale(int S, cudaStream_t st, size_t nodes, const Vec8& scale, double* z);

@@ -101,20 +101,26 @@ __global__ void __launch_bounds__(BX* BY) stage_apply_kernel(int nx, const doubl
   }
 }
 
-// IA form (Sec. 3, eq. block_struct_IA): y_i = sum_j mixM_ij M x_j + dt K x_i (mixM = A^{-1} or A^{-T},
-// passed already multiplied by the mass scale h^2 / 36).
+// IA form (Sec. 3, eq. block_struct_IA): y_i = sum_j mixM_ij M x_j + dt K x_i (mixM = A^{-1} or A^{-T}),
+// with the diagonal term folded into one stencil per stage, C_i = mixM_ii M + dt K (crec: S blocks of the
+// five planar record planes, built on the host): y_i = C_i x_i + sum_{j != i} mixM_ij M x_j.  11 FP64
+// operations per node and stage instead of 13 (the kernel is FP64-pipe-bound); M x_j from the separable
+// mass stencil over node pairs as above.  offMh = mixM h^2/36 with a zero diagonal.
 template <int S>
-__global__ void __launch_bounds__(BX* BY) stage_apply_ia_kernel(int nx, const double* __restrict__ cf, Mat4 mixMh,
-                                                                double dt, const double* __restrict__ x,
+__global__ void __launch_bounds__(BX* BY) stage_apply_ia_kernel(int nx, const double* __restrict__ crec, Mat4 offMh,
+                                                                const double* __restrict__ x,
                                                                 double* __restrict__ y) {
   IRK_PDL_ENTRY;
   const NodePair q(nx);
   if (q.ix >= nx || q.iy0 >= nx) return;
   const bool in[2] = {q.in0, q.in1};
+  const size_t rstride = (size_t)kCoef2 * nx * nx;
   double mx[2][S];
-  if (q.in0 || q.in1) {
+  if constexpr (S > 1) {
+    if (q.in0 || q.in1) {
 #pragma unroll
-    for (int j = 0; j < S; ++j) mass_pair<S>(x, q, nx, j, mx[0][j], mx[1][j]);
+      for (int j = 0; j < S; ++j) mass_pair<S>(x, q, nx, j, mx[0][j], mx[1][j]);
+    }
   }
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
@@ -127,9 +133,10 @@ __global__ void __launch_bounds__(BX* BY) stage_apply_ia_kernel(int nx, const do
     }
 #pragma unroll
     for (int i = 0; i < S; ++i) {
-      double acc = dt * k_apply<S, double>(cf, x, p, nx, i);
+      double acc = k_apply<S, double>(crec + (size_t)i * rstride, x, p, nx, i);
 #pragma unroll
-      for (int j = 0; j < S; ++j) acc += mixMh.v[i * S + j] * mx[r][j];
+      for (int j = 0; j < S; ++j)
+        if (j != i) acc += offMh.v[i * S + j] * mx[r][j];
       y[(size_t)p * S + i] = acc;
     }
   }
@@ -336,11 +343,12 @@ void launch_stage_apply(int S, cudaStream_t st, int nx, const double* cf, double
                         double* y) {
   IRK_DISPATCH_S(S, launch_k(stage_apply_kernel<SS>, pair_grid(nx), dim3(BX, BY), 0, st, nx, cf, hm, mix, x, y));
 }
-void launch_stage_apply_ia(int S, cudaStream_t st, int nx, const double* cf, double hm, const Mat4& mixM, double dt,
+void launch_stage_apply_ia(int S, cudaStream_t st, int nx, const double* crec, double hm, const Mat4& mixM,
                            const double* x, double* y) {
-  Mat4 mixMh = mixM;
-  for (int e = 0; e < S * S; ++e) mixMh.v[e] *= hm;
-  IRK_DISPATCH_S(S, launch_k(stage_apply_ia_kernel<SS>, pair_grid(nx), dim3(BX, BY), 0, st, nx, cf, mixMh, dt, x, y));
+  Mat4 offMh = mixM;
+  for (int i = 0; i < S; ++i)
+    for (int j = 0; j < S; ++j) offMh.v[i * S + j] = (i == j) ? 0.0 : offMh.v[i * S + j] * hm;
+  IRK_DISPATCH_S(S, launch_k(stage_apply_ia_kernel<SS>, pair_grid(nx), dim3(BX, BY), 0, st, nx, crec, offMh, x, y));
 }
 void launch_stage_mix(int S, cudaStream_t st, size_t nodes, const Mat4& mix, const double* in, double* out) {
   int blocks = (int)std::min<size_t>((nodes + 255) / 256, 152 * 8);
