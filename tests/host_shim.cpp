@@ -70,4 +70,15 @@ int shim_mmg_coarse_inverse(int N, const double* cf, double hm, const double* A,
   return 1;
 }
 
+void shim_q1_classes_3d(double h, double* mass, double* stiff) { irk::q1_classes_3d(h, mass, stiff); }
+
+int shim_dense_block_inverse_3d(int N, const double* mass, const double* stiff, double sigma, double* out) {
+  std::vector<int> map;
+  irk::interior_nodes_3d(N, map);
+  std::vector<double> inv;
+  if (!irk::dense_block_inverse_3d(N, mass, stiff, sigma, map, inv)) return 0;
+  copy_out(inv, out);
+  return 1;
+}
+
 }  // extern "C"

@@ -5,7 +5,8 @@ and called with ctypes; no GPU is involved.  Each test converts what the library
 and compares them with the oracle's element-by-element assembly and Galerkin products (Sec. 3.1's
 multigrid ingredients): the stiffness stencil records, their Galerkin coarsening, the records of the
 diagonal blocks M + sigma K, the Jacobi diagonals, the scaled Jacobi stencil of the finest-level
-sweeps, the dense coarsest inverses and the monolithic point blocks and coupled coarse inverse.
+sweeps, the dense coarsest inverses, the monolithic point blocks and coupled coarse inverse, and the
+3D Q1 class values with their dense coarsest inverse.
 """
 import ctypes
 import os
@@ -199,3 +200,28 @@ def test_monolithic_point_blocks_and_coupled_coarse_inverse(lib):
     perm = np.array([i * n + q for q in range(n) for i in range(s)])  # interleaved row q s + i
     Si = S[np.ix_(perm, perm)]
     assert np.abs(inv.reshape(n * s, n * s) @ Si - np.eye(n * s)).max() < 1e-11
+
+
+def test_3d_q1_classes_and_coarsest_inverse(lib):
+    """3D (kappa = 1): the 27-point Q1 mass and stiffness values by offset class (number of nonzero offset
+    coordinates) against the oracle's assembly, and the dense inverse of M + sigma K on the interior."""
+    N, sigma = 4, 0.8
+    h = 1.0 / N
+    mass, stiff = np.empty(4), np.empty(4)
+    lib.shim_q1_classes_3d(ctypes.c_double(h), ptr(mass), ptr(stiff))
+    Mf, Kf = fem.assemble(3, N)
+    nx = N + 1
+    p = 2 + nx * (2 + nx * 2)  # the centre node: all 26 neighbours interior
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                q = p + dx + nx * (dy + nx * dz)
+                cls = abs(dx) + abs(dy) + abs(dz)
+                assert abs(Mf[p, q] - mass[cls]) <= 1e-15 * abs(mass[0])
+                assert abs(Kf[p, q] - stiff[cls]) <= 1e-14 * abs(stiff[0])
+    n = (N - 1) ** 3
+    inv = np.empty(n * n)
+    assert lib.shim_dense_block_inverse_3d(N, ptr(mass), ptr(stiff), ctypes.c_double(sigma), ptr(inv)) == 1
+    d = fem.Discretisation(3, N)
+    B = (d.M + sigma * d.K).toarray()
+    assert np.abs(inv.reshape(n, n) @ B - np.eye(n)).max() < 1e-12
