@@ -72,6 +72,9 @@ struct Level {
   float* brec_f = nullptr;    // FP32 / BF16 V-cycles: the same records in FP32
   double* mblk_d = nullptr;   // monolithic multigrid: omega (M_pp I + dt K_pp A)^{-1} per node (s x s planes)
   float* mblk_f = nullptr;
+  // FP64 V-cycles, coarse levels with the large-tile legs: the scaled Jacobi stencils of the one-block
+  // V-cycles (nine planes per stage, scaled_jacobi_records_2d)
+  double* srec_d = nullptr;
   double* dinv_d = nullptr;   // omega / diag(B_i): node-major (s per node), then stage-major (nn per stage)
   float* dinv_f = nullptr;
   void* xa = nullptr;         // V-cycle vectors (s per node, V-cycle precision)
@@ -472,6 +475,14 @@ int build_operators(irk_handle* h) {
       iarec = planar<double>(iarec, Lv.nn, kCoef2);
       CK(cudaMemcpyAsync(h->iarec_d, iarec.data(), iarec.size() * 8, cudaMemcpyHostToDevice, h->st));
     }
+    if (l >= 1 && Lv.srec_d) {  // coarse level with large-tile legs: its own scaled stencils
+      std::vector<double> sl(9 * Lv.nn * s);
+      for (int i = 0; i < s; ++i)
+        scaled_jacobi_records_2d(Lv.N, brec.data() + (size_t)i * Lv.nn * kCoef2, dinv.data() + Lv.nn * s + (size_t)i * Lv.nn,
+                                 sl.data() + (size_t)i * 9 * Lv.nn);
+      srec.swap(sl);
+      CK(cudaMemcpyAsync(Lv.srec_d, srec.data(), srec.size() * 8, cudaMemcpyHostToDevice, h->st));
+    }
     if (l == 0 && h->srec_d) {
       srec.resize(9 * Lv.nn * s);
       for (int i = 0; i < s; ++i)
@@ -521,7 +532,7 @@ void destroy(irk_handle* h) {
   if (!h) return;
   for (Level& Lv : h->lev) {
     dfree(Lv.cf_d), dfree(Lv.cf_f), dfree(Lv.brec_d), dfree(Lv.brec_f), dfree(Lv.dinv_d), dfree(Lv.dinv_f);
-    dfree(Lv.mblk_d), dfree(Lv.mblk_f);
+    dfree(Lv.mblk_d), dfree(Lv.mblk_f), dfree(Lv.srec_d);
     dfree(Lv.xa), dfree(Lv.xb), dfree(Lv.b), dfree(Lv.r);
   }
   dfree(h->cmap), dfree(h->binv_d), dfree(h->binv_f), dfree(h->kappa_d), dfree(h->minv_d), dfree(h->minv_f);
@@ -629,6 +640,9 @@ int create(irk_handle** out, const irk_mesh* mesh, const irk_tableau* tab, doubl
       if (opt->vcycle_prec != IRK_PREC_FP64 && (r = dalloc(&Lv.brec_f, Lv.nn * kCoef2 * s * 4))) return bail(r);
       if (opt->precond == IRK_PC_MONOLITHIC &&
           ((r = dalloc(&Lv.mblk_d, Lv.nn * s * s * 8)) || (r = dalloc(&Lv.mblk_f, Lv.nn * s * s * 4))))
+        return bail(r);
+      if (l >= 1 && Lv.nx >= kMgLargeNx && opt->vcycle_prec == IRK_PREC_FP64 && opt->precond != IRK_PC_MONOLITHIC &&
+          (r = dalloc(&Lv.srec_d, Lv.nn * 9 * s * 8)))
         return bail(r);
       if ((r = dalloc(&Lv.cf_d, Lv.nn * kCoef2 * 8)) || (r = dalloc(&Lv.cf_f, Lv.nn * kCoef2 * 4)) ||
           (r = dalloc(&Lv.dinv_d, Lv.nn * s * 2 * 8)) || (r = dalloc(&Lv.dinv_f, Lv.nn * s * 2 * 4)))
@@ -820,6 +834,11 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2, b
     const C* rec = P::rec(Lv);
     return rec ? rec + (size_t)st0 * Lv.nn * kCoef2 : nullptr;
   };
+  // FP64 one-block V-cycles: the large-tile legs sweep with the level's scaled stencil
+  auto srec_of = [&](const Level& Lv) -> const C* {
+    if (!f64 || S != 1 || Lv.srec_d == nullptr) return nullptr;
+    return reinterpret_cast<const C*>(Lv.srec_d + (size_t)st0 * 9 * Lv.nn);
+  };
   for (int l = 0; l < L - 1; ++l) {
     Level& Lv = h->lev[l];
     Level& Lc = h->lev[l + 1];
@@ -831,7 +850,7 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2, b
       KScope k(h, cls(Lv, IRK_K_JACOBI), n * S * (2 * p + c) + n * kCoef2 * c * (rec ? S : 1) + nc * S * p,
                n * S * (rec ? 42.0 : 66.0));
       MG::down_leg(S, st, Lv.nx, cf, Lv.hm, sig, rec_of(Lv), Lv.nn * kCoef2, dinv, s_d, bl, (T*)Lv.xa, Lc.nx,
-                   (T*)Lc.b);
+                   (T*)Lc.b, srec_of(Lv));
       cur[l] = (T*)Lv.xa;
       bl = (const T*)Lc.b;
       continue;
@@ -925,7 +944,7 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2, b
       KScope k(h, cls(Lv, IRK_K_JACOBI), nf * S * (4 * p + c) + nf * kCoef2 * c * (rec ? S : 1) + nc * S * p,
                nf * S * (rec ? 45.0 : 69.0));
       MG::up_leg(S, st, Lv.nx, cf, Lv.hm, sig, rec_of(Lv), Lv.nn * kCoef2, dinv, s_d, cur[l], bfine, Lc.nx,
-                 cur[l + 1], xo);
+                 cur[l + 1], xo, srec_of(Lv));
       cur[l] = xo;
       continue;
     }

@@ -56,11 +56,13 @@ struct MG2 {
   static void coarse_solve(int S, cudaStream_t st, int nxc, const C* binv, const T* b, T* x);
   // fused V(2, 2) legs of a coarse level (mg2d_legs.cuh): x = J(J(0; b)), b_c = P^T (b - B x); and
   // xout = J(J(xin + P e_c; b)) (xout != xin).  rec != nullptr: B_i records, else hm M + sigma K.
+  // srec != nullptr (S = 1, with rec): the sweeps use the block's scaled stencil (scaled_jacobi_records_2d)
   static void down_leg(int S, cudaStream_t st, int nxf, const C* cf, double hm, const Vec8& sigma, const C* rec,
-                       size_t rstride, const C* dinv, int dstride, const T* b, T* xout, int nxc, T* bc);
+                       size_t rstride, const C* dinv, int dstride, const T* b, T* xout, int nxc, T* bc,
+                       const C* srec = nullptr);
   static void up_leg(int S, cudaStream_t st, int nxf, const C* cf, double hm, const Vec8& sigma, const C* rec,
                      size_t rstride, const C* dinv, int dstride, const T* xin, const T* b, int nxc, const T* ec,
-                     T* xout);
+                     T* xout, const C* srec = nullptr);
   // monolithic multigrid (mmg2d.cuh) on S-interleaved level vectors, mix = dt A (or dt A^T):
   // x_out = x_in + omega D^{-1} (b - S_l x_in) with the per-node s x s inverses dblk (x_in == nullptr:
   // zero guess); r = b - S_l x; exact coarsest solve with the dense inverse of the coupled system.
