@@ -134,9 +134,9 @@ void irk_default_options(irk_options* opt);
  * coarsest blocks, uploads everything and allocates the Krylov basis.
  * Device memory, with n = (N+1)^dim nodes and s stages: the Krylov basis, (2 restart + 1) vectors of 8 s n
  * bytes; four level vectors per level in the V-cycle precision; in 2D per level the stencil records (5 planes,
- * FP64 and FP32) and the records of each diagonal block; FP64 triangular sweeps add nine planes of 8 n bytes
- * per stage on the finest level and on coarse levels of at least 513 nodes per axis; the IA form adds five
- * planes per stage on the finest level; monolithic multigrid adds s^2 values per node and level.
+ * FP64 and FP32) and the records of each diagonal block; FP64 V-cycles add nine planes of 8 bytes per node and
+ * stage on coarse levels of at least 513 nodes per axis, and with triangular sweeps on the finest level; the IA
+ * form adds five planes per stage on the finest level; monolithic multigrid adds s^2 values per node and level.
  * stream: a cudaStream_t (NULL = legacy default stream).  *out is set on success. */
 int irk_create(irk_handle** out, const irk_mesh* mesh, const irk_tableau* tab, double dt,
                const irk_options* opt, void* stream);
