@@ -1,5 +1,6 @@
-"""bench.py's reference arm (the oracle, timed on host cores) runs on CPU: its one JSON line carries the
-fields of the benchmark contract, with the oracle described in cpu_baseline and no host-device traffic."""
+"""Host logic of bench.py on CPU: the reference arm (the oracle, timed on host cores) prints one JSON line with
+the fields of the benchmark contract, the oracle described in cpu_baseline and no host-device traffic; the
+clock sampler reduces nvidia-smi rows to the clocks record (median SM clock, maximum, active throttle reasons)."""
 import json
 import os
 import subprocess
@@ -27,3 +28,32 @@ def test_reference_arm_json_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_clock_sampler_parses_nvidia_smi_rows(tmp_path):
+    """The clocks record of the JSON line: median SM clock under load, the maximum, and the throttle reasons
+    seen active in any sample (nvidia-smi csv,noheader,nounits rows; 'Not Active' is not a reason)."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    c = bench.Clocks(None)
+    rows = ["0, 2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+            "0, 1980, 2070, 1390.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+            "0, 2070, 2070, 1200.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+            "garbage line"]
+    c.path = str(tmp_path / "clocks.csv")
+    with open(c.path, "w") as f:
+        f.write("\n".join(rows) + "\n")
+
+    class Done:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    c.proc = Done()
+    c.fh = open(os.devnull, "w")
+    rec = c.stop()
+    assert rec == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    assert not os.path.exists(c.path)
