@@ -1,5 +1,6 @@
 """GPU edge cases against the oracle: the smallest mesh, a zero right-hand side, extreme step sizes,
-the deepest hierarchy, ragged tiles at every fused-leg tile size, high-contrast diffusivity, and the
+the deepest hierarchy, ragged tiles at every fused-leg tile size (and a ragged 1088^2 hierarchy whose
+second level runs the large-tile legs), high-contrast diffusivity, and the
 2048^2 long-horizon workload at full size (stage equations checked with the oracle's assembled system).
 """
 import numpy as np
@@ -115,6 +116,31 @@ def test_ragged_tiles_on_every_level(splitting, prec, tol):
         sv.apply_preconditioner(torch.from_numpy(v_full).cuda(), z)
         z = z.cpu().numpy()
     assert rel(d.to_interior(z, s).reshape(-1), z_ref) < tol
+
+
+@pytest.mark.parametrize("splitting", ["ai", "ia"])
+def test_large_ragged_hierarchy_fp64(splitting):
+    """1088^2 on 6 levels (1089, 545, 273, 137, 69, 35 nodes per axis): the FP64 triangular sweep with the
+    finest level's scaled sweeps, the 545^2 level's large-tile legs with scaled-stencil sweeps, medium and
+    small legs and the coarse solve, none of the tiles filled exactly.  One application against the oracle."""
+    N, levels, s, dt = 1088, 6, 3, 1 / 256
+    kap = W.lognormal_kappa(2, N, 0.5, seed=99)
+    d = fem.Discretisation(2, N, kap)
+    ot = OT.radau_iia(s)
+    h = mg.Hierarchy(d, levels)
+    v_full = W.random_nodal(2, N, seed=100, s=s)
+    v = d.to_interior(v_full, s).reshape(-1)
+    if splitting == "ai":
+        P = krylov.BlockPreconditioner("lower", ot.A, d.K, dt, [mg.VCycle(h, dt * ot.A[i, i]) for i in range(s)])
+    else:
+        T = np.tril(ot.A)
+        P = krylov.IABlockPreconditioner(T, d.M, dt, [mg.VCycle(h, dt * T[i, i]) for i in range(s)])
+    z_ref = P(v)
+    with Solver(N, PT.radau_iia(s), dt, kappa=kap, levels=levels, precond="lower", splitting=splitting) as sv:
+        z = torch.empty(sv.n_nodes * s, dtype=torch.float64, device="cuda")
+        sv.apply_preconditioner(torch.from_numpy(v_full).cuda(), z)
+        z = z.cpu().numpy()
+    assert rel(d.to_interior(z, s).reshape(-1), z_ref) < 1e-12
 
 
 @pytest.mark.parametrize("splitting", ["ai", "ia"])
