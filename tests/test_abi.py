@@ -1,5 +1,6 @@
 """Host-side checks of the C ABI: the library loads, exports what include/irk.h
-declares, and rejects bad arguments before touching the GPU."""
+declares, and rejects bad arguments before touching the GPU; without the library the
+binding fails loudly, and the package never imports the oracle."""
 import ctypes as C
 
 import numpy as np
@@ -72,3 +73,29 @@ def _create(N=8, levels=1, A=None, s=2, dt=0.1, **opt_over):
 def test_create_rejects_bad_input(kwargs, needle):
     rc, msg = _create(**kwargs)
     assert rc == -1 and needle in msg
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """Without the built library the binding raises: there is no CPU fallback."""
+    from paper_2403_08084_gb300 import _lib
+
+    with pytest.raises(ImportError, match="no fallback"):
+        _lib.load(str(tmp_path / "libirk.so"))
+
+
+def test_product_never_imports_the_oracle():
+    """The oracle is test infrastructure: no module of the package imports it."""
+    import ast
+    import pathlib
+
+    pkg = pathlib.Path(__file__).resolve().parents[1] / "paper_2403_08084_gb300"
+    for py in pkg.glob("*.py"):
+        tree = ast.parse(py.read_text())
+        for node in ast.walk(tree):
+            if isinstance(node, ast.Import):
+                names = [a.name for a in node.names]
+            elif isinstance(node, ast.ImportFrom):
+                names = [node.module or ""]
+            else:
+                continue
+            assert not any(n == "oracle" or n.startswith("oracle.") for n in names), (py.name, names)
