@@ -4,8 +4,10 @@
  * The library advances the Q1 finite-element heat equation
  *     M u' + K(kappa) u = F(t)          (Kirby & MacLachlan, "Extending Irksome",
  *                                        Sec. 2, eq. heat / rkheat)
- * on a uniform mesh of the unit square (dim = 2) with homogeneous Dirichlet
- * data by one s-stage Runge-Kutta step at a time.  Each step solves the
+ * on a uniform mesh of the unit square (dim = 2, per-cell kappa) or the unit cube
+ * (dim = 3, 27-point Q1 stencils, kappa = 1) with homogeneous Dirichlet data (or
+ * DAE-type boundary data, irk_step_dirichlet) by one s-stage Runge-Kutta step at a
+ * time.  Each step solves the
  * stage-coupled system of Sec. 3, eq. block_struct_AI,
  *     (I (x) M + dt A (x) K) k = r,   r_i = F(t_n + c_i dt) - K u_n,
  * with FP64 flexible GMRES preconditioned by the block-diagonal (P_D, eq.
@@ -90,10 +92,11 @@ extern "C" {
 typedef struct irk_handle irk_handle;
 
 typedef struct {
-  int dim;             /* 2 */
+  int dim;             /* 2 (quadrilaterals) or 3 (hexahedra; kappa must be NULL) */
   int n_cells;         /* N: cells per axis of the uniform mesh of [0,1]^dim */
   int levels;          /* multigrid levels >= 1; N divisible by 2^(levels-1), coarsest >= 2 cells */
-  const double* kappa; /* host, N^dim per-cell diffusivities (> 0), or NULL for kappa = 1; copied */
+  const double* kappa; /* host, N^dim per-cell diffusivities (> 0), or NULL for kappa = 1 (dim = 3: NULL
+                          only); copied */
 } irk_mesh;
 
 typedef struct {
@@ -187,7 +190,8 @@ int irk_solve(irk_handle* h, const double* r, double* k, irk_stats* stats);
 int irk_apply_operator(irk_handle* h, const double* x, double* y, int transpose);
 
 /* y = M x for nodal vectors (the Q1 mass matrix; boundary entries of x read as 0,
- * of y written as 0).  Used for M-weighted objectives such as 1/2 ||u - u*||_M^2. */
+ * of y written as 0).  Used for M-weighted objectives such as 1/2 ||u - u*||_M^2.
+ * dim = 2 only (IRK_EINVAL for dim = 3). */
 int irk_apply_mass(irk_handle* h, const double* x, double* y);
 
 /* z = P^{-1} v: one application of the configured block preconditioner, each
@@ -202,15 +206,19 @@ int irk_apply_preconditioner(irk_handle* h, const double* v, double* z, int tran
  * where K_e is the unit-diffusivity element matrix, so grad accumulates dJ/d(log kappa).
  *   u_n, stages   the forward step's input state and stages (nodal / stage vectors).
  *   lam_np1       nodal adjoint state after the step (input); lam_n nodal output (may alias).
- *   grad_accum    per-cell, N^dim doubles, accumulated (+=); may be NULL. */
+ *   grad_accum    per-cell, N^dim doubles, accumulated (+=); may be NULL.
+ * dim = 2 and IRK_SPLIT_AI only (IRK_EINVAL otherwise); FGMRES or IRK_SOLVER_DIRK_CG. */
 int irk_step_adjoint(irk_handle* h, const double* u_n, const double* stages, const double* lam_np1,
                      double* lam_n, double* grad_accum, irk_stats* stats);
 
 /* z = P^{-1} v like irk_apply_preconditioner, for callers that cannot allocate
- * device memory when they apply it (for example while a stream is being captured
- * into a CUDA graph, or on threads that must not touch the allocator).  The paper
- * has no counterpart; it is an interface convenience.
+ * device memory when they apply it: host threads that must not enter the
+ * allocator (real-time loops, where a cudaMalloc or an allocator lock would
+ * break the latency budget) and embeddings in a framework that owns all device
+ * memory and gives the library a fixed budget.  The paper has no counterpart;
+ * it is an interface convenience.
  *   v, z       device pointers (host pointers are rejected: staging would allocate).
+ *   transpose  as irk_apply_preconditioner (needs IRK_SPLIT_AI, else IRK_EINVAL).
  * The V-cycle level vectors live in one static device array of 16 MiB shared by
  * every call in the process (each GPU that loads the library holds it until exit);
  * handles whose V-cycle needs more scratch than that are rejected with IRK_EINVAL.
@@ -218,8 +226,11 @@ int irk_step_adjoint(irk_handle* h, const double* u_n, const double* stages, con
  * make that first call before any stream capture.  Each call clears the part of
  * the array it uses, so results never depend on earlier calls, but calls that
  * overlap on the GPU (other streams, other threads, other handles) race on the
- * shared array and must be serialised by the caller.  Allocates no device memory:
- * calls no cudaMalloc, cudaFree or other allocating CUDA or torch routine. */
+ * shared array and must be serialised by the caller.  The triangular sweeps also
+ * write two buffers the handle allocated at irk_create (the FP64 first-sweep
+ * buffer and the FP32 / BF16 stage copies), so calls on one handle race there too.
+ * Returns after the work has finished on the handle's stream.  Allocates no device
+ * memory: calls no cudaMalloc, cudaFree or other allocating CUDA or torch routine. */
 int irk_apply_preconditioner_noalloc(irk_handle* h, const double* v, double* z, int transpose);
 
 /* Kernel classes counted by the built-in instrumentation. */

@@ -2031,15 +2031,17 @@ int irk_step_adjoint(irk_handle* h, const double* u_n, const double* stages, con
 // Preconditioner application that allocates nothing.
 //
 // Some callers cannot allocate device memory at the time they apply the
-// preconditioner: code running while a stream is being captured into a CUDA
-// graph (cudaMalloc is not allowed there), host threads that must not touch the
-// allocator (real-time loops, allocators owned by another framework), or
-// embeddings that hand the library a fixed memory budget.  For them,
-// irk_apply_preconditioner_noalloc runs the same V-cycle preconditioner as
-// irk_apply_preconditioner, but its multigrid level vectors live in one
-// file-scope device array of kNoAllocScratchBytes (16 MiB) instead of the
-// handle's buffers.  Every GPU that loads the library holds that array until
-// the process exits.
+// preconditioner: host threads that must not enter the allocator (real-time
+// loops whose latency a cudaMalloc or an allocator's lock would break), and
+// embeddings in a framework that owns all device memory and hands the library a
+// fixed budget.  For them, irk_apply_preconditioner_noalloc runs the same V-cycle
+// preconditioner as irk_apply_preconditioner, but its multigrid level vectors
+// live in one file-scope device array of kNoAllocScratchBytes (16 MiB) instead of
+// the handle's buffers.  Every GPU that loads the library holds that array until
+// the process exits.  The triangular sweeps still write two buffers the handle
+// allocated at create time (the first-sweep buffer x1_d of FP64 cycles and the
+// stage-major copies zt of FP32 / BF16 cycles), so calls on one handle must not
+// overlap either.
 // ============================================================================
 namespace {
 
@@ -2072,6 +2074,8 @@ inline size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 
 extern "C" int irk_apply_preconditioner_noalloc(irk_handle* h, const double* v, double* z, int transpose) {
   if (!h || !v || !z) return fail(IRK_EINVAL, "null argument");
+  if (transpose && h->opt.splitting != IRK_SPLIT_AI)
+    return fail(IRK_EINVAL, "the transposed preconditioner needs the AI splitting");
   if (!is_device_ptr(v) || !is_device_ptr(z))
     return fail(IRK_EINVAL, "irk_apply_preconditioner_noalloc takes device pointers only");
   // scratch layout: four level vectors (xa, xb, b, r) per level, 256-byte aligned
