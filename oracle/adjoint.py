@@ -26,7 +26,7 @@ import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
 from .fem import assemble, cell_node_ids, element_matrices, interior_index
-from .rk import kronecker_operator
+from .rk import EigenSolver, kronecker_operator
 
 
 def objective(M, u_N, u_target) -> float:
@@ -34,14 +34,33 @@ def objective(M, u_N, u_target) -> float:
     return 0.5 * float(e @ (M @ e))
 
 
-def forward(M, K, tab, dt, steps, u0, loads):
+class _KroneckerLU:
+    """S = I (x) M + dt A (x) K factored whole; solve(r, trans) gives S^{-1} r or S^{-T} r."""
+
+    def __init__(self, M, K, A, dt):
+        self.lu = spla.splu(kronecker_operator(M, K, A, dt).tocsc())
+
+    def solve(self, r, trans=False):
+        return self.lu.solve(np.asarray(r).reshape(-1), trans="T" if trans else "N")
+
+
+def direct_solver(M, K, tab, dt, direct: str):
+    """The direct stage solver: the Kronecker LU, or the eigen-decoupled solve (s complex sparse LUs of
+    M + dt lam_i K; exact up to rounding, for sizes where the Kronecker LU is too large)."""
+    if direct == "kronecker":
+        return _KroneckerLU(M, K, tab.A, dt)
+    if direct == "eigen":
+        return EigenSolver(M, K, tab.A, dt)
+    raise ValueError(direct)
+
+
+def forward(M, K, tab, dt, steps, u0, loads, solver=None):
     """loads: (steps, s, n) interior loads.  Returns (u list, k list)."""
-    S = kronecker_operator(M, K, tab.A, dt)
-    lu = spla.splu(S.tocsc())
+    lu = solver or _KroneckerLU(M, K, tab.A, dt)
     us, ks = [np.array(u0)], []
     for n in range(steps):
         r = loads[n] - (K @ us[-1])[None, :]
-        k = lu.solve(r.reshape(-1)).reshape(tab.s, -1)
+        k = np.asarray(lu.solve(r)).reshape(tab.s, -1)
         ks.append(k)
         us.append(us[-1] + dt * (tab.b @ k))
     return us, ks
@@ -59,20 +78,20 @@ def cell_gradient_term(dim, N, kappa, mu_full, U_full):
     return kappa * g
 
 
-def gradient(dim, N, kappa, tab, dt, steps, u0, loads, u_target):
-    """(J, dJ/dtheta) by the reverse sweep above, everything on interior nodes."""
+def gradient(dim, N, kappa, tab, dt, steps, u0, loads, u_target, direct="kronecker"):
+    """(J, dJ/dtheta) by the reverse sweep above, everything on interior nodes.  ``direct`` picks the
+    direct stage solver ("kronecker" or "eigen", see direct_solver); both solve S and S^T exactly."""
     M, K = assemble(dim, N, kappa)
     ii = interior_index(dim, N)
     M, K = M[ii][:, ii].tocsr(), K[ii][:, ii].tocsr()
-    us, ks = forward(M, K, tab, dt, steps, u0, loads)
+    lu = direct_solver(M, K, tab, dt, direct)
+    us, ks = forward(M, K, tab, dt, steps, u0, loads, lu)
     J = objective(M, us[-1], u_target)
-    St = kronecker_operator(M, K, tab.A.T, dt)  # = S^T since M, K are symmetric
-    lu = spla.splu(St.tocsc())
     nfull = (N + 1) ** dim
     lam = M @ (us[-1] - u_target)
     g = np.zeros(N**dim)
     for n in range(steps - 1, -1, -1):
-        mu = lu.solve(dt * np.kron(tab.b, lam)).reshape(tab.s, -1)
+        mu = np.asarray(lu.solve(dt * np.kron(tab.b, lam), trans=True)).reshape(tab.s, -1)
         U = us[n][None, :] + dt * (tab.A @ ks[n])
         mu_f = np.zeros((tab.s, nfull))
         U_f = np.zeros((tab.s, nfull))

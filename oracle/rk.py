@@ -66,12 +66,27 @@ class EigenSolver:
         lam, V = np.linalg.eig(self.A)
         self.V, self.Vinv = V.astype(complex), np.linalg.inv(V).astype(complex)
         Mc, Kc = M.astype(complex), K.astype(complex)
-        self.lus = [spla.splu((Mc + dt * lam[i] * Kc).tocsc()) for i in range(self.s)]
+        # M, K are real, so M + dt conj(lam) K is the complex conjugate of M + dt lam K: the second member
+        # of a conjugate pair is solved with the first one's factor, x = conj(B^{-1} conj(r))
+        self.lus, self.conj_of = [], []
+        for i in range(self.s):
+            j = next((j for j in range(i) if self.conj_of[j] < 0 and abs(lam[j].imag) > 0
+                      and abs(lam[i] - np.conj(lam[j])) <= 1e-12 * abs(lam[j])), -1)
+            self.conj_of.append(j)
+            self.lus.append(None if j >= 0 else spla.splu((Mc + dt * lam[i] * Kc).tocsc()))
 
-    def solve(self, r: np.ndarray) -> np.ndarray:
-        rt = self.Vinv @ np.asarray(r, dtype=complex)
-        w = np.stack([self.lus[i].solve(rt[i]) for i in range(self.s)])
-        return np.real(self.V @ w)
+    def _block_solve(self, i, r):
+        j = self.conj_of[i]
+        return np.conj(self.lus[j].solve(np.conj(r))) if j >= 0 else self.lus[i].solve(r)
+
+    def solve(self, r: np.ndarray, trans: bool = False) -> np.ndarray:
+        """k = S^{-1} r, or S^{-T} r: S^T = I (x) M + dt A^T (x) K = (V^{-T} (x) I) D (V^T (x) I) with the
+        same block-diagonal D (its blocks M + dt lam_i K are complex symmetric), so the factors are reused."""
+        r = np.asarray(r, dtype=complex).reshape(self.s, self.n)
+        left, right = (self.Vinv.T, self.V.T) if trans else (self.V, self.Vinv)
+        rt = right @ r
+        w = np.stack([self._block_solve(i, rt[i]) for i in range(self.s)])
+        return np.real(left @ w)
 
 
 def step(solver, K, b: np.ndarray, dt: float, u_n: np.ndarray, F_stages: np.ndarray):

@@ -41,3 +41,17 @@ def test_adjoint_state_is_initial_gradient():
     Jm = adjoint.gradient(dim, N, kap, tab, dt, steps, u0 - eps * du, loads, u_target)[0]
     fd = (Jp - Jm) / (2 * eps)  # exact for a quadratic up to roundoff
     assert abs(lam0 @ du - fd) < 1e-8 * abs(fd)
+
+
+@pytest.mark.parametrize("tab", [T.radau_iia(3), T.gauss_legendre(2)])
+def test_eigen_decoupled_gradient_matches_complex_step(tab):
+    """The eigen-decoupled direct solver (used at sizes the Kronecker LU cannot factor) gives the same
+    gradient, pinned by the complex step like the Kronecker path."""
+    dim, N, kap, tab, dt, steps, u0, loads, u_target = setup(N=7, steps=3, tab=tab, seed=4)
+    J, g, lam = adjoint.gradient(dim, N, kap, tab, dt, steps, u0, loads, u_target, direct="eigen")
+    J2, g2, lam2 = adjoint.gradient(dim, N, kap, tab, dt, steps, u0, loads, u_target)
+    assert abs(J - J2) <= 1e-13 * abs(J2)
+    assert np.linalg.norm(lam - lam2) <= 1e-12 * np.linalg.norm(lam2)
+    for d in W.unit_directions(N**dim, 2, seed=5):
+        cs = adjoint.complex_step_derivative(dim, N, np.log(kap), d, tab, dt, steps, u0, loads, u_target)
+        assert abs(g @ d - cs) <= 1e-11 * max(abs(cs), 1e-300) + 1e-16

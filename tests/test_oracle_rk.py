@@ -38,6 +38,19 @@ def test_eigen_solver_agrees_with_kronecker_lu():
     assert np.abs(k1 - k2).max() < 1e-11 * np.abs(k1).max()
 
 
+@pytest.mark.parametrize("tab", [T.radau_iia(3), T.gauss_legendre(4), T.radau_iia(2)])
+def test_eigen_solver_transposed_solve(tab):
+    """S^T k = r from the reused block factors: the residual against the assembled transpose."""
+    d = small_problem(N=9)
+    rng = np.random.default_rng(7)
+    r = rng.standard_normal((tab.s, d.n))
+    k = rk.EigenSolver(d.M, d.K, tab.A, 0.07).solve(r, trans=True)
+    St = rk.kronecker_operator(d.M, d.K, tab.A, 0.07).T
+    assert np.linalg.norm(St @ k.reshape(-1) - r.reshape(-1)) < 1e-12 * np.linalg.norm(r)
+    kn = rk.EigenSolver(d.M, d.K, tab.A, 0.07).solve(r)
+    assert np.linalg.norm(kn - k) > 1e-3 * np.linalg.norm(k)  # A is not symmetric: the two differ
+
+
 def test_dense_brute_force():
     """Tiny grid: the sparse LU solve equals a dense solve of the same block system."""
     d = small_problem(N=4)
