@@ -43,6 +43,7 @@ class _Trajectory(torch.autograd.Function):
         grad = torch.zeros(sv.n_cells, dtype=torch.float64, device=lam.device)
         starts = sorted(ctx.ckpt)
         ends = starts[1:] + [ctx.steps]
+        sv.adjoint_its = []  # Krylov iterations of every adjoint solve, in the order they ran
         for a, b in reversed(list(zip(starts, ends))):
             # regenerate the segment's states and stages
             us, ks = [ctx.ckpt[a].clone()], []
@@ -54,7 +55,8 @@ class _Trajectory(torch.autograd.Function):
                 us.append(u1)
                 ks.append(k)
             for n in range(b - 1, a - 1, -1):
-                sv.step_adjoint(us[n - a], ks[n - a], lam, lam, grad, allow_noconv=ctx.allow_noconv)
+                st = sv.step_adjoint(us[n - a], ks[n - a], lam, lam, grad, allow_noconv=ctx.allow_noconv)
+                sv.adjoint_its.append(st["fgmres_its"])
         return grad.to(theta.dtype), lam, None, None, None, None, None, None
 
 

@@ -25,6 +25,15 @@ def test_reference_arm_json_line():
     assert d["unit"] == "time-steps/s" and d["higher_is_better"] is True
     assert d["value"] > 0 and abs(d["ms_per_step"] - 1000.0 / d["value"]) <= 0.05 * d["ms_per_step"] + 0.01
     assert d["config"]["workload"] == "heat2d-32-radau2"
+    # the same config object the GPU arm prints for these arguments (the driver compares the two)
+    sys.path.insert(0, ROOT)
+    import argparse
+
+    import bench
+
+    wl = bench.W.WORKLOADS["heat2d-32-radau2"]
+    args = argparse.Namespace(orth="cgs", restart=50, tab_override=None)
+    assert d["config"] == bench.workload_config(wl, args, "fp64", "lower", "ia", 1)
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
