@@ -8,9 +8,9 @@ semidiscretisation with continuous Q1 elements gives M u' + K u = F with
 
     M_ab = int phi_a phi_b,     K_ab = int kappa grad phi_a . grad phi_b.
 
-Element matrices are built by tensor-product 2-point Gauss quadrature, which is
-exact for these polynomial integrands on axis-aligned cells, and assembled cell
-by cell (one scatter per local (a, b) pair, all cells at once).  ``kappa`` is
+Element matrices are the closed-form integrals (tensor products of the 1D
+linear-element mass and stiffness integrals, see element_matrices), assembled
+cell by cell (one scatter per local (a, b) pair, all cells at once).  ``kappa`` is
 piecewise constant per cell.  Nodes are numbered x fastest over the full
 (N+1)^dim grid; cells likewise over N^dim.
 """
@@ -28,26 +28,29 @@ def local_corners(dim: int) -> np.ndarray:
 
 
 def element_matrices(dim: int, h: float) -> tuple[np.ndarray, np.ndarray]:
-    """(M_e, K_e) for one cell [0, h]^dim with kappa = 1, by 2-point Gauss per axis."""
-    g = np.array([0.5 - 0.5 / np.sqrt(3.0), 0.5 + 0.5 / np.sqrt(3.0)])  # on [0, 1]
-    w = np.array([0.5, 0.5])
+    """(M_e, K_e) for one cell [0, h]^dim with kappa = 1.
+
+    Q1 shape functions are products of the 1D hats, so the element integrals are
+    tensor products of the 1D linear-element integrals
+
+        m = int phi_a phi_b = h [[1/3, 1/6], [1/6, 1/3]],   k = int phi_a' phi_b' = (1/h) [[1, -1], [-1, 1]]:
+
+    M_e[a, b] = prod_d m[a_d, b_d] and K_e[a, b] = sum_d k[a_d, b_d] prod_{e != d} m[a_e, b_e] (local
+    index a = sum_d a_d 2^d, x fastest).  Written out this way every stiffness row sums to zero in
+    floating point as it does exactly (the gradient of a constant vanishes) when h is a power of two.
+    """
+    m1 = h * np.array([[1.0 / 3.0, 1.0 / 6.0], [1.0 / 6.0, 1.0 / 3.0]])
+    k1 = (1.0 / h) * np.array([[1.0, -1.0], [-1.0, 1.0]])
     corners = local_corners(dim)
     nloc = 2**dim
     Me = np.zeros((nloc, nloc))
     Ke = np.zeros((nloc, nloc))
-    for q in itertools.product(range(2), repeat=dim):
-        xi = np.array([g[qi] for qi in q])  # reference point in [0,1]^dim
-        wq = np.prod([w[qi] for qi in q]) * h**dim
-        phi = np.empty(nloc)
-        grad = np.empty((nloc, dim))
-        for a in range(nloc):
-            f1 = np.where(corners[a] == 1, xi, 1.0 - xi)  # 1D factors
-            d1 = np.where(corners[a] == 1, 1.0, -1.0) / h  # their x-derivatives
-            phi[a] = np.prod(f1)
-            for d in range(dim):
-                grad[a, d] = d1[d] * np.prod(np.delete(f1, d))
-        Me += wq * np.outer(phi, phi)
-        Ke += wq * grad @ grad.T
+    for a in range(nloc):
+        for b in range(nloc):
+            ca, cb = corners[a], corners[b]
+            Me[a, b] = np.prod([m1[ca[d], cb[d]] for d in range(dim)])
+            Ke[a, b] = sum(k1[ca[d], cb[d]] * np.prod([m1[ca[e], cb[e]] for e in range(dim) if e != d])
+                           for d in range(dim))
     return Me, Ke
 
 

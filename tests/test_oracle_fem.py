@@ -51,6 +51,35 @@ def test_assembly_exact_integrals(dim, N):
     assert abs(K - K.T).max() < 1e-15
 
 
+def _row_sums(K):
+    """Exact sums (math.fsum) of the stored entries of every row."""
+    K = K.tocsr()
+    return np.array([math.fsum(K.data[K.indptr[i]:K.indptr[i + 1]]) for i in range(K.shape[0])])
+
+
+@pytest.mark.parametrize("dim,N", [(2, 16), (2, 64), (3, 8)])
+def test_stiffness_rows_sum_to_zero_exactly(dim, N):
+    """The gradient of a constant vanishes, so every interior row of K sums to zero.  For kappa = 1 and h a
+    power of two the stored entries must satisfy it exactly: a same-sign rounding bias in the row sums acts
+    like a small reaction term, which the stiff stage systems amplify (the stiffness stencil applied to a
+    smooth state cancels by a factor of order h^2)."""
+    _, K = fem.assemble(dim, N)
+    rs = _row_sums(K)[fem.interior_index(dim, N)]
+    assert np.all(rs == 0.0)
+
+
+def test_stiffness_row_sums_unbiased_for_variable_kappa():
+    """With per-cell lognormal kappa the entries round independently: interior row sums average to zero
+    (relative to the diagonal) far below one rounding unit, with no systematic sign."""
+    N = 128
+    kap = W.lognormal_kappa(2, N, 0.5, 3)
+    _, K = fem.assemble(2, N, kap)
+    ii = fem.interior_index(2, N)
+    rs, D = _row_sums(K)[ii], K.diagonal()[ii]
+    assert abs(rs.mean()) <= 1e-17 * D.mean()
+    assert np.abs(rs).max() <= 4e-16 * D.max()
+
+
 def test_variable_kappa_energy():
     """For u = x, u^T K(kappa) u = sum_c kappa_c |cell| (grad u = e_x on every cell)."""
     N = 6
