@@ -18,6 +18,7 @@ if not torch.cuda.is_available():  # pragma: no cover
 
 from paper_2403_08084_gb300 import Solver  # noqa: E402
 from paper_2403_08084_gb300 import tableaux as PT  # noqa: E402
+from parity import check_vcycle  # noqa: E402
 
 
 def rel(a, b):
@@ -87,12 +88,28 @@ def test_deepest_hierarchy():
     with Solver(N, PT.radau_iia(s), dt, kappa=kap, levels=levels, precond="lower") as sv:
         z = np.empty(sv.n_nodes * s)
         sv.apply_preconditioner(v_full, z)
-    assert rel(d.to_interior(z, s).reshape(-1), z_ref) < 1e-12
+    check_vcycle(d.to_interior(z, s).reshape(-1), z_ref, "fp64", "deepest-hierarchy 256^2 8 levels")
 
 
-@pytest.mark.parametrize("splitting,prec,tol", [("ai", "fp64", 1e-12), ("ia", "fp64", 1e-12), ("ia", "fp32", 2e-5),
-                                                ("ai", "bf16", 3e-2)])
-def test_ragged_tiles_on_every_level(splitting, prec, tol):
+def oracle_lower_preconditioner(ot, dt, levels, splitting, v):
+    """disc -> the oracle's P_L (AI) or IA lower block preconditioner with V-cycle blocks, applied to v."""
+    s = ot.s
+
+    def apply(d):
+        h = mg.Hierarchy(d, levels)
+        if splitting == "ai":
+            P = krylov.BlockPreconditioner("lower", ot.A, d.K, dt, [mg.VCycle(h, dt * ot.A[i, i]) for i in range(s)])
+        else:
+            T = np.tril(ot.A)
+            P = krylov.IABlockPreconditioner(T, d.M, dt, [mg.VCycle(h, dt * T[i, i]) for i in range(s)])
+        return P(v)
+
+    return apply
+
+
+@pytest.mark.parametrize("splitting,prec", [("ai", "fp64"), ("ia", "fp64"), ("ia", "fp32"), ("ai", "fp32"),
+                                            ("ai", "bf16"), ("ia", "bf16")])
+def test_ragged_tiles_on_every_level(splitting, prec):
     """800^2 on 5 levels (800, 400, 200, 100, 50 cells): node counts per axis that fill none of the
     fused-leg tiles (32 x 16, 16 x 16 and 8 x 8 owned nodes) or the 32 x 8 sweep blocks exactly (FP32 /
     BF16 cycles run the finest level as fused legs too).  One application of the triangular
@@ -101,21 +118,15 @@ def test_ragged_tiles_on_every_level(splitting, prec, tol):
     kap = W.lognormal_kappa(2, N, 0.5, seed=96)
     d = fem.Discretisation(2, N, kap)
     ot = OT.radau_iia(s)
-    h = mg.Hierarchy(d, levels)
     v_full = W.random_nodal(2, N, seed=97, s=s)
     v = d.to_interior(v_full, s).reshape(-1)
-    if splitting == "ai":
-        P = krylov.BlockPreconditioner("lower", ot.A, d.K, dt, [mg.VCycle(h, dt * ot.A[i, i]) for i in range(s)])
-    else:
-        T = np.tril(ot.A)
-        P = krylov.IABlockPreconditioner(T, d.M, dt, [mg.VCycle(h, dt * T[i, i]) for i in range(s)])
-    z_ref = P(v)
+    z_ref = oracle_lower_preconditioner(ot, dt, levels, splitting, v)(d)
     with Solver(N, PT.radau_iia(s), dt, kappa=kap, levels=levels, precond="lower", splitting=splitting,
                 vcycle=prec) as sv:
         z = torch.empty(sv.n_nodes * s, dtype=torch.float64, device="cuda")
         sv.apply_preconditioner(torch.from_numpy(v_full).cuda(), z)
         z = z.cpu().numpy()
-    assert rel(d.to_interior(z, s).reshape(-1), z_ref) < tol
+    check_vcycle(d.to_interior(z, s).reshape(-1), z_ref, prec, f"ragged-800 {splitting}")
 
 
 @pytest.mark.parametrize("splitting", ["ai", "ia"])
@@ -127,20 +138,14 @@ def test_large_ragged_hierarchy_fp64(splitting):
     kap = W.lognormal_kappa(2, N, 0.5, seed=99)
     d = fem.Discretisation(2, N, kap)
     ot = OT.radau_iia(s)
-    h = mg.Hierarchy(d, levels)
     v_full = W.random_nodal(2, N, seed=100, s=s)
     v = d.to_interior(v_full, s).reshape(-1)
-    if splitting == "ai":
-        P = krylov.BlockPreconditioner("lower", ot.A, d.K, dt, [mg.VCycle(h, dt * ot.A[i, i]) for i in range(s)])
-    else:
-        T = np.tril(ot.A)
-        P = krylov.IABlockPreconditioner(T, d.M, dt, [mg.VCycle(h, dt * T[i, i]) for i in range(s)])
-    z_ref = P(v)
+    z_ref = oracle_lower_preconditioner(ot, dt, levels, splitting, v)(d)
     with Solver(N, PT.radau_iia(s), dt, kappa=kap, levels=levels, precond="lower", splitting=splitting) as sv:
         z = torch.empty(sv.n_nodes * s, dtype=torch.float64, device="cuda")
         sv.apply_preconditioner(torch.from_numpy(v_full).cuda(), z)
         z = z.cpu().numpy()
-    assert rel(d.to_interior(z, s).reshape(-1), z_ref) < 1e-12
+    check_vcycle(d.to_interior(z, s).reshape(-1), z_ref, "fp64", f"ragged-1088 {splitting}")
 
 
 @pytest.mark.parametrize("splitting", ["ai", "ia"])

@@ -15,6 +15,7 @@ if not torch.cuda.is_available():  # pragma: no cover
 
 from paper_2403_08084_gb300 import IRKError, Solver  # noqa: E402
 from paper_2403_08084_gb300 import tableaux as PT  # noqa: E402
+from parity import check_vcycle  # noqa: E402
 
 
 def rel(a, b):
@@ -78,8 +79,8 @@ def test_dirk_adjoint_matches_oracle():
     assert rel(g, g_ref) < 1e-9 and rel(d.to_interior(lam), lam_ref) < 1e-9
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
-def test_rana_ld_preconditioner(prec, tol):
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+def test_rana_ld_preconditioner(prec):
     N, levels, s, dt = 64, 3, 3, 1 / 64
     kap = W.lognormal_kappa(2, N, 0.5, seed=52)
     d = fem.Discretisation(2, N, kap)
@@ -95,7 +96,7 @@ def test_rana_ld_preconditioner(prec, tol):
         with Solver(N, PT.radau_iia(s), dt, kappa=kap, levels=levels, precond="rana_ld", vcycle=prec) as sv:
             z = np.empty(sv.n_nodes * s)
             sv.apply_preconditioner(v, z, transpose=transpose)
-        assert rel(z, z_ref) < tol
+        check_vcycle(z, z_ref, prec, f"rana-ld transpose={transpose}")
 
 
 def test_rana_ld_solve_and_iterations():
@@ -142,8 +143,8 @@ def test_ia_operator(dim, N, s, transpose):
 
 @pytest.mark.parametrize("dim,N,levels", [(2, 64, 3), (3, 16, 2)])
 @pytest.mark.parametrize("kind", ["diag", "lower", "rana_ld"])
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
-def test_ia_preconditioner(dim, N, levels, kind, prec, tol):
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+def test_ia_preconditioner(dim, N, levels, kind, prec):
     s, dt = 3, 1 / 64
     kap = W.lognormal_kappa(2, N, 0.5, seed=62) if dim == 2 else None
     d = fem.Discretisation(dim, N, kap)
@@ -158,7 +159,7 @@ def test_ia_preconditioner(dim, N, levels, kind, prec, tol):
                 splitting="ia") as sv:
         z = np.empty(sv.n_nodes * s)
         sv.apply_preconditioner(v, z)
-    assert rel(z, z_ref) < tol
+    check_vcycle(z, z_ref, prec, f"ia-preconditioner {dim}d {kind}")
 
 
 @pytest.mark.parametrize("kind", ["lower", "rana_ld"])
