@@ -45,7 +45,8 @@ extern "C" {
 
 #define IRK_OK 0
 #define IRK_EINVAL (-1)     /* bad argument, tableau, mesh or option */
-#define IRK_ENOMEM (-2)     /* device or host allocation failed */
+#define IRK_ENOMEM (-2)     /* device or host allocation failed (for tests, IRK_FAIL_DEVICE_ALLOC=n in the
+                               environment makes every n-th device allocation of the process fail) */
 #define IRK_ECUDA (-3)      /* a CUDA runtime call failed */
 #define IRK_ENOCONV (-4)    /* FGMRES reached maxit; outputs hold the last iterate */
 #define IRK_ENONFINITE (-5) /* NaN or Inf in the residual */

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -141,6 +142,11 @@ struct irk_handle {
   double *cg_x = nullptr, *cg_r = nullptr, *cg_z = nullptr, *cg_p = nullptr, *cg_q = nullptr, *cg_b = nullptr;
   cudaStream_t cap_stream = nullptr;
   bool use_graphs = true;
+  // small-level V-cycle tails as one cooperative launch (mg2d_tail.cuh): barrier words and error flag
+  unsigned* tail_state = nullptr;  // [0] arrivals, [1] generation, [2] error flag
+  bool tail_on = false;
+  bool tail_used = false;
+  long long tail_spin = 2000000000LL;  // barrier wait limit, SM clock cycles (about one second)
   // instrumentation
   irk_perf perf{};
   unsigned perf_mask = 0;
@@ -154,10 +160,24 @@ namespace {
 // ----------------------------------------------------------------------------
 // memory helpers
 // ----------------------------------------------------------------------------
+// Allocation-failure injection (environment IRK_FAIL_DEVICE_ALLOC=n, read once per process): every n-th
+// device allocation of the process fails with IRK_ENOMEM before cudaMalloc is called, so that the error
+// paths (and their clean-up) can be exercised without exhausting the device.
+long injected_failure_period() {
+  static const long n = [] {
+    const char* e = getenv("IRK_FAIL_DEVICE_ALLOC");
+    return e ? atol(e) : 0L;
+  }();
+  return n;
+}
+std::atomic<long> g_device_allocs{0};
+
 template <typename P>
 int dalloc(P** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) bytes = 16;
+  if (const long n = injected_failure_period(); n > 0 && ++g_device_allocs % n == 0)
+    return fail(IRK_ENOMEM, "device allocation of %zu bytes failed (injected by IRK_FAIL_DEVICE_ALLOC)", bytes);
   cudaError_t e = cudaMalloc((void**)p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -548,6 +568,7 @@ void destroy(irk_handle* h) {
     for (auto& G : gv)
       if (G.exec) cudaGraphExecDestroy(G.exec);
   dfree(h->cg_x), dfree(h->cg_r), dfree(h->cg_z), dfree(h->cg_p), dfree(h->cg_q), dfree(h->cg_b);
+  dfree(h->tail_state);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->pinned) cudaFreeHost(h->pinned);
   delete h;
@@ -719,6 +740,14 @@ int create(irk_handle** out, const irk_mesh* mesh, const irk_tableau* tab, doubl
       return bail(fail(IRK_ECUDA, "cudaMemsetAsync failed"));
   }
   if (const char* e = getenv("IRK_NO_GRAPHS")) h->use_graphs = (e[0] == '\0' || e[0] == '0');
+  // IRK_TAIL=1: run the small-level legs and the coarsest solve as one cooperative launch instead of
+  // separate ones (off by default: on GB300 inside CUDA graphs the separate launches measured faster, the
+  // kernel's six grid barriers costing more than the graph's launch latency);
+  // IRK_TAIL_SPIN_CYCLES: the tail kernel's barrier wait limit
+  if (const char* e = getenv("IRK_TAIL")) h->tail_on = (e[0] == '1');
+  if (const char* e = getenv("IRK_TAIL_SPIN_CYCLES")) h->tail_spin = atoll(e);
+  if ((r = dalloc(&h->tail_state, 4 * sizeof(unsigned))) != IRK_OK) return bail(r);
+  if (cudaMemsetAsync(h->tail_state, 0, 4 * sizeof(unsigned), h->st)) return bail(fail(IRK_ECUDA, "cudaMemsetAsync failed"));
   *out = h;
   return IRK_OK;
 }
@@ -839,7 +868,17 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2, b
     if (!f64 || S != 1 || Lv.srec_d == nullptr) return nullptr;
     return reinterpret_cast<const C*>(Lv.srec_d + (size_t)st0 * 9 * Lv.nn);
   };
-  for (int l = 0; l < L - 1; ++l) {
+  // the small-level tail (levels tl0 .. L - 1: fused legs below kMgLargeNx nodes per axis, never the
+  // finest level, and the coarsest solve) as one cooperative launch (mg2d_tail.cuh); tl0 = L: none
+  int tl0 = L;
+  if (h->tail_on && !d3 && nu1 == 2 && nu2 == 2 && L >= 3) {
+    int l0 = L - 1;
+    while (l0 - 1 >= 1 && h->lev[l0 - 1].nx < kMgLargeNx && fused_leg(l0 - 1) && rec_of(h->lev[l0 - 1]) != nullptr)
+      --l0;
+    if (l0 <= L - 2 && L - 1 - l0 <= kTailMaxLevels) tl0 = l0;
+  }
+  const int l_down_end = (tl0 < L) ? tl0 : L - 1;
+  for (int l = 0; l < l_down_end; ++l) {
     Level& Lv = h->lev[l];
     Level& Lc = h->lev[l + 1];
     const C* cf = d3 ? nullptr : P::cf(Lv);
@@ -919,7 +958,42 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2, b
     }
     bl = (const T*)Lc.b;
   }
-  {  // coarsest level: exact solve
+  if (tl0 < L) {
+    TailSpec<C> sp{};
+    sp.levels = L - 1 - tl0;
+    double bytes = 0.0, flops = 0.0;
+    for (int k = 0; k < sp.levels; ++k) {
+      Level& Lv = h->lev[tl0 + k];
+      const double n = interior(Lv), nc = interior(h->lev[tl0 + k + 1]);
+      sp.nx[k] = Lv.nx;
+      sp.rec[k] = rec_of(Lv);
+      sp.rstride[k] = Lv.nn * kCoef2;
+      sp.dinv[k] = dinv_of(Lv);
+      sp.b[k] = Lv.b;
+      sp.xa[k] = Lv.xa;
+      sp.xb[k] = Lv.xb;
+      // the down and up legs' algorithmic bytes and flops (as counted for the separate legs)
+      bytes += n * S * (2 * p + c) + n * kCoef2 * c * S + nc * S * p + n * S * (4 * p + c) + n * kCoef2 * c * S +
+               nc * S * p;
+      flops += n * S * (42.0 + 45.0);
+    }
+    Level& Lc = h->lev[L - 1];
+    const double ni = h->nint;
+    sp.nxc = Lc.nx;
+    sp.binv = P::binv(h) + (size_t)st0 * h->nint * h->nint;
+    sp.bc = Lc.b;
+    sp.xc = Lc.xa;
+    sp.bar = h->tail_state;
+    sp.err = reinterpret_cast<int*>(h->tail_state + 2);
+    sp.spin_cycles = h->tail_spin;
+    {
+      KScope k(h, IRK_K_MG_TAIL, bytes + S * ni * ni * c + 2 * S * ni * p, flops + 2.0 * S * ni * ni);
+      MG::tail_cycle(S, st, sp, s_d);  // a failed launch is reported by the caller's launch check
+    }
+    h->tail_used = true;
+    for (int l = tl0; l <= L - 2; ++l) cur[l] = (T*)h->lev[l].xb;
+    cur[L - 1] = (T*)Lc.xa;
+  } else {  // coarsest level: exact solve
     Level& Lc = h->lev[L - 1];
     T* xc = (L == 1 && x0) ? x0 : (T*)Lc.xa;
     const C* binv = P::binv(h) + (size_t)st0 * h->nint * h->nint;
@@ -931,7 +1005,7 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2, b
       MG::coarse_solve(S, st, Lc.nx, binv, bl, xc);
     cur[L - 1] = xc;
   }
-  for (int l = L - 2; l >= 0; --l) {
+  for (int l = (tl0 < L ? tl0 - 1 : L - 2); l >= 0; --l) {
     Level& Lv = h->lev[l];
     Level& Lc = h->lev[l + 1];
     const C* cf = d3 ? nullptr : P::cf(Lv);
@@ -1684,9 +1758,24 @@ int dirk_solve(irk_handle* h, const double* rhs, double* k, bool transpose, irk_
   return IRK_OK;
 }
 
+// After work that may have run the multigrid tail kernel: a grid-barrier wait that ran out there is
+// reported as IRK_ECUDA (the results of the call are invalid) and the barrier state is cleared.
+int tail_status(irk_handle* h) {
+  if (!h->tail_used) return IRK_OK;
+  int* flag = reinterpret_cast<int*>(h->pinned + 6);
+  CK(cudaMemcpyAsync(flag, h->tail_state + 2, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  if (*flag == 0) return IRK_OK;
+  CK(cudaMemsetAsync(h->tail_state, 0, 4 * sizeof(unsigned), h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return fail(IRK_ECUDA, "a grid barrier of the multigrid tail kernel timed out: the results of this call are invalid");
+}
+
 int solve(irk_handle* h, const double* rhs, double* k, bool transpose, irk_stats* stats) {
-  if (h->opt.solver == IRK_SOLVER_DIRK_CG) return dirk_solve(h, rhs, k, transpose, stats);
-  return fgmres(h, rhs, k, transpose, stats);
+  const int rc = (h->opt.solver == IRK_SOLVER_DIRK_CG) ? dirk_solve(h, rhs, k, transpose, stats)
+                                                        : fgmres(h, rhs, k, transpose, stats);
+  const int ts = tail_status(h);
+  return ts != IRK_OK ? ts : rc;
 }
 
 }  // namespace
@@ -1814,7 +1903,7 @@ int irk_apply_preconditioner(irk_handle* h, const double* v, double* z, int tran
   TRY(precond(h, (const double*)vd, (double*)zd, transpose != 0));
   if (zhost) TRY(dev_out_finish(h, z, zd, bytes));
   CK(cudaStreamSynchronize(h->st));
-  return IRK_OK;
+  return tail_status(h);
 }
 
 int irk_solve(irk_handle* h, const double* r, double* k, irk_stats* stats) {
@@ -2114,5 +2203,5 @@ extern "C" int irk_apply_preconditioner_noalloc(irk_handle* h, const double* v, 
   h->perf_mask = saved_mask;
   if (rc != IRK_OK) return rc;
   CK(cudaStreamSynchronize(h->st));
-  return IRK_OK;
+  return tail_status(h);
 }

@@ -17,6 +17,28 @@ struct Cls4 {
   double v[4][4];
 };
 
+// The small-level tail of a 2D block V(2, 2) cycle run by one cooperative launch (mg2d_tail.cuh):
+// the down legs of levels[0 .. levels-1] (finest first), the coarsest solve, the up legs.
+constexpr int kTailMaxLevels = 8;
+template <typename C>
+struct TailSpec {
+  int levels;                      // leg levels, 1 .. kTailMaxLevels
+  int nx[kTailMaxLevels];          // nodes per axis of each leg level
+  const C* rec[kTailMaxLevels];    // B-records of the cycle's first block (stage-major, stride rstride)
+  size_t rstride[kTailMaxLevels];
+  const C* dinv[kTailMaxLevels];   // omega / diag(B), dstride values per node
+  void* b[kTailMaxLevels];         // right-hand sides (b[0] is the input)
+  void* xa[kTailMaxLevels];        // down-leg iterates
+  void* xb[kTailMaxLevels];        // up-leg results (xb[0] is the output)
+  int nxc;                         // coarsest level: nodes per axis
+  const C* binv;                   // S dense inverses of the coarsest blocks
+  void* bc;                        // coarsest right-hand side and solution
+  void* xc;
+  unsigned* bar;                   // grid barrier state (two words, zero between launches)
+  int* err;                        // set to 1 when a barrier wait ran out
+  long long spin_cycles;           // barrier wait limit in SM clock cycles
+};
+
 // Multigrid kernels for one precision: storage T, arithmetic C (mg2d.cuh).
 template <typename T, typename C>
 struct MG2 {
@@ -79,6 +101,8 @@ struct MG2 {
                            bool transpose, const T* b, T* xout, int nxc, T* bc);
   static void mmg_up_leg(int S, cudaStream_t st, int nxf, const C* cf, double hm, const Mat4& mix, const C* dblk,
                          bool transpose, const T* xin, const T* b, int nxc, const T* ec, T* xout);
+  // the tail of S batched blocks (S = 1: one block) as one cooperative launch (mg2d_tail.cuh)
+  static cudaError_t tail_cycle(int S, cudaStream_t st, const TailSpec<C>& spec, int dstride);
 };
 
 // Coarse levels whose finer grid has at least this many nodes per axis run the fused V-cycle legs

@@ -501,4 +501,5 @@ void MG2<T, C>::coarse_solve(int S, cudaStream_t st, int nxc, const C* binv, con
 }  // namespace irk
 
 #include "mg2d_legs.cuh"
+#include "mg2d_tail.cuh"
 #include "mmg2d.cuh"

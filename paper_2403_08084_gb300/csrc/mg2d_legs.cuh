@@ -208,17 +208,16 @@ __device__ __forceinline__ void load_stages(const T* __restrict__ b, int p, C (&
 // NT threads; every phase loop has a compile-time trip count and is unrolled, so that all the
 // global loads of a phase are in flight together (the small levels are latency-bound).
 template <typename T, typename C, int S, int CX, int CY, int NT, typename R>
-__global__ void __launch_bounds__(NT) down_leg_kernel(int nxf, R relax, const T* __restrict__ b,
-                                                       T* __restrict__ xout, int nxc, T* __restrict__ bc) {
-  IRK_PDL_ENTRY;
+__device__ __forceinline__ void down_leg_tile(int bx, int by, int nxf, const R& relax, const T* __restrict__ b,
+                                              T* __restrict__ xout, int nxc, T* __restrict__ bc,
+                                              unsigned char* smem) {
   constexpr int W1 = 2 * CX + 5, H1 = 2 * CY + 5;
   constexpr int W2 = 2 * CX + 3, H2 = 2 * CY + 3;
   constexpr int W3 = 2 * CX + 1, H3 = 2 * CY + 1;
-  extern __shared__ unsigned char leg_smem[];
-  C* X1 = reinterpret_cast<C*>(leg_smem);
+  C* X1 = reinterpret_cast<C*>(smem);
   C* X2 = X1 + W1 * H1 * S;
   C* Rr = X2 + W2 * H2 * S;
-  const int FX0 = 1 + 2 * CX * blockIdx.x, FY0 = 1 + 2 * CY * blockIdx.y;
+  const int FX0 = 1 + 2 * CX * bx, FY0 = 1 + 2 * CY * by;
 
   // x1 = J(0; b), 0 off the interior
 #pragma unroll
@@ -286,7 +285,7 @@ __global__ void __launch_bounds__(NT) down_leg_kernel(int nxf, R relax, const T*
   // b_c = P^T r (full weighting), same order as restrict_kernel
 #pragma unroll
   for (int t = threadIdx.x; t < CX * CY; t += NT) {
-    const int I = 1 + CX * blockIdx.x + t % CX, J = 1 + CY * blockIdx.y + t / CX;
+    const int I = 1 + CX * bx + t % CX, J = 1 + CY * by + t / CX;
     if (I > nxc - 2 || J > nxc - 2) continue;
     const int lx = 2 * I - FX0, ly = 2 * J - FY0;  // in [1, 2CX - 1]
 #pragma unroll
@@ -299,20 +298,26 @@ __global__ void __launch_bounds__(NT) down_leg_kernel(int nxf, R relax, const T*
   }
 }
 
+template <typename T, typename C, int S, int CX, int CY, int NT, typename R>
+__global__ void __launch_bounds__(NT) down_leg_kernel(int nxf, R relax, const T* __restrict__ b,
+                                                       T* __restrict__ xout, int nxc, T* __restrict__ bc) {
+  IRK_PDL_ENTRY;
+  extern __shared__ unsigned char leg_smem[];
+  down_leg_tile<T, C, S, CX, CY, NT, R>(blockIdx.x, blockIdx.y, nxf, relax, b, xout, nxc, bc, leg_smem);
+}
+
 // Up leg.  The block owns fine nodes [FX0, FX0 + TX) x [FY0, FY0 + TY), FX0 = 1 + TX bx.  Regions:
 //   y0 = x + P e_c on [FX0 - 2, FX0 + TX + 1], y1 = J(y0) on [FX0 - 1, FX0 + TX], y2 = J(y1) owned.
 // xout must not alias xin (other blocks read xin on their halos).
 template <typename T, typename C, int S, int TX, int TY, int NT, typename R>
-__global__ void __launch_bounds__(NT) up_leg_kernel(int nxf, R relax, const T* __restrict__ xin,
-                                                     const T* __restrict__ b, int nxc, const T* __restrict__ ec,
-                                                     T* __restrict__ xout) {
-  IRK_PDL_ENTRY;
+__device__ __forceinline__ void up_leg_tile(int bx, int by, int nxf, const R& relax, const T* __restrict__ xin,
+                                            const T* __restrict__ b, int nxc, const T* __restrict__ ec,
+                                            T* __restrict__ xout, unsigned char* smem) {
   constexpr int W0 = TX + 4, H0 = TY + 4;
   constexpr int W1 = TX + 2, H1 = TY + 2;
-  extern __shared__ unsigned char leg_smem[];
-  C* Y0 = reinterpret_cast<C*>(leg_smem);
+  C* Y0 = reinterpret_cast<C*>(smem);
   C* Y1 = Y0 + W0 * H0 * S;
-  const int FX0 = 1 + TX * blockIdx.x, FY0 = 1 + TY * blockIdx.y;
+  const int FX0 = 1 + TX * bx, FY0 = 1 + TY * by;
 
   // y0 = x + P e_c (bilinear interpolation as in prolong_add_kernel), 0 off the interior
 #pragma unroll
@@ -367,6 +372,15 @@ __global__ void __launch_bounds__(NT) up_leg_kernel(int nxf, R relax, const T* _
 #pragma unroll
     for (int i = 0; i < S; ++i) st(xout + (size_t)p * S + i, out[i]);
   }
+}
+
+template <typename T, typename C, int S, int TX, int TY, int NT, typename R>
+__global__ void __launch_bounds__(NT) up_leg_kernel(int nxf, R relax, const T* __restrict__ xin,
+                                                     const T* __restrict__ b, int nxc, const T* __restrict__ ec,
+                                                     T* __restrict__ xout) {
+  IRK_PDL_ENTRY;
+  extern __shared__ unsigned char leg_smem[];
+  up_leg_tile<T, C, S, TX, TY, NT, R>(blockIdx.x, blockIdx.y, nxf, relax, xin, b, nxc, ec, xout, leg_smem);
 }
 
 // ----------------------------------------------------------------------------
