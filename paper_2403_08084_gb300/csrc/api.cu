@@ -785,8 +785,18 @@ struct Prec<__nv_bfloat16, float> {
 // first_done: the finest level's first sweep from a zero guess has already been written, by the
 // kernel that formed b0, to the buffer that sweep would write (level 0's xa if nu1 + nu2 is odd,
 // else xb; see precond_apply).
+// A request to put a one-block cycle's result, times scale, straight into stage i of the interleaved FP64
+// stage vector z (the triangular sweeps' scatter); done is set when the last finest-level sweep did so.
+struct ZOut {
+  double* z;
+  int i;
+  double scale;
+  bool done;
+};
+
 template <typename T, typename C>
-T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2, bool first_done = false) {
+T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2, bool first_done = false,
+          ZOut* zo = nullptr) {
   using MG = MG2<T, C>;
   using MG3T = MG3<T, C>;
   using P = Prec<T, C>;
@@ -1034,6 +1044,18 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2, b
     T* a = cur[l];
     T* bnext = (a == last) ? other : last;
     for (int k = 0; k < nu2; ++k) {
+      if constexpr (f64) {
+        // the last finest-level sweep of a scaled one-block cycle may write the caller's stage vector
+        if (zo && l == 0 && k == nu2 - 1 && scaled && x0 == nullptr) {
+          const double n = interior(Lv);
+          KScope kk(h, IRK_K_JACOBI, n * (3 * p + 9 * c), 19.0 * n);
+          if (MG::jacobi_scaled_z(s, st, Lv.nx, h->srec_d + (size_t)st0 * 9 * Lv.nn, h->x1_d, a, zo->i, zo->z,
+                                  zo->scale)) {
+            zo->done = true;
+            break;
+          }
+        }
+      }
       sweep(Lv, cf, dinv, a, bfine, bnext);
       std::swap(a, bnext);
     }
@@ -1254,9 +1276,11 @@ int precond_apply(irk_handle* h, const double* v, double* z, bool transpose) {
         MG::block_rhs(s, st, L0.nx, cf, v, z, i, cj, (T*)L0.b, fuse_first ? d1 : nullptr, x1buf, zt, zs);
       }
     }
-    T* x = vcycle<T, C>(h, 1, i, (const T*)L0.b, nullptr, nu1, nu2, fuse_first);
-    KScope k(h, IRK_K_OTHER, n * (p + 8), 0);
     const double scale = ia ? h->Tm[i * s + i] : 1.0;
+    ZOut zo{z, i, scale, false};
+    T* x = vcycle<T, C>(h, 1, i, (const T*)L0.b, nullptr, nu1, nu2, fuse_first, (!d3 && !zt) ? &zo : nullptr);
+    if (zo.done) continue;  // the last sweep wrote scale * x into stage i of z
+    KScope k(h, IRK_K_OTHER, n * (p + 8), 0);
     T* zti = zt ? zt + (size_t)i * zs : nullptr;
     if (d3)
       MG3<T, C>::scatter_stage(s, st, L0.nx, x, i, z, scale, zti);

@@ -55,6 +55,10 @@ struct MG2 {
   // one block after its first sweep x1: x_out = x1 + sum_k c'_k x_k with the nine scaled planes sr
   // (scaled_jacobi_records_2d); nine FMAs per node
   static void jacobi_scaled(cudaStream_t st, int nx, const C* sr, const T* x1, const T* xin, T* xout);
+  // the same sweep writing scale * x_out into stage i of the SF-interleaved FP64 vector z (FP64 only;
+  // false, nothing launched, otherwise)
+  static bool jacobi_scaled_z(int SF, cudaStream_t st, int nx, const C* sr, const T* x1, const T* xin, int i,
+                              double* z, double scale);
   static void residual_rec(int S, cudaStream_t st, int nx, const C* rec, size_t rstride, const T* x, const T* b,
                            T* r);
   static void restrict_(int S, cudaStream_t st, int nxf, const T* rf, int nxc, T* bc);

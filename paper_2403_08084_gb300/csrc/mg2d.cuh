@@ -100,6 +100,34 @@ __global__ void __launch_bounds__(kBX* kBY) jacobi_scaled_kernel(int nx, const C
   st(xout + p, acc);
 }
 
+// The same sweep writing scale * x_out into stage i of the SF-interleaved FP64 vector z instead of a
+// level vector: the last sweep of a block V-cycle in the triangular sweeps (what scatter_stage_kernel
+// would write from its output).
+template <typename C, int SF>
+__global__ void __launch_bounds__(kBX* kBY) jacobi_scaled_z_kernel(int nx, const C* __restrict__ sr,
+                                                                   const double* __restrict__ x1,
+                                                                   const double* __restrict__ xin, int i,
+                                                                   double* __restrict__ z, double scale) {
+  IRK_PDL_ENTRY;
+  const int ix = 1 + blockIdx.x * kBX + threadIdx.x;
+  const int iy = 1 + blockIdx.y * kBY + threadIdx.y;
+  if (ix > nx - 2 || iy > nx - 2) return;
+  const int p = ix + nx * iy;
+  const size_t n = (size_t)nx * nx;
+  auto X = [&](int q) { return xin[q]; };
+  double acc = x1[p];
+  acc = fma(sr[p], X(p), acc);
+  acc = fma(sr[n + p], X(p + 1), acc);
+  acc = fma(sr[2 * n + p], X(p - 1), acc);
+  acc = fma(sr[3 * n + p], X(p + nx), acc);
+  acc = fma(sr[4 * n + p], X(p - nx), acc);
+  acc = fma(sr[5 * n + p], X(p + nx + 1), acc);
+  acc = fma(sr[6 * n + p], X(p - nx - 1), acc);
+  acc = fma(sr[7 * n + p], X(p + nx - 1), acc);
+  acc = fma(sr[8 * n + p], X(p - nx + 1), acc);
+  z[(size_t)p * SF + i] = scale * acc;
+}
+
 template <typename T, typename C, int S>
 __global__ void __launch_bounds__(kBX* kBY) residual_rec_kernel(int nx, const C* __restrict__ rec, size_t rstride,
                                                                 const T* __restrict__ x, const T* __restrict__ b,
@@ -409,6 +437,17 @@ template <typename T, typename C>
 void MG2<T, C>::jacobi_scaled(cudaStream_t st, int nx, const C* sr, const T* x1, const T* xin, T* xout) {
   dim3 g = interior_grid(nx), blk(kBX, kBY);
   launch_k(jacobi_scaled_kernel<T, C>, g, blk, 0, st, nx, sr, x1, xin, xout);
+}
+template <typename T, typename C>
+bool MG2<T, C>::jacobi_scaled_z(int SF, cudaStream_t st, int nx, const C* sr, const T* x1, const T* xin, int i,
+                                double* z, double scale) {
+  if constexpr (std::is_same<T, double>::value && std::is_same<C, double>::value) {
+    dim3 g = interior_grid(nx), blk(kBX, kBY);
+    IRK_DISPATCH_S(SF, launch_k(jacobi_scaled_z_kernel<C, SS>, g, blk, 0, st, nx, sr, x1, xin, i, z, scale));
+    return true;
+  } else {
+    return false;
+  }
 }
 template <typename T, typename C>
 void MG2<T, C>::residual_rec(int S, cudaStream_t st, int nx, const C* rec, size_t rstride, const T* x, const T* b,
