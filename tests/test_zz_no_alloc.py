@@ -12,6 +12,7 @@ transposed IA preconditioner).  This file is collected last, so a run that stops
 at its first failure has run every other test before it.
 """
 import ctypes as C
+import gc
 
 import numpy as np
 import pytest
@@ -90,11 +91,18 @@ def test_noalloc_leaves_device_memory_unchanged():
         v = torch.from_numpy(W.random_nodal(2, 128, seed=8, s=s)).cuda()
         z = torch.empty(sv.n_nodes * s, dtype=torch.float64, device="cuda")
         assert noalloc(sv, v, z) == 0  # the first call may load the library's device code
-        free0, torch0 = free_bytes(), (torch.cuda.memory_allocated(), torch.cuda.memory_reserved())
-        for transpose in (False, True, False):
-            assert noalloc(sv, v, z, transpose) == 0, _lib.lib.irk_last_error().decode()
-        assert free_bytes() == free0
-        assert (torch.cuda.memory_allocated(), torch.cuda.memory_reserved()) == torch0
+        # tensors left by earlier tests are freed first, and no collection runs during the calls
+        gc.collect()
+        gc.disable()
+        try:
+            free0, torch0 = free_bytes(), (torch.cuda.memory_allocated(), torch.cuda.memory_reserved())
+            for transpose in (False, True, False):
+                assert noalloc(sv, v, z, transpose) == 0, _lib.lib.irk_last_error().decode()
+            free1, torch1 = free_bytes(), (torch.cuda.memory_allocated(), torch.cuda.memory_reserved())
+        finally:
+            gc.enable()
+        assert free1 == free0
+        assert torch1 == torch0
 
 
 def test_noalloc_rejects_oversize_host_pointers_and_transposed_ia():
