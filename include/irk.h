@@ -119,6 +119,10 @@ typedef struct {
   int orth;         /* IRK_ORTH_* (default IRK_ORTH_CGS2) */
   int solver;       /* IRK_SOLVER_* (default IRK_SOLVER_FGMRES) */
   int splitting;    /* IRK_SPLIT_* (default IRK_SPLIT_AI); IA needs an invertible A and FGMRES */
+  int warm_start;   /* 1: irk_step starts FGMRES from the stage solution of this handle's previous irk_step
+                       (the stopping test stays ||r_j||_2 <= rtol ||r||_2 with r the step's right-hand side,
+                       so the accuracy is that of a zero start); 0 (default): zero initial guess, as the
+                       paper's solver runs.  Ignored by IRK_SOLVER_DIRK_CG. */
 } irk_options;
 
 typedef struct {
@@ -151,6 +155,11 @@ int irk_destroy(irk_handle* h);
 /* Replace the per-cell diffusivity (host, N^dim doubles) and rebuild the
  * operators, the hierarchy and the coarse factors; the step size is kept. */
 int irk_set_kappa(irk_handle* h, const double* kappa_host);
+
+/* With irk_options.warm_start = 1: make the next irk_step start FGMRES from zero (as the first step of a
+ * handle does), e.g. before a new trajectory from other initial data.  A no-op otherwise.  Returns IRK_OK,
+ * or IRK_EINVAL for a NULL handle. */
+int irk_reset_initial_guess(irk_handle* h);
 
 /* One RK step (Sec. 2): solve for the stages k and set
  * u_np1 = u_n + dt sum_i b_i k_i.

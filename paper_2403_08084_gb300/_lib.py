@@ -44,7 +44,7 @@ class irk_tableau(C.Structure):
 class irk_options(C.Structure):
     _fields_ = [("precond", C.c_int), ("vcycle_prec", C.c_int), ("nu_pre", C.c_int), ("nu_post", C.c_int),
                 ("omega", C.c_double), ("rtol", C.c_double), ("restart", C.c_int), ("maxit", C.c_int),
-                ("orth", C.c_int), ("solver", C.c_int), ("splitting", C.c_int)]
+                ("orth", C.c_int), ("solver", C.c_int), ("splitting", C.c_int), ("warm_start", C.c_int)]
 
 
 class irk_stats(C.Structure):
@@ -82,6 +82,7 @@ _SIGNATURES = {
                              C.POINTER(irk_options), _P]),
     "irk_destroy": (C.c_int, [_P]),
     "irk_set_kappa": (C.c_int, [_P, _P]),
+    "irk_reset_initial_guess": (C.c_int, [_P]),
     "irk_step": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, C.POINTER(irk_stats)]),
     "irk_step_dirichlet": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, C.POINTER(irk_stats)]),
     "irk_solve": (C.c_int, [_P, _P, _P, C.POINTER(irk_stats)]),

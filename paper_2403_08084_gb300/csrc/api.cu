@@ -146,6 +146,7 @@ struct irk_handle {
   unsigned* tail_state = nullptr;  // [0] arrivals, [1] generation, [2] error flag
   bool tail_on = false;
   bool tail_used = false;
+  bool k_from_step = false;  // h->k holds the stage solution of the last forward irk_step (warm start)
   long long tail_spin = 2000000000LL;  // barrier wait limit, SM clock cycles (about one second)
   // instrumentation
   irk_perf perf{};
@@ -399,6 +400,7 @@ int validate(const irk_mesh* mesh, const irk_tableau* tab, double dt, const irk_
     return fail(IRK_EINVAL, "bad solver %d", opt->solver);
   if (opt->splitting != IRK_SPLIT_AI && opt->splitting != IRK_SPLIT_IA)
     return fail(IRK_EINVAL, "bad splitting %d", opt->splitting);
+  if (opt->warm_start != 0 && opt->warm_start != 1) return fail(IRK_EINVAL, "bad warm_start %d", opt->warm_start);
   if (opt->splitting == IRK_SPLIT_IA && opt->solver != IRK_SOLVER_FGMRES)
     return fail(IRK_EINVAL, "the IA splitting is implemented for the FGMRES solver");
   if (opt->solver == IRK_SOLVER_DIRK_CG) {
@@ -1545,13 +1547,14 @@ int run_arnoldi_step(irk_handle* h, int j, bool transpose) {
   return run_graph(h, h->graphs[transpose ? 1 : 0][j], [h, j, transpose] { return arnoldi_step(h, j, transpose); });
 }
 
-int fgmres(irk_handle* h, const double* rhs, double* x, bool transpose, irk_stats* stats) {
+// from_x: start from the contents of x instead of zero; the stopping test stays relative to ||rhs||.
+int fgmres(irk_handle* h, const double* rhs, double* x, bool transpose, irk_stats* stats, bool from_x = false) {
   cudaStream_t st = h->st;
   const size_t ne = h->ne;
   const int m = h->m, ldh = m + 1;
   h->vcycles = 0;
-  CK(cudaMemsetAsync(x, 0, ne * 8, st));
-  // beta = ||rhs||; scal[0] = beta, scal[1] = beta^2; r0 kept in scal[9]
+  if (!from_x) CK(cudaMemsetAsync(x, 0, ne * 8, st));
+  // r0 = ||rhs|| kept in scal[9] (the reference of the stopping test); scal[0] = beta, scal[1] = beta^2
   TRY(norm2(h, rhs, 0));
   CK(cudaMemcpyAsync(h->scal + 9, h->scal, 8, cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(h->pinned, h->scal, 8, cudaMemcpyDeviceToHost, st));
@@ -1562,6 +1565,26 @@ int fgmres(irk_handle* h, const double* rhs, double* x, bool transpose, irk_stat
   double rel = (r0 == 0.0) ? 0.0 : 1.0;
   bool conv = (r0 == 0.0);
   const double* r = rhs;
+  if (from_x && !conv) {  // r = rhs - S x, beta = ||r|| (as at a restart)
+    TRY(apply_operator(h, x, h->tmp, transpose));
+    {
+      KScope k(h, IRK_K_OTHER, 24.0 * ne, (double)ne);
+      launch_sub(st, h->tmp, rhs, h->tmp, ne);
+    }
+    TRY(norm2(h, h->tmp, 0));
+    CK(cudaMemcpyAsync(h->pinned, h->scal, 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    rel = h->pinned[0] / r0;
+    if (!std::isfinite(rel)) return fail(IRK_ENONFINITE, "initial residual is %g", rel);
+    conv = rel <= h->opt.rtol;
+    r = h->tmp;
+    if (rel >= 1.0) {  // the guess is no better than zero (a fast transient between the steps): drop it
+      CK(cudaMemsetAsync(x, 0, ne * 8, st));
+      TRY(norm2(h, rhs, 0));
+      rel = 1.0;
+      r = rhs;
+    }
+  }
   while (!conv && its < h->opt.maxit) {
     scale(h, h->V, r, h->scal);  // V_0 = r / beta
     {
@@ -1795,9 +1818,9 @@ int tail_status(irk_handle* h) {
   return fail(IRK_ECUDA, "a grid barrier of the multigrid tail kernel timed out: the results of this call are invalid");
 }
 
-int solve(irk_handle* h, const double* rhs, double* k, bool transpose, irk_stats* stats) {
+int solve(irk_handle* h, const double* rhs, double* k, bool transpose, irk_stats* stats, bool from_k = false) {
   const int rc = (h->opt.solver == IRK_SOLVER_DIRK_CG) ? dirk_solve(h, rhs, k, transpose, stats)
-                                                        : fgmres(h, rhs, k, transpose, stats);
+                                                        : fgmres(h, rhs, k, transpose, stats, from_k);
   const int ts = tail_status(h);
   return ts != IRK_OK ? ts : rc;
 }
@@ -1822,6 +1845,7 @@ void irk_default_options(irk_options* o) {
   o->orth = IRK_ORTH_CGS2;
   o->solver = IRK_SOLVER_FGMRES;
   o->splitting = IRK_SPLIT_AI;
+  o->warm_start = 0;
 }
 
 const char* irk_last_error(void) { return g_err.c_str(); }
@@ -1857,6 +1881,12 @@ int irk_destroy(irk_handle* h) {
   if (!h) return IRK_OK;
   cudaStreamSynchronize(h->st);
   destroy(h);
+  return IRK_OK;
+}
+
+int irk_reset_initial_guess(irk_handle* h) {
+  if (!h) return fail(IRK_EINVAL, "null handle");
+  h->k_from_step = false;
   return IRK_OK;
 }
 
@@ -1940,6 +1970,7 @@ int irk_solve(irk_handle* h, const double* r, double* k, irk_stats* stats) {
   TRY(dev_out(h, k, bytes, 1, &kd, &khost));
   const bool ia = (h->opt.splitting == IRK_SPLIT_IA);
   // IA: w in h->k (not h->tmp, which FGMRES uses for restart residuals)
+  if (ia) h->k_from_step = false;
   const int rc = solve(h, (const double*)rd, ia ? h->k : (double*)kd, false, stats);
   if (rc != IRK_OK && rc != IRK_ENOCONV) return rc;
   if (ia) {  // k = (A^{-1} (x) I) w
@@ -1979,8 +2010,12 @@ int irk_step(irk_handle* h, const double* u_n, const double* f_space, const doub
                  (const double*)fsd, h->rhs);
   }
   CK_LAUNCH();
-  const int rc = solve(h, h->rhs, h->k, false, stats);
+  // warm start: h->k still holds the previous step's stages (w in the IA form) unless another call replaced them
+  const bool warm = h->opt.warm_start && h->k_from_step;
+  h->k_from_step = false;
+  const int rc = solve(h, h->rhs, h->k, false, stats, warm);
   if (rc != IRK_OK && rc != IRK_ENOCONV) return rc;
+  h->k_from_step = true;
   Vec8 bdt{};
   const bool ia = (h->opt.splitting == IRK_SPLIT_IA);
   for (int i = 0; i < s; ++i) bdt.v[i] = h->dt * (ia ? h->bIA[i] : h->b[i]);  // IA: dt (A^{-T} b) . w
@@ -2023,7 +2058,8 @@ int irk_step_dirichlet(irk_handle* h, const double* u_n, const double* g_stages,
   TRY(dev_in(h, f_stages, sb, 4, &fsd));
   TRY(dev_out(h, u_np1, nb, 5, &outd, &outhost));
   TRY(dev_out(h, stages_out, sb, 6, &kd, &khost));
-  if (!h->bnd) TRY(dalloc(&h->bnd, sb));  // not h->bnd: FGMRES restarts use it
+  if (!h->bnd) TRY(dalloc(&h->bnd, sb));  // its own buffer, not h->tmp: FGMRES restarts use that
+  h->k_from_step = false;
   // boundary unknowns of the solved system: k_B = A^{-1} (g - u_n) / dt (AI), w_B = (g - u_n) / dt (IA)
   Mat4 bmix{};
   for (int i = 0; i < s; ++i)
@@ -2118,6 +2154,7 @@ int irk_step_adjoint(irk_handle* h, const double* u_n, const double* stages, con
     launch_rhs(s, h->st, h->lev[0].nx, h->lev[0].cf_d, nullptr, (const double*)ld, fc, nullptr, h->rhs);
   }
   CK_LAUNCH();
+  h->k_from_step = false;
   const int rc = solve(h, h->rhs, h->k, true, stats);  // h->k = mu
   if (rc != IRK_OK && rc != IRK_ENOCONV) return rc;
   if (gd) {

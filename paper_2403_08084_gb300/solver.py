@@ -34,7 +34,8 @@ class Solver:
     def __init__(self, n_cells: int, tableau, dt: float, *, kappa=None, levels: int = 1, dim: int = 2,
                  precond: str = "lower", vcycle: str = "fp64", nu_pre: int = 2, nu_post: int = 2,
                  omega: float = 2.0 / 3.0, rtol: float = 1e-10, restart: int = 50, maxit: int = 500,
-                 orth: str = "cgs2", solver: str = "fgmres", splitting: str = "ai", stream=None):
+                 orth: str = "cgs2", solver: str = "fgmres", splitting: str = "ai", warm_start: bool = False,
+                 stream=None):
         A = np.ascontiguousarray(tableau.A, dtype=np.float64)
         self.s = int(A.shape[0])
         self.N, self.dim, self.dt = int(n_cells), int(dim), float(dt)
@@ -62,6 +63,7 @@ class Solver:
         opt.orth = L.ORTH[orth]
         opt.solver = L.SOLVER[solver]
         opt.splitting = L.SPLIT[splitting]
+        opt.warm_start = int(bool(warm_start))
         self.options = opt
         self.stream = stream if stream is not None else _current_stream()
         h = C.c_void_p()
@@ -182,3 +184,9 @@ class Solver:
         L.check(L.lib.irk_set_kappa(self._h, C.c_void_p(kap.ctypes.data)))
 
     set_kappa = irk_set_kappa
+
+    def irk_reset_initial_guess(self) -> None:
+        """The next step starts FGMRES from zero (with ``warm_start``; a no-op otherwise)."""
+        L.check(L.lib.irk_reset_initial_guess(self._h))
+
+    reset_initial_guess = irk_reset_initial_guess

@@ -25,6 +25,7 @@ def test_default_options():
     L.lib.irk_default_options(C.byref(opt))
     assert (opt.precond, opt.vcycle_prec, opt.nu_pre, opt.nu_post, opt.restart, opt.orth) == (1, 0, 2, 2, 50, 0)
     assert abs(opt.omega - 2 / 3) < 1e-15 and opt.rtol == 1e-10
+    assert (opt.solver, opt.splitting, opt.warm_start) == (0, 0, 0)
 
 
 @pytest.mark.parametrize("s", [1, 2, 3, 4])
@@ -68,6 +69,7 @@ def _create(N=8, levels=1, A=None, s=2, dt=0.1, **opt_over):
         (dict(precond=7), "precond"),
         (dict(orth=5), "orth"),
         (dict(solver=1), "lower-triangular"),
+        (dict(warm_start=2), "warm_start"),
     ],
 )
 def test_create_rejects_bad_input(kwargs, needle):
