@@ -77,6 +77,15 @@ def test_create_rejects_bad_input(kwargs, needle):
     assert rc == -1 and needle in msg
 
 
+def test_null_handle_is_rejected_without_a_gpu():
+    """Entry points given a NULL handle return IRK_EINVAL before touching the device."""
+    from paper_2403_08084_gb300 import _lib as L
+
+    assert L.lib.irk_reset_initial_guess(None) == L.IRK_EINVAL
+    assert "null" in L.lib.irk_last_error().decode()
+    assert L.lib.irk_destroy(None) == 0
+
+
 def test_missing_library_fails_loudly(tmp_path):
     """Without the built library the binding raises: there is no CPU fallback."""
     from paper_2403_08084_gb300 import _lib
