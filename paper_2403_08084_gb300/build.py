@@ -58,7 +58,7 @@ def build(verbose: bool = False, extra: list[str] | None = None) -> str:
     stamp = os.path.join(BUILD, "libirk.arch")
     stale = not os.path.exists(stamp) or open(stamp).read() != platform.machine()
     if stale or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        cmd = [nvcc()] + ARCH + ["-shared", "-o", LIB] + objs
+        cmd = [nvcc()] + ARCH + ["-shared", "-o", LIB] + objs + ["-ldl"]  # NVTX loads a profiler's library
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{' '.join(cmd)}\n{r.stdout}\n{r.stderr}")

@@ -4,6 +4,7 @@
 // and the RK update of Sec. 2.  See include/irk.h for the contract.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <atomic>
@@ -57,6 +58,16 @@ int fail(int code, const char* fmt, ...) {
     int r_ = (x);       \
     if (r_ != IRK_OK) return r_; \
   } while (0)
+
+// An NVTX range over a host scope: the entry points, the FGMRES solve and each Arnoldi step (host time
+// of enqueueing; a profiler maps the kernels launched inside to it, e.g. ncu --nvtx --nvtx-include
+// "irk_step/").  A no-op unless a tool is attached.
+struct Nvtx {
+  explicit Nvtx(const char* name) { nvtxRangePushA(name); }
+  ~Nvtx() { nvtxRangePop(); }
+  Nvtx(const Nvtx&) = delete;
+  Nvtx& operator=(const Nvtx&) = delete;
+};
 
 size_t prec_bytes(int prec) { return prec == IRK_PREC_FP64 ? 8 : (prec == IRK_PREC_FP32 ? 4 : 2); }
 
@@ -1549,6 +1560,7 @@ int run_arnoldi_step(irk_handle* h, int j, bool transpose) {
 
 // from_x: start from the contents of x instead of zero; the stopping test stays relative to ||rhs||.
 int fgmres(irk_handle* h, const double* rhs, double* x, bool transpose, irk_stats* stats, bool from_x = false) {
+  Nvtx range("fgmres");
   cudaStream_t st = h->st;
   const size_t ne = h->ne;
   const int m = h->m, ldh = m + 1;
@@ -1593,7 +1605,10 @@ int fgmres(irk_handle* h, const double* rhs, double* x, bool transpose, irk_stat
     }
     int J = 0;
     for (int j = 0; j < m; ++j) {
-      TRY(run_arnoldi_step(h, j, transpose));
+      {
+        Nvtx step_range("arnoldi");
+        TRY(run_arnoldi_step(h, j, transpose));
+      }
       CK(cudaStreamSynchronize(st));
       rel = h->pinned[2];
       const double hn = h->pinned[3];
@@ -1735,6 +1750,7 @@ int cg_iteration(irk_handle* h, int i, bool transpose) {
 }
 
 int dirk_solve(irk_handle* h, const double* rhs, double* k, bool transpose, irk_stats* stats) {
+  Nvtx range("dirk_cg");
   cudaStream_t st = h->st;
   const int s = h->s;
   Level& L0 = h->lev[0];
@@ -1942,6 +1958,7 @@ int irk_apply_mass(irk_handle* h, const double* x, double* y) {
 }
 
 int irk_apply_preconditioner(irk_handle* h, const double* v, double* z, int transpose) {
+  Nvtx range("irk_apply_preconditioner");
   if (!h || !v || !z) return fail(IRK_EINVAL, "null argument");
   if (transpose && h->opt.splitting != IRK_SPLIT_AI)
     return fail(IRK_EINVAL, "the transposed preconditioner needs the AI splitting");
@@ -1961,6 +1978,7 @@ int irk_apply_preconditioner(irk_handle* h, const double* v, double* z, int tran
 }
 
 int irk_solve(irk_handle* h, const double* r, double* k, irk_stats* stats) {
+  Nvtx range("irk_solve");
   if (!h || !r || !k) return fail(IRK_EINVAL, "null argument");
   const size_t bytes = h->ne * 8;
   const void* rd;
@@ -1985,6 +2003,7 @@ int irk_solve(irk_handle* h, const double* r, double* k, irk_stats* stats) {
 
 int irk_step(irk_handle* h, const double* u_n, const double* f_space, const double* f_coef, const double* f_stages,
              double* u_np1, double* stages_out, irk_stats* stats) {
+  Nvtx range("irk_step");
   if (!h || !u_n || !u_np1) return fail(IRK_EINVAL, "null argument");
   const int s = h->s;
   const size_t nn = h->lev[0].nn, nb = nn * 8, sb = h->ne * 8;
@@ -2043,6 +2062,7 @@ int irk_step(irk_handle* h, const double* u_n, const double* f_space, const doub
 int irk_step_dirichlet(irk_handle* h, const double* u_n, const double* g_stages, const double* f_space,
                        const double* f_coef, const double* f_stages, double* u_np1, double* stages_out,
                        irk_stats* stats) {
+  Nvtx range("irk_step_dirichlet");
   if (!h || !u_n || !g_stages || !u_np1) return fail(IRK_EINVAL, "null argument");
   if (!h->ainv_ok) return fail(IRK_EINVAL, "DAE-type boundary conditions need an invertible Butcher matrix");
   const int s = h->s;
@@ -2124,6 +2144,7 @@ int irk_step_dirichlet(irk_handle* h, const double* u_n, const double* g_stages,
 
 int irk_step_adjoint(irk_handle* h, const double* u_n, const double* stages, const double* lam_np1, double* lam_n,
                      double* grad_accum, irk_stats* stats) {
+  Nvtx range("irk_step_adjoint");
   if (!h || !u_n || !stages || !lam_np1 || !lam_n) return fail(IRK_EINVAL, "null argument");
   if (h->dim != 2) return fail(IRK_EINVAL, "irk_step_adjoint is implemented for dim = 2");
   if (h->opt.splitting != IRK_SPLIT_AI) return fail(IRK_EINVAL, "irk_step_adjoint needs the AI splitting");
