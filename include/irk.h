@@ -119,10 +119,13 @@ typedef struct {
   int orth;         /* IRK_ORTH_* (default IRK_ORTH_CGS2) */
   int solver;       /* IRK_SOLVER_* (default IRK_SOLVER_FGMRES) */
   int splitting;    /* IRK_SPLIT_* (default IRK_SPLIT_AI); IA needs an invertible A and FGMRES */
-  int warm_start;   /* 1: irk_step starts FGMRES from the stage solution of this handle's previous irk_step
-                       (the stopping test stays ||r_j||_2 <= rtol ||r||_2 with r the step's right-hand side,
-                       so the accuracy is that of a zero start); 0 (default): zero initial guess, as the
-                       paper's solver runs.  Ignored by IRK_SOLVER_DIRK_CG. */
+  int warm_start;   /* 1: irk_step starts FGMRES from the stage solution (w in the IA form) of this handle's
+                       previous irk_step, unless a call since has replaced it (irk_step_dirichlet,
+                       irk_step_adjoint, an IA-form irk_solve, irk_reset_initial_guess) or its residual is
+                       not below ||r||_2; the stopping test stays ||r_j||_2 <= rtol ||r||_2 with r the
+                       step's right-hand side, so the residual bound is that of a zero start.
+                       0 (default): zero initial guess (the paper does not say which it uses).
+                       Ignored by IRK_SOLVER_DIRK_CG. */
 } irk_options;
 
 typedef struct {
@@ -170,6 +173,7 @@ int irk_reset_initial_guess(irk_handle* h);
  *   u_np1      nodal, output (may alias u_n).
  *   stages_out stage vector, optional output of k.
  *   stats      optional.
+ * With irk_options.warm_start = 1 FGMRES starts from the previous step's stages (see there).
  * Returns IRK_ENOCONV if FGMRES did not reach rtol within maxit (outputs still written). */
 int irk_step(irk_handle* h, const double* u_n, const double* f_space, const double* f_coef,
              const double* f_stages, double* u_np1, double* stages_out, irk_stats* stats);
