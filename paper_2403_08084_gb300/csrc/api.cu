@@ -805,6 +805,7 @@ struct ZOut {
   int i;
   double scale;
   bool done;
+  void* zt = nullptr;  // FP32 / BF16 cycles: stage i's copy in the V-cycle precision (stage-major)
 };
 
 template <typename T, typename C>
@@ -1038,10 +1039,17 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2, b
     if (fused_leg(l)) {
       T* xo = (cur[l] == (T*)Lv.xa) ? (T*)Lv.xb : (T*)Lv.xa;
       const bool rec = P::rec(Lv) != nullptr;
-      KScope k(h, cls(Lv, IRK_K_JACOBI), nf * S * (4 * p + c) + nf * kCoef2 * c * (rec ? S : 1) + nc * S * p,
-               nf * S * (rec ? 45.0 : 69.0));
+      // one-block FP32 / BF16 cycle: the finest up leg writes the caller's stage vector directly
+      ZSink<T> zs{};
+      if (lowp && zo && l == 0 && S == 1 && x0 == nullptr && zo->zt != nullptr) {
+        zs = ZSink<T>{zo->z, s, zo->i, zo->scale, reinterpret_cast<T*>(zo->zt)};
+        zo->done = true;
+      }
+      KScope k(h, cls(Lv, IRK_K_JACOBI),
+               nf * S * (4 * p + c) + nf * kCoef2 * c * (rec ? S : 1) + nc * S * p + (zs.z ? nf * 8.0 : 0.0),
+               nf * S * (rec ? 45.0 : 69.0) + (zs.z ? nf : 0.0));
       MG::up_leg(S, st, Lv.nx, cf, Lv.hm, sig, rec_of(Lv), Lv.nn * kCoef2, dinv, s_d, cur[l], bfine, Lc.nx,
-                 cur[l + 1], xo, srec_of(Lv));
+                 cur[l + 1], xo, srec_of(Lv), zs);
       cur[l] = xo;
       continue;
     }
@@ -1290,9 +1298,9 @@ int precond_apply(irk_handle* h, const double* v, double* z, bool transpose) {
       }
     }
     const double scale = ia ? h->Tm[i * s + i] : 1.0;
-    ZOut zo{z, i, scale, false};
-    T* x = vcycle<T, C>(h, 1, i, (const T*)L0.b, nullptr, nu1, nu2, fuse_first, (!d3 && !zt) ? &zo : nullptr);
-    if (zo.done) continue;  // the last sweep wrote scale * x into stage i of z
+    ZOut zo{z, i, scale, false, zt ? zt + (size_t)i * zs : nullptr};
+    T* x = vcycle<T, C>(h, 1, i, (const T*)L0.b, nullptr, nu1, nu2, fuse_first, !d3 ? &zo : nullptr);
+    if (zo.done) continue;  // the last sweep (or up leg) wrote scale * x into stage i of z
     KScope k(h, IRK_K_OTHER, n * (p + 8), 0);
     T* zti = zt ? zt + (size_t)i * zs : nullptr;
     if (d3)

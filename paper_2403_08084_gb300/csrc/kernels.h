@@ -20,6 +20,18 @@ struct Cls4 {
 // The small-level tail of a 2D block V(2, 2) cycle run by one cooperative launch (mg2d_tail.cuh):
 // the down legs of levels[0 .. levels-1] (finest first), the coarsest solve, the up legs.
 constexpr int kTailMaxLevels = 8;
+// Where the last finest-level up leg of a one-block FP32 / BF16 cycle writes its result: stage i of the
+// sf-interleaved FP64 stage vector z (times scale) and the stage-major copy zt; z == nullptr: its level
+// vector as usual.
+template <typename T>
+struct ZSink {
+  double* z = nullptr;
+  int sf = 1;
+  int i = 0;
+  double scale = 1.0;
+  T* zt = nullptr;
+};
+
 template <typename C>
 struct TailSpec {
   int levels;                      // leg levels, 1 .. kTailMaxLevels
@@ -86,9 +98,10 @@ struct MG2 {
   static void down_leg(int S, cudaStream_t st, int nxf, const C* cf, double hm, const Vec8& sigma, const C* rec,
                        size_t rstride, const C* dinv, int dstride, const T* b, T* xout, int nxc, T* bc,
                        const C* srec = nullptr);
+  // zs.z != nullptr (S = 1): the up leg writes its result into stage zs.i of the FP64 stage vector instead
   static void up_leg(int S, cudaStream_t st, int nxf, const C* cf, double hm, const Vec8& sigma, const C* rec,
                      size_t rstride, const C* dinv, int dstride, const T* xin, const T* b, int nxc, const T* ec,
-                     T* xout, const C* srec = nullptr);
+                     T* xout, const C* srec = nullptr, const ZSink<T>& zs = ZSink<T>{});
   // monolithic multigrid (mmg2d.cuh) on S-interleaved level vectors, mix = dt A (or dt A^T):
   // x_out = x_in + omega D^{-1} (b - S_l x_in) with the per-node s x s inverses dblk (x_in == nullptr:
   // zero guess); r = b - S_l x; exact coarsest solve with the dense inverse of the coupled system.

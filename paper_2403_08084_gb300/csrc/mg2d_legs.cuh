@@ -309,10 +309,14 @@ __global__ void __launch_bounds__(NT) down_leg_kernel(int nxf, R relax, const T*
 // Up leg.  The block owns fine nodes [FX0, FX0 + TX) x [FY0, FY0 + TY), FX0 = 1 + TX bx.  Regions:
 //   y0 = x + P e_c on [FX0 - 2, FX0 + TX + 1], y1 = J(y0) on [FX0 - 1, FX0 + TX], y2 = J(y1) owned.
 // xout must not alias xin (other blocks read xin on their halos).
+// With zs.z set (one block, S = 1, the finest level of a triangular sweep) y2 goes to the caller's FP64
+// stage vector instead of xout: z[p * zs.sf + zs.i] = zs.scale * y2 and zs.zt[p] = y2, with y2 rounded to
+// T first (what the separate scatter of the stored iterate wrote).
 template <typename T, typename C, int S, int TX, int TY, int NT, typename R>
 __device__ __forceinline__ void up_leg_tile(int bx, int by, int nxf, const R& relax, const T* __restrict__ xin,
                                             const T* __restrict__ b, int nxc, const T* __restrict__ ec,
-                                            T* __restrict__ xout, unsigned char* smem) {
+                                            T* __restrict__ xout, unsigned char* smem,
+                                            const ZSink<T>& zs = ZSink<T>{}) {
   constexpr int W0 = TX + 4, H0 = TY + 4;
   constexpr int W1 = TX + 2, H1 = TY + 2;
   C* Y0 = reinterpret_cast<C*>(smem);
@@ -369,6 +373,13 @@ __device__ __forceinline__ void up_leg_tile(int bx, int by, int nxf, const R& re
     load_stages<T, C, S>(b, p, bv);
     auto xs = [&](int i, int dx, int dy) { return Y1[((ly + 1 + dy) * W1 + (lx + 1 + dx)) * S + i]; };
     relax.sweep(p, nxf, xs, bv, out);
+    if (zs.z != nullptr) {
+      T t;
+      st(&t, out[0]);
+      zs.z[(size_t)p * zs.sf + zs.i] = zs.scale * static_cast<double>(ld<C>(&t));
+      zs.zt[p] = t;
+      continue;
+    }
 #pragma unroll
     for (int i = 0; i < S; ++i) st(xout + (size_t)p * S + i, out[i]);
   }
@@ -377,10 +388,10 @@ __device__ __forceinline__ void up_leg_tile(int bx, int by, int nxf, const R& re
 template <typename T, typename C, int S, int TX, int TY, int NT, typename R>
 __global__ void __launch_bounds__(NT) up_leg_kernel(int nxf, R relax, const T* __restrict__ xin,
                                                      const T* __restrict__ b, int nxc, const T* __restrict__ ec,
-                                                     T* __restrict__ xout) {
+                                                     T* __restrict__ xout, ZSink<T> zs) {
   IRK_PDL_ENTRY;
   extern __shared__ unsigned char leg_smem[];
-  up_leg_tile<T, C, S, TX, TY, NT, R>(blockIdx.x, blockIdx.y, nxf, relax, xin, b, nxc, ec, xout, leg_smem);
+  up_leg_tile<T, C, S, TX, TY, NT, R>(blockIdx.x, blockIdx.y, nxf, relax, xin, b, nxc, ec, xout, leg_smem, zs);
 }
 
 // ----------------------------------------------------------------------------
@@ -405,14 +416,14 @@ void launch_down_leg(cudaStream_t st, int nxf, const R& relax, const T* b, T* xo
 
 template <typename T, typename C, int S, int TX, int TY, int NT, typename R>
 void launch_up_leg(cudaStream_t st, int nxf, const R& relax, const T* xin, const T* b, int nxc, const T* ec,
-                   T* xout) {
+                   T* xout, const ZSink<T>& zs) {
   const size_t smem = sizeof(C) * S * (size_t)((TX + 4) * (TY + 4) + (TX + 2) * (TY + 2));
   auto kern = up_leg_kernel<T, C, S, TX, TY, NT, R>;
   leg_smem_attr(kern, smem);
   const int m = nxf - 2;
   dim3 g((m + TX - 1) / TX, (m + TY - 1) / TY);
   launch_pdl(TX < 32 ? pdl_mode() >= 1 : pdl_mode() == 2, kern, g, dim3(NT), smem, st, nxf, relax, xin, b, nxc, ec,
-             xout);
+             xout, zs);
 }
 
 // Levels whose fine grid has at least kMgLargeNx nodes per axis use the large tiles (fewer halo
@@ -434,13 +445,14 @@ void down_leg_s(cudaStream_t st, int nxf, const R& relax, const T* b, T* xout, i
 }
 
 template <typename T, typename C, int S, typename R>
-void up_leg_s(cudaStream_t st, int nxf, const R& relax, const T* xin, const T* b, int nxc, const T* ec, T* xout) {
+void up_leg_s(cudaStream_t st, int nxf, const R& relax, const T* xin, const T* b, int nxc, const T* ec, T* xout,
+              const ZSink<T>& zs = ZSink<T>{}) {
   if (nxf >= kLegLargeNx)
-    launch_up_leg<T, C, S, 32, 16, 256>(st, nxf, relax, xin, b, nxc, ec, xout);
+    launch_up_leg<T, C, S, 32, 16, 256>(st, nxf, relax, xin, b, nxc, ec, xout, zs);
   else if (nxf >= kLegMediumNx)  // regions 20 x 20, 18 x 18, 16 x 16
-    launch_up_leg<T, C, S, 16, 16, 256>(st, nxf, relax, xin, b, nxc, ec, xout);
+    launch_up_leg<T, C, S, 16, 16, 256>(st, nxf, relax, xin, b, nxc, ec, xout, zs);
   else  // regions 12 x 12, 10 x 10, 8 x 8
-    launch_up_leg<T, C, S, 8, 8, 160>(st, nxf, relax, xin, b, nxc, ec, xout);
+    launch_up_leg<T, C, S, 8, 8, 160>(st, nxf, relax, xin, b, nxc, ec, xout, zs);
 }
 
 #define IRK_LEG_DISPATCH(S, FN, ...)                                  \
@@ -473,7 +485,8 @@ void down_leg_any(cudaStream_t st, int nxf, const C* cf, double hm, const Vec8& 
 
 template <typename T, typename C, int S>
 void up_leg_any(cudaStream_t st, int nxf, const C* cf, double hm, const Vec8& sigma, const C* rec, size_t rstride,
-                const C* dinv, int dstride, const T* xin, const T* b, int nxc, const T* ec, T* xout, const C* srec) {
+                const C* dinv, int dstride, const T* xin, const T* b, int nxc, const T* ec, T* xout, const C* srec,
+                const ZSink<T>& zs) {
   if constexpr (S == 1) {
     if (srec != nullptr && rec != nullptr) {
       ScaledRelax<C> r{rec, srec, dinv};
@@ -481,12 +494,14 @@ void up_leg_any(cudaStream_t st, int nxf, const C* cf, double hm, const Vec8& si
       return;
     }
   }
+  // the stage-vector sink only for one block
+  const ZSink<T> z1 = (S == 1) ? zs : ZSink<T>{};
   if (rec != nullptr) {
     BlockRelax<C, S, true> r{rec, rstride, nullptr, C(0), {}, dinv, dstride};
-    up_leg_s<T, C, S>(st, nxf, r, xin, b, nxc, ec, xout);
+    up_leg_s<T, C, S>(st, nxf, r, xin, b, nxc, ec, xout, z1);
   } else {
     BlockRelax<C, S, false> r{nullptr, 0, cf, (C)hm, to_vec<C>(sigma), dinv, dstride};
-    up_leg_s<T, C, S>(st, nxf, r, xin, b, nxc, ec, xout);
+    up_leg_s<T, C, S>(st, nxf, r, xin, b, nxc, ec, xout, z1);
   }
 }
 
@@ -524,8 +539,9 @@ void MG2<T, C>::down_leg(int S, cudaStream_t st, int nxf, const C* cf, double hm
 template <typename T, typename C>
 void MG2<T, C>::up_leg(int S, cudaStream_t st, int nxf, const C* cf, double hm, const Vec8& sigma, const C* rec,
                        size_t rstride, const C* dinv, int dstride, const T* xin, const T* b, int nxc, const T* ec,
-                       T* xout, const C* srec) {
-  IRK_LEG_DISPATCH(S, up_leg_any, st, nxf, cf, hm, sigma, rec, rstride, dinv, dstride, xin, b, nxc, ec, xout, srec)
+                       T* xout, const C* srec, const ZSink<T>& zs) {
+  IRK_LEG_DISPATCH(S, up_leg_any, st, nxf, cf, hm, sigma, rec, rstride, dinv, dstride, xin, b, nxc, ec, xout, srec,
+                   zs)
 }
 
 template <typename T, typename C>
