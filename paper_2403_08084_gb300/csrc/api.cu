@@ -802,11 +802,25 @@ struct Prec<__nv_bfloat16, float> {
 // stage vector z (the triangular sweeps' scatter); done is set when the last finest-level sweep did so.
 struct ZOut {
   double* z;
-  int i;
+  int i;         // < 0: all stages of a batched or monolithic cycle, stage k scaled by sc[k]
   double scale;
   bool done;
-  void* zt = nullptr;  // FP32 / BF16 cycles: stage i's copy in the V-cycle precision (stage-major)
+  void* zt = nullptr;  // FP32 / BF16 one-block cycles: stage i's copy in the V-cycle precision (stage-major)
+  double sc[4] = {1.0, 1.0, 1.0, 1.0};
 };
+
+// The up-leg sink for a ZOut request (FP32 / BF16 cycles; see ZSink).
+template <typename T>
+ZSink<T> zsink_of(const ZOut& zo, int s) {
+  ZSink<T> zs{};
+  zs.z = zo.z;
+  zs.sf = s;
+  zs.i = zo.i;
+  zs.scale = zo.scale;
+  zs.zt = reinterpret_cast<T*>(zo.zt);
+  for (int k = 0; k < 4; ++k) zs.sc[k] = zo.sc[k];
+  return zs;
+}
 
 template <typename T, typename C>
 T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2, bool first_done = false,
@@ -1039,10 +1053,12 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2, b
     if (fused_leg(l)) {
       T* xo = (cur[l] == (T*)Lv.xa) ? (T*)Lv.xb : (T*)Lv.xa;
       const bool rec = P::rec(Lv) != nullptr;
-      // one-block FP32 / BF16 cycle: the finest up leg writes the caller's stage vector directly
+      // FP32 / BF16 cycle: the finest up leg writes the caller's stage vector directly (one block, or all
+      // stages of the batched cycle)
       ZSink<T> zs{};
-      if (lowp && zo && l == 0 && S == 1 && x0 == nullptr && zo->zt != nullptr) {
-        zs = ZSink<T>{zo->z, s, zo->i, zo->scale, reinterpret_cast<T*>(zo->zt)};
+      if (lowp && zo && l == 0 && x0 == nullptr &&
+          ((S == 1 && zo->i >= 0 && zo->zt != nullptr) || (S == s && S > 1 && zo->i < 0))) {
+        zs = zsink_of<T>(*zo, s);
         zo->done = true;
       }
       KScope k(h, cls(Lv, IRK_K_JACOBI),
@@ -1093,7 +1109,7 @@ T* vcycle(irk_handle* h, int S, int st0, const T* b0, T* x0, int nu1, int nu2, b
 // transpose: the transposed cycle (the adjoint's preconditioner): S^T = I (x) M + dt A^T (x) K, D^{-T},
 // inv^T; the caller swaps nu1 and nu2, and R = P^T keeps the transfer pair.
 template <typename T, typename C>
-T* mmg_vcycle(irk_handle* h, const T* b0, T* x0, int nu1, int nu2, bool transpose = false) {
+T* mmg_vcycle(irk_handle* h, const T* b0, T* x0, int nu1, int nu2, bool transpose = false, ZOut* zo = nullptr) {
   using MG = MG2<T, C>;
   using P = Prec<T, C>;
   constexpr bool f64 = std::is_same<C, double>::value;
@@ -1180,7 +1196,14 @@ T* mmg_vcycle(irk_handle* h, const T* b0, T* x0, int nu1, int nu2, bool transpos
       T* xo = (cur[l] == (T*)Lv.xa) ? (T*)Lv.xb : (T*)Lv.xa;
       KScope k(h, cls(Lv, IRK_K_JACOBI), nf * (3 * s * p + kCoef2 * c + s * s * c) + nc * s * p,
                nf * (2 * (fres + fblk) + 5.0 * s));
-      MG::mmg_up_leg(s, st, Lv.nx, P::cf(Lv), Lv.hm, mix, blk(Lv), transpose, cur[l], bfine, Lc.nx, cur[l + 1], xo);
+      // FP32 / BF16: the finest up leg writes the caller's stage vector directly
+      ZSink<T> zs{};
+      if (!f64 && zo && l == 0 && x0 == nullptr && zo->i < 0) {
+        zs = zsink_of<T>(*zo, s);
+        zo->done = true;
+      }
+      MG::mmg_up_leg(s, st, Lv.nx, P::cf(Lv), Lv.hm, mix, blk(Lv), transpose, cur[l], bfine, Lc.nx, cur[l + 1], xo,
+                     zs);
       cur[l] = xo;
       continue;
     }
@@ -1223,9 +1246,12 @@ int precond_apply(irk_handle* h, const double* v, double* z, bool transpose) {
         KScope k(h, IRK_K_OTHER, ne * (8 + p), 0);
         MG::cast_to(st, v, (T*)L0.b, h->ne);
       }
-      T* x = mmg_vcycle<T, C>(h, (const T*)L0.b, nullptr, nu1, nu2, transpose);
-      KScope k(h, IRK_K_OTHER, ne * (8 + p), 0);
-      MG::cast_from(st, x, z, h->ne);
+      ZOut zo{z, -1, 1.0, false};
+      T* x = mmg_vcycle<T, C>(h, (const T*)L0.b, nullptr, nu1, nu2, transpose, &zo);
+      if (!zo.done) {
+        KScope k(h, IRK_K_OTHER, ne * (8 + p), 0);
+        MG::cast_from(st, x, z, h->ne);
+      }
     }
     CK_LAUNCH();
     return IRK_OK;
@@ -1238,7 +1264,14 @@ int precond_apply(irk_handle* h, const double* v, double* z, bool transpose) {
         KScope k(h, IRK_K_OTHER, ne * (8 + p), 0);
         MG::cast_to(st, v, (T*)L0.b, h->ne);
       }
-      T* x = vcycle<T, C>(h, s, 0, (const T*)L0.b, nullptr, nu1, nu2);
+      // the batched cycle's finest up leg writes z, with the IA scaling below folded in
+      ZOut zo{z, -1, 1.0, false};
+      for (int i = 0; i < s; ++i) zo.sc[i] = ia ? h->Tm[i * s + i] : 1.0;
+      T* x = vcycle<T, C>(h, s, 0, (const T*)L0.b, nullptr, nu1, nu2, false, &zo);
+      if (zo.done) {
+        CK_LAUNCH();
+        return IRK_OK;
+      }
       KScope k(h, IRK_K_OTHER, ne * (8 + p), 0);
       MG::cast_from(st, x, z, h->ne);
     }

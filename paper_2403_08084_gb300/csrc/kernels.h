@@ -20,9 +20,10 @@ struct Cls4 {
 // The small-level tail of a 2D block V(2, 2) cycle run by one cooperative launch (mg2d_tail.cuh):
 // the down legs of levels[0 .. levels-1] (finest first), the coarsest solve, the up legs.
 constexpr int kTailMaxLevels = 8;
-// Where the last finest-level up leg of a one-block FP32 / BF16 cycle writes its result: stage i of the
-// sf-interleaved FP64 stage vector z (times scale) and the stage-major copy zt; z == nullptr: its level
-// vector as usual.
+// Where the last finest-level up leg of an FP32 / BF16 cycle writes its result instead of its level
+// vector (z == nullptr: the level vector as usual).  One block (i >= 0): stage i of the sf-interleaved FP64
+// stage vector z, times scale, and the stage-major copy zt.  All stages of a batched or monolithic cycle
+// (i < 0, S == sf): z[p sf + k] = sc[k] * x_k.  Each value is rounded to T first, as the stored iterate was.
 template <typename T>
 struct ZSink {
   double* z = nullptr;
@@ -30,6 +31,7 @@ struct ZSink {
   int i = 0;
   double scale = 1.0;
   T* zt = nullptr;
+  double sc[4] = {1.0, 1.0, 1.0, 1.0};
 };
 
 template <typename C>
@@ -117,7 +119,8 @@ struct MG2 {
   static void mmg_down_leg(int S, cudaStream_t st, int nxf, const C* cf, double hm, const Mat4& mix, const C* dblk,
                            bool transpose, const T* b, T* xout, int nxc, T* bc);
   static void mmg_up_leg(int S, cudaStream_t st, int nxf, const C* cf, double hm, const Mat4& mix, const C* dblk,
-                         bool transpose, const T* xin, const T* b, int nxc, const T* ec, T* xout);
+                         bool transpose, const T* xin, const T* b, int nxc, const T* ec, T* xout,
+                         const ZSink<T>& zs = ZSink<T>{});
   // the tail of S batched blocks (S = 1: one block) as one cooperative launch (mg2d_tail.cuh)
   static cudaError_t tail_cycle(int S, cudaStream_t st, const TailSpec<C>& spec, int dstride);
 };

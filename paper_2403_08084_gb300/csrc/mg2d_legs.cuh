@@ -309,9 +309,10 @@ __global__ void __launch_bounds__(NT) down_leg_kernel(int nxf, R relax, const T*
 // Up leg.  The block owns fine nodes [FX0, FX0 + TX) x [FY0, FY0 + TY), FX0 = 1 + TX bx.  Regions:
 //   y0 = x + P e_c on [FX0 - 2, FX0 + TX + 1], y1 = J(y0) on [FX0 - 1, FX0 + TX], y2 = J(y1) owned.
 // xout must not alias xin (other blocks read xin on their halos).
-// With zs.z set (one block, S = 1, the finest level of a triangular sweep) y2 goes to the caller's FP64
-// stage vector instead of xout: z[p * zs.sf + zs.i] = zs.scale * y2 and zs.zt[p] = y2, with y2 rounded to
-// T first (what the separate scatter of the stored iterate wrote).
+// With zs.z set (the finest level) y2 goes to the caller's FP64 stage vector instead of xout (ZSink in
+// kernels.h): one block, z[p * zs.sf + zs.i] = zs.scale * y2 and zs.zt[p] = y2; all stages (zs.i < 0),
+// z[p * S + k] = zs.sc[k] * y2_k; y2 rounded to T first (what the separate scatter or cast of the stored
+// iterate wrote).
 template <typename T, typename C, int S, int TX, int TY, int NT, typename R>
 __device__ __forceinline__ void up_leg_tile(int bx, int by, int nxf, const R& relax, const T* __restrict__ xin,
                                             const T* __restrict__ b, int nxc, const T* __restrict__ ec,
@@ -374,10 +375,19 @@ __device__ __forceinline__ void up_leg_tile(int bx, int by, int nxf, const R& re
     auto xs = [&](int i, int dx, int dy) { return Y1[((ly + 1 + dy) * W1 + (lx + 1 + dx)) * S + i]; };
     relax.sweep(p, nxf, xs, bv, out);
     if (zs.z != nullptr) {
-      T t;
-      st(&t, out[0]);
-      zs.z[(size_t)p * zs.sf + zs.i] = zs.scale * static_cast<double>(ld<C>(&t));
-      zs.zt[p] = t;
+      if (zs.i >= 0) {
+        T t;
+        st(&t, out[0]);
+        zs.z[(size_t)p * zs.sf + zs.i] = zs.scale * static_cast<double>(ld<C>(&t));
+        zs.zt[p] = t;
+      } else {
+#pragma unroll
+        for (int i = 0; i < S; ++i) {
+          T t;
+          st(&t, out[i]);
+          zs.z[(size_t)p * S + i] = zs.sc[i] * static_cast<double>(ld<C>(&t));
+        }
+      }
       continue;
     }
 #pragma unroll
@@ -494,8 +504,8 @@ void up_leg_any(cudaStream_t st, int nxf, const C* cf, double hm, const Vec8& si
       return;
     }
   }
-  // the stage-vector sink only for one block
-  const ZSink<T> z1 = (S == 1) ? zs : ZSink<T>{};
+  // the stage-vector sink: one block, or all S stages of a batched cycle
+  const ZSink<T> z1 = (S == 1 || zs.i < 0) ? zs : ZSink<T>{};
   if (rec != nullptr) {
     BlockRelax<C, S, true> r{rec, rstride, nullptr, C(0), {}, dinv, dstride};
     up_leg_s<T, C, S>(st, nxf, r, xin, b, nxc, ec, xout, z1);
@@ -519,13 +529,13 @@ void mmg_down_leg_any(cudaStream_t st, int nxf, const C* cf, double hm, const Ma
 
 template <typename T, typename C, int S>
 void mmg_up_leg_any(cudaStream_t st, int nxf, const C* cf, double hm, const Mat4& mix, const C* dblk, bool transpose,
-                    const T* xin, const T* b, int nxc, const T* ec, T* xout) {
+                    const T* xin, const T* b, int nxc, const T* ec, T* xout, const ZSink<T>& zs) {
   if (transpose) {
     MonoRelax<C, S, true> r{cf, (C)hm, to_mat<C>(mix), dblk};
-    up_leg_s<T, C, S>(st, nxf, r, xin, b, nxc, ec, xout);
+    up_leg_s<T, C, S>(st, nxf, r, xin, b, nxc, ec, xout, zs);
   } else {
     MonoRelax<C, S, false> r{cf, (C)hm, to_mat<C>(mix), dblk};
-    up_leg_s<T, C, S>(st, nxf, r, xin, b, nxc, ec, xout);
+    up_leg_s<T, C, S>(st, nxf, r, xin, b, nxc, ec, xout, zs);
   }
 }
 
@@ -552,8 +562,9 @@ void MG2<T, C>::mmg_down_leg(int S, cudaStream_t st, int nxf, const C* cf, doubl
 
 template <typename T, typename C>
 void MG2<T, C>::mmg_up_leg(int S, cudaStream_t st, int nxf, const C* cf, double hm, const Mat4& mix, const C* dblk,
-                           bool transpose, const T* xin, const T* b, int nxc, const T* ec, T* xout) {
-  IRK_LEG_DISPATCH(S, mmg_up_leg_any, st, nxf, cf, hm, mix, dblk, transpose, xin, b, nxc, ec, xout)
+                           bool transpose, const T* xin, const T* b, int nxc, const T* ec, T* xout,
+                           const ZSink<T>& zs) {
+  IRK_LEG_DISPATCH(S, mmg_up_leg_any, st, nxf, cf, hm, mix, dblk, transpose, xin, b, nxc, ec, xout, zs)
 }
 
 #undef IRK_LEG_DISPATCH
